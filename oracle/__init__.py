@@ -1,0 +1,6 @@
+"""FP64 CPU oracle of the staggered-grid Navier-Stokes time step.
+
+TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the CPU-baseline
+leg of bench.py.  It shares no code with the CUDA library.
+"""
+from .oracle import Oracle, bc_faces, build, exact_poisson_periodic, PERIODIC, WALL  # noqa: F401
