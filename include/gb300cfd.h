@@ -1,0 +1,216 @@
+/* gb300cfd — explicit staggered-grid incompressible Navier-Stokes time step
+ * on GB300 (sm_103a), behind a plain C ABI.
+ *
+ * The method is the 3D CFD demonstration code of Blazewicz et al.,
+ * "A Massive Data Parallel Computational Framework for Petascale/Exascale
+ * Hybrid Computer Systems": Navier-Stokes with modified pressure phi = p/rho
+ * (Sec. 4.1, Eq. 1) and incompressibility (Eq. 2), finite differences on a
+ * regular rectangular staggered grid (Sec. 4.1), explicit Runge-Kutta Method
+ * of Lines time integration (Sec. 1), block-structured grid components with
+ * ghost regions of run-time width filled by copy from the neighbouring
+ * component or from the physical boundary condition (Sec. 1.1), and a
+ * velocity update u <- u - (dt/rho) grad p with separate in/out velocity
+ * buffers (the UPDATE_VELOCITY kernel descriptor of Sec. 3, Listing 1).
+ *
+ * Discretisation (where the paper is silent):
+ *   MAC placement, cell (i,j,k) of size h = (hx,hy,hz):
+ *     p at ((i+1/2)hx,(j+1/2)hy,(k+1/2)hz); u, v, w on the +x, +y, +z faces.
+ *   F(u) = -(u . grad) u + nu lap u, advective form, central differences;
+ *     order 2 (ghost >= 1) or order 4 (ghost = 2).
+ *   Heun RK2, each stage projected:
+ *     stage 1: w = u^n + dt F(u^n),              c = 1
+ *     stage 2: w = 1/2 u^n + 1/2 u1 + 1/2 dt F(u1), c = 1/2
+ *     r = (D w)/(c dt);  p <- K weighted Jacobi sweeps of L p = r (warm start);
+ *     u_next = w - c dt G p.
+ *
+ * Conventions for every entry point:
+ *   - Return value is a cfd_status; no call aborts, exits or throws.  On an
+ *     error, cfd_last_error() returns a message (a per-thread copy).
+ *   - Work is enqueued asynchronously on the grid's stream (the stream given
+ *     at creation; 0 means the legacy default stream).  Internally the
+ *     library runs on a private stream joined to the caller's stream with
+ *     events on entry and exit, so ordering with the caller's own work on
+ *     that stream is preserved.  Calls that return host values
+ *     (cfd_reduce, cfd_residual, cfd_check) synchronise.
+ *   - CFD_ECUDA is sticky: after an asynchronous CUDA error the grid refuses
+ *     further work.
+ *   - Arrays: one array per field and block, storage type chosen at creation
+ *     (FP32, BF16 or FP16; arithmetic is always FP32, global reductions FP64).
+ *     Layout: (nz+2g) planes x (ny+2g) rows x row pitch, x fastest; the
+ *     interior x = 0 of every row is 128-byte aligned.  cfd_array_layout()
+ *     gives the exact offsets.  Device memory is either bound by the caller
+ *     (cfd_bind_memory; the library never frees it) or allocated by the
+ *     library (cfd_alloc_memory; freed by cfd_grid_destroy).
+ */
+#ifndef GB300CFD_H
+#define GB300CFD_H
+
+#include <stddef.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct cfd_grid cfd_grid;
+
+typedef enum {
+  CFD_OK = 0,
+  CFD_EINVAL = 1,        /* bad argument (sizes, pointers, face/array ids) */
+  CFD_ENOMEM = 2,        /* bound memory too small / allocation failed */
+  CFD_ECUDA = 3,         /* a CUDA call failed (sticky) */
+  CFD_ESTATE = 4,        /* call out of order (no memory bound, ...) */
+  CFD_EUNSUPPORTED = 5,  /* valid but not implemented combination */
+  CFD_ENONFINITE = 6,    /* a reduction met NaN or Inf */
+  CFD_ETIMEOUT = 7       /* a bounded device wait gave up (device error flag) */
+} cfd_status;
+
+typedef enum { CFD_F32 = 0, CFD_BF16 = 1, CFD_F16 = 2 } cfd_dtype;
+
+/* Face kinds.  PERIODIC: ghost cells copy the opposite side (or, in a block
+ * set, the neighbouring block).  WALL: no-slip wall moving with a given
+ * tangential velocity: the wall-normal velocity is zero (the normal face
+ * unknown on the high side is held at 0), tangential ghosts are
+ * 2 U_wall - first interior, pressure ghosts copy the first interior
+ * (zero normal gradient).  Sec. 1.1: physical boundaries are set from
+ * boundary conditions, internal ones copied from neighbours. */
+typedef enum { CFD_BC_PERIODIC = 0, CFD_BC_WALL = 1 } cfd_bc;
+
+/* Array ids.  State: U, V, W (velocity) and P (pressure, also the Jacobi
+ * warm start).  Work arrays: WU..WW (provisional stage velocity), U1..W1
+ * (stage-1 velocity), P2 (Jacobi ping-pong), R (Poisson right-hand side). */
+typedef enum {
+  CFD_U = 0, CFD_V = 1, CFD_W = 2, CFD_P = 3,
+  CFD_WU = 4, CFD_WV = 5, CFD_WW = 6,
+  CFD_U1 = 7, CFD_V1 = 8, CFD_W1 = 9,
+  CFD_P2 = 10, CFD_R = 11,
+  CFD_NUM_ARRAYS = 12
+} cfd_array;
+
+/* Velocity triples for cfd_stage / cfd_project / cfd_reduce. */
+typedef enum { CFD_SET_U = 0, CFD_SET_W = 1, CFD_SET_U1 = 2 } cfd_vset;
+
+/* ---------------------------------------------------------------- set-up */
+
+/* One block of dims[0] x dims[1] x dims[2] interior cells (x, y, z), ghost
+ * width 1 or 2 (Sec. 1.1: chosen at run time), cell size h (> 0), storage
+ * dtype.  All faces start PERIODIC.  dims[d] >= 2*ghost.  stream is a
+ * cudaStream_t (may be NULL).  *out receives the handle. */
+cfd_status cfd_grid_create(const int dims[3], int ghost, const double h[3], int storage,
+                           void* stream, cfd_grid** out);
+
+/* nblocks blocks tiling the periodic box global_dims exactly as a
+ * rectilinear (slab-product) tiling: dims and origin are nblocks*3 ints
+ * (x,y,z per block).  Ghost cells are copied from the neighbouring block
+ * (Sec. 1.1: the driver's ghost exchange between grid components, here an
+ * on-device copy).  Every block needs dims[d] >= 2*ghost. */
+cfd_status cfd_blockset_create(int nblocks, const int* dims, const int* origin,
+                               const int global_dims[3], int ghost, const double h[3],
+                               int storage, void* stream, cfd_grid** out);
+
+/* Releases the grid (and memory from cfd_alloc_memory).  Waits for the
+ * grid's queued work. */
+cfd_status cfd_grid_destroy(cfd_grid* g);
+
+/* Device bytes needed for all arrays of all blocks plus the library's
+ * tables and reduction scratch. */
+cfd_status cfd_memory_bytes(const cfd_grid* g, size_t* bytes);
+
+/* Binds caller-owned device memory (>= cfd_memory_bytes, 256-byte aligned).
+ * The caller keeps ownership and must keep it alive until destroy. */
+cfd_status cfd_bind_memory(cfd_grid* g, void* dev_ptr, size_t bytes);
+
+/* Allocates the memory with cudaMalloc instead (owned by the grid). */
+cfd_status cfd_alloc_memory(cfd_grid* g);
+
+/* Layout of one array of one block: byte offset of element (-g,-g,-g)
+ * from the bound base, shape (z, y, x) including ghosts, strides in
+ * elements (z, y, x), and element size in bytes. */
+cfd_status cfd_array_layout(const cfd_grid* g, int block, int array, long long* offset_bytes,
+                            long long shape[3], long long strides[3], int* elem_bytes);
+
+/* Number of blocks, ghost width and interior dims of a block. */
+cfd_status cfd_block_info(const cfd_grid* g, int block, int dims[3], int origin[3], int* ghost);
+
+/* Face 0..5 = -x,+x,-y,+y,-z,+z.  Periodic faces come in pairs; WALL needs
+ * a single-block grid; the normal component of wall_velocity must be 0
+ * (may be NULL for a still wall). */
+cfd_status cfd_set_bc(cfd_grid* g, int face, int kind, const double wall_velocity[3]);
+
+/* Physical and solver parameters: viscosity nu >= 0, Jacobi sweeps per
+ * solve (>= 0), Jacobi weight omega in (0, 2), stencil order 2 or 4
+ * (order 4 needs ghost 2). */
+cfd_status cfd_set_params(cfd_grid* g, double nu, int jacobi_iters, double omega, int order);
+
+/* ------------------------------------------------------ steps of the path */
+
+/* Fill ghost cells of the arrays in mask (bit = 1 << cfd_array) on every
+ * block: periodic/neighbour copy or wall rule, axis passes x then y then z
+ * over the full extent (a later pass wins on edges and corners).  Sec. 1.1. */
+cfd_status cfd_ghost_fill(cfd_grid* g, unsigned mask);
+
+/* out = a * X + b * Y + c * F(Y) on the interior, F(u) = -(u.grad)u + nu lap u
+ * (Eq. 1 without pressure, f = 0).  Y needs filled ghosts; wall-normal
+ * faces of out are set to 0; out's ghosts are not filled.  x_set is ignored
+ * when a == 0.  out must differ from x_set and y_set. */
+cfd_status cfd_stage(cfd_grid* g, double a, int x_set, double b, int y_set, double c,
+                     int out_set);
+
+/* F(U) into WU, WV, WW (cfd_stage(g, 0, -, 0, U, 1, W)). */
+cfd_status cfd_rhs_eval(cfd_grid* g);
+
+/* R = (D W)/c_dt (W ghosts must be filled), then iters weighted Jacobi
+ * sweeps on P (warm start, ghosts filled) with the pressure halo refreshed
+ * by each sweep, result in P.  If residual != NULL, also ||L P - R||_2 in
+ * FP64 (synchronises).  Eq. 2 enforced through the pressure Poisson
+ * equation. */
+cfd_status cfd_pressure_solve(cfd_grid* g, double c_dt, int iters, double* residual);
+
+/* iters weighted Jacobi sweeps on P against the current R (no divergence
+ * step), ghost-on-write halo refresh, result in P.  The sweep of Sec. 4.1's
+ * pressure solve on its own, e.g. to continue a solve or to time it. */
+cfd_status cfd_jacobi(cfd_grid* g, int iters);
+
+/* out = W - c_dt G P on the interior (wall-normal faces 0), ghosts of out
+ * filled.  The UPDATE_VELOCITY kernel of Sec. 3 with rho = 1. */
+cfd_status cfd_project(cfd_grid* g, double c_dt, int out_set);
+
+/* One full RK2 stage (1 or 2) with time step dt, as listed above; stage 2
+ * overwrites U, stage 1 writes U1. */
+cfd_status cfd_rk_step(cfd_grid* g, int stage, double dt);
+
+/* n full RK2 steps (both stages) replayed from a CUDA graph captured on the
+ * first call for this dt; t += n dt.  Does not synchronise. */
+cfd_status cfd_step(cfd_grid* g, double dt, int n);
+
+/* FP64 global quantities of a velocity set over all blocks' interiors:
+ * kinetic energy 1/2 sum |u|^2 hx hy hz, max |u_d|, max |D u|.  NULL
+ * pointers are skipped.  Synchronises; CFD_ENONFINITE if any is NaN/Inf. */
+cfd_status cfd_reduce(cfd_grid* g, int set, double* kinetic_energy, double* max_abs_u,
+                      double* max_abs_div);
+
+/* ||L P - R||_2 over all interior cells, FP64.  Synchronises. */
+cfd_status cfd_residual(cfd_grid* g, double* residual);
+
+/* Simulation time and step counter (for checkpoint/resume). */
+cfd_status cfd_get_state(const cfd_grid* g, double* t, long long* step);
+cfd_status cfd_set_state(cfd_grid* g, double t, long long step);
+
+/* Copy the interior of one array of one block between host memory
+ * (compact (nz, ny, nx), storage dtype; pinned for asynchronous copies)
+ * and the device.  to_device != 0: host -> device.  Asynchronous. */
+cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int to_device);
+
+/* Number of kernel launches this grid has enqueued so far (graph replays
+ * count every kernel node once per replay). */
+cfd_status cfd_stats(const cfd_grid* g, long long* kernel_launches);
+
+/* Waits for the grid's work and reports device-side errors. */
+cfd_status cfd_check(cfd_grid* g);
+
+/* Last error message of the calling thread (never NULL). */
+const char* cfd_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif

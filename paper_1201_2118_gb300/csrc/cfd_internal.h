@@ -1,0 +1,82 @@
+// Internal types shared by the runtime and the kernel translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+namespace cfd {
+
+constexpr int kNumArrays = 12;   // matches CFD_NUM_ARRAYS
+constexpr int kMaxBlocks = 512;
+constexpr int kAlignBytes = 128; // interior x = 0 of every row, and row pitch
+constexpr int kMaxGhost = 2;
+
+// Array ids (same numbering as cfd_array).
+enum Arr {
+  A_U = 0, A_V = 1, A_W = 2, A_P = 3,
+  A_WU = 4, A_WV = 5, A_WW = 6,
+  A_U1 = 7, A_V1 = 8, A_W1 = 9,
+  A_P2 = 10, A_R = 11
+};
+
+// Field kind of each array: 0 u, 1 v, 2 w (velocity components), 3 scalar.
+__host__ __device__ inline int array_kind(int a) {
+  return (a == A_P || a == A_P2 || a == A_R) ? 3 : (a < 3 ? a : (a - 4) % 3);
+}
+
+enum Bc { BC_PERIODIC = 0, BC_WALL = 1 };
+
+// One grid component (block) as the kernels see it.
+struct BlockDev {
+  int n[3];                    // interior cells
+  int py;                      // row pitch (elements)
+  long long pz;                // plane pitch (elements)
+  long long org[kNumArrays];   // element offset of interior (0,0,0) per array
+  int nbr[6];                  // neighbour block per face (self if periodic single block)
+  int bc[6];                   // Bc per face
+  float wall[6][3];            // wall velocity per face
+};
+
+// What every launch needs.
+struct Launch {
+  const BlockDev* blocks;      // device table
+  int nblocks;
+  void* base;                  // arena base (arrays addressed by element offsets)
+  int dtype;                   // 0 f32, 1 bf16, 2 f16
+  int ghost;
+  float ih[3];                 // 1/h
+  float ih2[3];                // 1/h^2
+  int* err_flag;               // device error word
+  cudaStream_t stream;
+  int sms;                     // multiprocessor count
+  // host copy of block dims for grid sizing
+  const int (*hn)[3];
+};
+
+// Kernel variants (autotuned).
+struct JacobiCfg { int vx, ty, zc; };   // x vector width, warps per CTA (rows), z chunk
+struct StencilCfg { int ty, zc; };      // rows per CTA (32 x ty threads), z chunk
+
+long long count_tiles(const Launch& L, int tx, int ty, int tz);
+
+cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr,
+                         const long long* d_prefix, long long total);
+cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float a,
+                         const int* xset, float b, const int* yset, float cdt, const int* oset,
+                         float nu);
+cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* wset,
+                              float inv_cdt, int r_arr);
+cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                          float omega);
+cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset, int p_arr,
+                           float cdt, const int* oset);
+cudaError_t launch_copy(const Launch& L, const StencilCfg& c, int src, int dst);
+
+// FP64 reductions: per-CTA partials into 'partials' (nparts x 4 doubles),
+// then a one-CTA fixed-order pass into 'out' (4 doubles).
+// mode 0: velocity set (sum |u|^2, max |u_d|, max |D u|, non-finite count)
+// mode 1: pressure residual (sum (L p - r)^2, -, -, non-finite count)
+cudaError_t launch_reduce(const Launch& L, int mode, const int* set, int p_arr, int r_arr,
+                          double* partials, int nparts, double* out);
+
+}  // namespace cfd

@@ -1,0 +1,747 @@
+// C ABI of the staggered-grid Navier-Stokes step: grid objects, device
+// layout, boundary tables, stage orchestration and CUDA-graph replay.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <string>
+#include <vector>
+
+#include "cfd_internal.h"
+#include "gb300cfd.h"
+
+using namespace cfd;
+
+namespace {
+
+thread_local std::string t_err = "no error";
+
+cfd_status fail(cfd_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof buf, fmt, ap);
+  va_end(ap);
+  t_err = buf;
+  return s;
+}
+
+size_t round_up(size_t x, size_t a) { return (x + a - 1) / a * a; }
+
+const int kSets[3][3] = {{A_U, A_V, A_W}, {A_WU, A_WV, A_WW}, {A_U1, A_V1, A_W1}};
+
+struct HostBlock {
+  int n[3];
+  int origin[3];
+  int py;
+  long long pz;
+  long long planes;
+  size_t array_bytes;
+  size_t first_byte;     // byte offset of this block's first array from base
+  int nbr[6];
+};
+
+}  // namespace
+
+struct cfd_grid {
+  int nblocks = 0, g = 1, dtype = CFD_F32, es = 4;
+  double h[3] = {1, 1, 1};
+  int gdims[3] = {0, 0, 0};
+  bool blockset = false;
+  std::vector<HostBlock> hb;
+  std::vector<int> hn;  // nblocks x 3 dims (for grid sizing)
+  int bc[6] = {0, 0, 0, 0, 0, 0};
+  double wall[6][3] = {};
+  double nu = 0.0, omega = 1.0;
+  int iters = 50, order = 2;
+
+  cudaStream_t user = nullptr, own = nullptr;
+  cudaEvent_t ev_in = nullptr, ev_out = nullptr;
+  int device = 0, sms = 1;
+
+  char* base = nullptr;
+  size_t bytes = 0;
+  bool owns = false;
+  size_t table_off = 0, prefix_off = 0, partial_off = 0, out_off = 0, flag_off = 0;
+  size_t arrays_off = 0;
+  int nparts = 0;
+  long long ghost_total = 0;
+  std::vector<long long> ghost_prefix;
+  std::vector<BlockDev> bdev;
+  double* h_out = nullptr;  // pinned, 4 doubles
+  int* h_flag = nullptr;    // pinned, 1 int
+
+  double t = 0.0;
+  long long step = 0;
+  bool sticky = false;
+
+  JacobiCfg jcfg{4, 8, 32};
+  StencilCfg scfg{8, 16};
+
+  cudaGraphExec_t gexec = nullptr;
+  bool graph_valid = false;
+  double graph_dt = 0.0;
+  long long graph_nodes = 0;   // kernel launches per replay
+  long long launches = 0;      // kernel launches enqueued (incl. replays)
+};
+
+namespace {
+
+cfd_status cuda_fail(cfd_grid* g, cudaError_t e, const char* what) {
+  if (g) g->sticky = true;
+  return fail(CFD_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+#define CK(g, call)                                           \
+  do {                                                        \
+    cudaError_t e_ = (call);                                  \
+    if (e_ != cudaSuccess) return cuda_fail((g), e_, #call);  \
+  } while (0)
+
+cfd_status usable(cfd_grid* g) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (g->sticky) return fail(CFD_ECUDA, "grid is in a failed state after an earlier CUDA error");
+  if (!g->base) return fail(CFD_ESTATE, "no device memory bound (cfd_bind_memory / cfd_alloc_memory)");
+  for (int d = 0; d < 3; ++d)
+    if ((g->bc[2 * d] == CFD_BC_PERIODIC) != (g->bc[2 * d + 1] == CFD_BC_PERIODIC))
+      return fail(CFD_EINVAL, "axis %d: periodic on one face but not the other", d);
+  if (g->order == 4 && g->g < 2) return fail(CFD_EINVAL, "order 4 needs ghost width 2");
+  return CFD_OK;
+}
+
+// Device layout: [tables][arrays of block 0][arrays of block 1]...
+void plan_layout(cfd_grid* g) {
+  const int align_e = kAlignBytes / g->es;
+  size_t off = 0;
+  g->table_off = off;
+  off = round_up(off + sizeof(BlockDev) * g->nblocks, 256);
+  g->prefix_off = off;
+  off = round_up(off + sizeof(long long) * (g->nblocks + 1), 256);
+  g->nparts = 4 * g->sms;
+  g->partial_off = off;
+  off = round_up(off + sizeof(double) * 4 * g->nparts, 256);
+  g->out_off = off;
+  off = round_up(off + sizeof(double) * 4, 256);
+  g->flag_off = off;
+  off = round_up(off + 256, 256);
+  g->arrays_off = off;
+  for (auto& b : g->hb) {
+    b.py = (int)round_up((size_t)align_e + b.n[0] + g->g, align_e);
+    b.pz = (long long)b.py * (b.n[1] + 2 * g->g);
+    b.planes = b.n[2] + 2 * g->g;
+    b.array_bytes = round_up((size_t)b.pz * b.planes * g->es, 256);
+    b.first_byte = off;
+    off += b.array_bytes * kNumArrays;
+  }
+  g->bytes = off;
+  // ghost-cell enumeration prefix (z-slabs, y-slabs, x-slabs per block)
+  g->ghost_prefix.assign(g->nblocks + 1, 0);
+  long long tot = 0;
+  for (int i = 0; i < g->nblocks; ++i) {
+    const int* n = g->hb[i].n;
+    const long long ex = n[0] + 2 * g->g, ey = n[1] + 2 * g->g;
+    g->ghost_prefix[i] = tot;
+    tot += 2LL * g->g * ey * ex + 2LL * g->g * n[2] * ex + 2LL * g->g * n[2] * n[1];
+  }
+  g->ghost_prefix[g->nblocks] = tot;
+  g->ghost_total = tot;
+}
+
+void build_tables(cfd_grid* g) {
+  const int align_e = kAlignBytes / g->es;
+  g->bdev.resize(g->nblocks);
+  for (int i = 0; i < g->nblocks; ++i) {
+    const HostBlock& b = g->hb[i];
+    BlockDev& d = g->bdev[i];
+    memset(&d, 0, sizeof d);
+    for (int a = 0; a < 3; ++a) d.n[a] = b.n[a];
+    d.py = b.py;
+    d.pz = b.pz;
+    for (int a = 0; a < kNumArrays; ++a) {
+      const size_t start = b.first_byte + b.array_bytes * a;
+      d.org[a] = (long long)(start / g->es) + (long long)g->g * b.pz + (long long)g->g * b.py + align_e;
+    }
+    for (int f = 0; f < 6; ++f) {
+      d.nbr[f] = b.nbr[f];
+      d.bc[f] = g->bc[f];
+      for (int c = 0; c < 3; ++c) d.wall[f][c] = (float)g->wall[f][c];
+    }
+  }
+}
+
+cfd_status upload_tables(cfd_grid* g) {
+  if (!g->base) return CFD_OK;
+  build_tables(g);
+  CK(g, cudaMemcpyAsync(g->base + g->table_off, g->bdev.data(), sizeof(BlockDev) * g->nblocks,
+                        cudaMemcpyHostToDevice, g->own));
+  CK(g, cudaMemcpyAsync(g->base + g->prefix_off, g->ghost_prefix.data(),
+                        sizeof(long long) * (g->nblocks + 1), cudaMemcpyHostToDevice, g->own));
+  CK(g, cudaMemsetAsync(g->base + g->flag_off, 0, 256, g->own));
+  CK(g, cudaStreamSynchronize(g->own));
+  return CFD_OK;
+}
+
+Launch make_launch(cfd_grid* g) {
+  Launch L;
+  L.blocks = reinterpret_cast<const BlockDev*>(g->base + g->table_off);
+  L.nblocks = g->nblocks;
+  L.base = g->base;
+  L.dtype = g->dtype;
+  L.ghost = g->g;
+  for (int d = 0; d < 3; ++d) {
+    L.ih[d] = (float)(1.0 / g->h[d]);
+    L.ih2[d] = (float)(1.0 / (g->h[d] * g->h[d]));
+  }
+  L.err_flag = reinterpret_cast<int*>(g->base + g->flag_off);
+  L.stream = g->own;
+  L.sms = g->sms;
+  L.hn = reinterpret_cast<const int(*)[3]>(g->hn.data());
+  return L;
+}
+
+cfd_status common_init(cfd_grid* g, int ghost, const double h[3], int storage, void* stream) {
+  if (ghost < 1 || ghost > kMaxGhost) return fail(CFD_EINVAL, "ghost width must be 1 or 2");
+  if (!h) return fail(CFD_EINVAL, "null h");
+  for (int d = 0; d < 3; ++d)
+    if (!(h[d] > 0.0) || !std::isfinite(h[d])) return fail(CFD_EINVAL, "cell size h[%d] must be > 0", d);
+  if (storage < CFD_F32 || storage > CFD_F16) return fail(CFD_EINVAL, "unknown storage dtype %d", storage);
+  g->g = ghost;
+  for (int d = 0; d < 3; ++d) g->h[d] = h[d];
+  g->dtype = storage;
+  g->es = storage == CFD_F32 ? 4 : 2;
+  g->user = reinterpret_cast<cudaStream_t>(stream);
+  cudaError_t e;
+  if ((e = cudaGetDevice(&g->device)) != cudaSuccess) return cuda_fail(nullptr, e, "cudaGetDevice");
+  if ((e = cudaDeviceGetAttribute(&g->sms, cudaDevAttrMultiProcessorCount, g->device)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaDeviceGetAttribute");
+  if ((e = cudaStreamCreateWithFlags(&g->own, cudaStreamNonBlocking)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaStreamCreate");
+  if ((e = cudaEventCreateWithFlags(&g->ev_in, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaEventCreate");
+  if ((e = cudaEventCreateWithFlags(&g->ev_out, cudaEventDisableTiming)) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaEventCreate");
+  if ((e = cudaMallocHost(&g->h_out, 8 * sizeof(double))) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaMallocHost");
+  g->h_flag = reinterpret_cast<int*>(g->h_out + 4);
+  g->hn.resize(3 * g->nblocks);
+  for (int b = 0; b < g->nblocks; ++b)
+    for (int d = 0; d < 3; ++d) g->hn[3 * b + d] = g->hb[b].n[d];
+  if (g->dtype == CFD_F32) g->jcfg = JacobiCfg{4, 8, 32};
+  else g->jcfg = JacobiCfg{4, 8, 32};
+  plan_layout(g);
+  return CFD_OK;
+}
+
+void destroy_handles(cfd_grid* g) {
+  if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->own) cudaStreamSynchronize(g->own);
+  if (g->owns && g->base) cudaFree(g->base);
+  if (g->h_out) cudaFreeHost(g->h_out);
+  if (g->ev_in) cudaEventDestroy(g->ev_in);
+  if (g->ev_out) cudaEventDestroy(g->ev_out);
+  if (g->own) cudaStreamDestroy(g->own);
+}
+
+// Order the private stream after the caller's stream, and back.
+cfd_status join_in(cfd_grid* g) {
+  CK(g, cudaEventRecord(g->ev_in, g->user));
+  CK(g, cudaStreamWaitEvent(g->own, g->ev_in, 0));
+  return CFD_OK;
+}
+cfd_status join_out(cfd_grid* g) {
+  CK(g, cudaEventRecord(g->ev_out, g->own));
+  CK(g, cudaStreamWaitEvent(g->user, g->ev_out, 0));
+  return CFD_OK;
+}
+
+// ------------------------------------------------------------- enqueuers
+
+cfd_status enq_ghost(cfd_grid* g, unsigned mask) {
+  int arrs[kNumArrays];
+  int n = 0;
+  for (int a = 0; a < kNumArrays; ++a)
+    if (mask & (1u << a)) arrs[n++] = a;
+  const Launch L = make_launch(g);
+  CK(g, launch_ghost(L, arrs, n, reinterpret_cast<const long long*>(g->base + g->prefix_off),
+                     g->ghost_total));
+  g->launches += (n + 3) / 4;
+  return CFD_OK;
+}
+
+unsigned set_mask(int s) {
+  return (1u << kSets[s][0]) | (1u << kSets[s][1]) | (1u << kSets[s][2]);
+}
+
+cfd_status enq_stage(cfd_grid* g, double a, int xs, double b, int ys, double c, int os) {
+  const Launch L = make_launch(g);
+  CK(g, launch_stage(L, g->scfg, g->order, (float)a, a != 0.0 ? kSets[xs] : nullptr, (float)b,
+                     kSets[ys], (float)c, kSets[os], (float)g->nu));
+  g->launches += 1;
+  return CFD_OK;
+}
+
+cfd_status enq_sweeps(cfd_grid* g, int iters) {
+  const Launch L = make_launch(g);
+  int cur = A_P, oth = A_P2;
+  for (int it = 0; it < iters; ++it) {
+    CK(g, launch_jacobi(L, g->jcfg, cur, oth, A_R, (float)g->omega));
+    std::swap(cur, oth);
+  }
+  g->launches += iters;
+  if (cur != A_P) {
+    CK(g, launch_copy(L, g->scfg, cur, A_P));
+    g->launches += 1;
+  }
+  return CFD_OK;
+}
+
+cfd_status enq_solve(cfd_grid* g, double c_dt, int iters) {
+  const Launch L = make_launch(g);
+  CK(g, launch_divergence(L, g->scfg, kSets[CFD_SET_W], (float)(1.0 / c_dt), A_R));
+  g->launches += 1;
+  return enq_sweeps(g, iters);
+}
+
+cfd_status enq_project(cfd_grid* g, double c_dt, int os) {
+  const Launch L = make_launch(g);
+  CK(g, launch_project(L, g->scfg, kSets[CFD_SET_W], A_P, (float)c_dt, kSets[os]));
+  g->launches += 1;
+  return enq_ghost(g, set_mask(os));
+}
+
+cfd_status enq_rk_stage(cfd_grid* g, int stage, double dt) {
+  cfd_status s;
+  if (stage == 1) {
+    if ((s = enq_ghost(g, set_mask(CFD_SET_U) | (1u << A_P))) != CFD_OK) return s;
+    if ((s = enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, dt, CFD_SET_W)) != CFD_OK) return s;
+    if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
+    if ((s = enq_solve(g, dt, g->iters)) != CFD_OK) return s;
+    return enq_project(g, dt, CFD_SET_U1);
+  }
+  if ((s = enq_stage(g, 0.5, CFD_SET_U, 0.5, CFD_SET_U1, 0.5 * dt, CFD_SET_W)) != CFD_OK) return s;
+  if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
+  if ((s = enq_solve(g, 0.5 * dt, g->iters)) != CFD_OK) return s;
+  return enq_project(g, 0.5 * dt, CFD_SET_U);
+}
+
+cfd_status run_reduce(cfd_grid* g, int mode, int set, double out[4]) {
+  const Launch L = make_launch(g);
+  double* partials = reinterpret_cast<double*>(g->base + g->partial_off);
+  double* dout = reinterpret_cast<double*>(g->base + g->out_off);
+  CK(g, launch_reduce(L, mode, mode == 0 ? kSets[set] : nullptr, A_P, A_R, partials, g->nparts, dout));
+  g->launches += 2;
+  CK(g, cudaMemcpyAsync(g->h_out, dout, 4 * sizeof(double), cudaMemcpyDeviceToHost, g->own));
+  CK(g, cudaStreamSynchronize(g->own));
+  for (int e = 0; e < 4; ++e) out[e] = g->h_out[e];
+  return CFD_OK;
+}
+
+void invalidate_graph(cfd_grid* g) { g->graph_valid = false; }
+
+}  // namespace
+
+// =================================================================== C ABI
+
+extern "C" {
+
+const char* cfd_last_error(void) { return t_err.c_str(); }
+
+cfd_status cfd_grid_create(const int dims[3], int ghost, const double h[3], int storage,
+                           void* stream, cfd_grid** out) {
+  if (!dims || !out) return fail(CFD_EINVAL, "null argument");
+  *out = nullptr;
+  for (int d = 0; d < 3; ++d)
+    if (dims[d] < 2 * ghost || dims[d] > (1 << 20))
+      return fail(CFD_EINVAL, "dims[%d] = %d must be >= 2*ghost", d, dims[d]);
+  cfd_grid* g = new cfd_grid();
+  g->nblocks = 1;
+  g->hb.resize(1);
+  for (int d = 0; d < 3; ++d) {
+    g->hb[0].n[d] = dims[d];
+    g->hb[0].origin[d] = 0;
+    g->gdims[d] = dims[d];
+  }
+  for (int f = 0; f < 6; ++f) g->hb[0].nbr[f] = 0;
+  cfd_status s = common_init(g, ghost, h, storage, stream);
+  if (s != CFD_OK) {
+    destroy_handles(g);
+    delete g;
+    return s;
+  }
+  *out = g;
+  return CFD_OK;
+}
+
+cfd_status cfd_blockset_create(int nblocks, const int* dims, const int* origin,
+                               const int global_dims[3], int ghost, const double h[3],
+                               int storage, void* stream, cfd_grid** out) {
+  if (!dims || !origin || !global_dims || !out) return fail(CFD_EINVAL, "null argument");
+  *out = nullptr;
+  if (nblocks < 1 || nblocks > kMaxBlocks) return fail(CFD_EINVAL, "nblocks must be 1..%d", kMaxBlocks);
+  // rectilinear tiling: per axis the distinct (origin, width) slabs partition [0, G)
+  std::vector<std::pair<int, int>> slabs[3];
+  for (int b = 0; b < nblocks; ++b)
+    for (int d = 0; d < 3; ++d) {
+      const int o = origin[3 * b + d], n = dims[3 * b + d];
+      if (n < 2 * ghost) return fail(CFD_EINVAL, "block %d: dims[%d] = %d < 2*ghost", b, d, n);
+      if (o < 0 || o + n > global_dims[d]) return fail(CFD_EINVAL, "block %d outside the domain", b);
+      slabs[d].push_back({o, n});
+    }
+  for (int d = 0; d < 3; ++d) {
+    std::sort(slabs[d].begin(), slabs[d].end());
+    slabs[d].erase(std::unique(slabs[d].begin(), slabs[d].end()), slabs[d].end());
+    int pos = 0;
+    for (auto& s : slabs[d]) {
+      if (s.first != pos) return fail(CFD_EINVAL, "axis %d: blocks do not form a rectilinear tiling", d);
+      pos += s.second;
+    }
+    if (pos != global_dims[d]) return fail(CFD_EINVAL, "axis %d: slabs do not cover the domain", d);
+  }
+  const size_t ns[3] = {slabs[0].size(), slabs[1].size(), slabs[2].size()};
+  if ((size_t)nblocks != ns[0] * ns[1] * ns[2])
+    return fail(CFD_EINVAL, "blocks must be one per slab combination (%zu x %zu x %zu)", ns[0], ns[1], ns[2]);
+  std::vector<int> at(nblocks, -1);
+  std::vector<int> sidx(3 * nblocks);
+  for (int b = 0; b < nblocks; ++b) {
+    size_t lin = 0;
+    for (int d = 2; d >= 0; --d) {
+      const std::pair<int, int> key{origin[3 * b + d], dims[3 * b + d]};
+      const size_t k = std::lower_bound(slabs[d].begin(), slabs[d].end(), key) - slabs[d].begin();
+      sidx[3 * b + d] = (int)k;
+      lin = lin * ns[d] + k;
+    }
+    if (at[lin] != -1) return fail(CFD_EINVAL, "blocks %d and %d coincide", at[lin], b);
+    at[lin] = b;
+  }
+  cfd_grid* g = new cfd_grid();
+  g->nblocks = nblocks;
+  g->blockset = true;
+  g->hb.resize(nblocks);
+  for (int d = 0; d < 3; ++d) g->gdims[d] = global_dims[d];
+  for (int b = 0; b < nblocks; ++b) {
+    for (int d = 0; d < 3; ++d) {
+      g->hb[b].n[d] = dims[3 * b + d];
+      g->hb[b].origin[d] = origin[3 * b + d];
+    }
+    for (int d = 0; d < 3; ++d)
+      for (int side = 0; side < 2; ++side) {
+        int s3[3] = {sidx[3 * b], sidx[3 * b + 1], sidx[3 * b + 2]};
+        s3[d] = (int)((s3[d] + (side ? 1 : (int)ns[d] - 1)) % ns[d]);
+        const size_t lin = ((size_t)s3[2] * ns[1] + s3[1]) * ns[0] + s3[0];
+        g->hb[b].nbr[2 * d + side] = at[lin];
+      }
+  }
+  cfd_status s = common_init(g, ghost, h, storage, stream);
+  if (s != CFD_OK) {
+    destroy_handles(g);
+    delete g;
+    return s;
+  }
+  *out = g;
+  return CFD_OK;
+}
+
+cfd_status cfd_grid_destroy(cfd_grid* g) {
+  if (!g) return CFD_OK;
+  destroy_handles(g);
+  delete g;
+  return CFD_OK;
+}
+
+cfd_status cfd_memory_bytes(const cfd_grid* g, size_t* bytes) {
+  if (!g || !bytes) return fail(CFD_EINVAL, "null argument");
+  *bytes = g->bytes;
+  return CFD_OK;
+}
+
+cfd_status cfd_bind_memory(cfd_grid* g, void* dev_ptr, size_t bytes) {
+  if (!g || !dev_ptr) return fail(CFD_EINVAL, "null argument");
+  if (reinterpret_cast<uintptr_t>(dev_ptr) % 256) return fail(CFD_EINVAL, "memory must be 256-byte aligned");
+  if (bytes < g->bytes) return fail(CFD_ENOMEM, "bound %zu bytes, need %zu", bytes, g->bytes);
+  if (g->owns && g->base) cudaFree(g->base);
+  g->owns = false;
+  g->base = static_cast<char*>(dev_ptr);
+  invalidate_graph(g);
+  return upload_tables(g);
+}
+
+cfd_status cfd_alloc_memory(cfd_grid* g) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  void* p = nullptr;
+  cudaError_t e = cudaMalloc(&p, g->bytes);
+  if (e != cudaSuccess) {
+    cudaGetLastError();
+    return fail(CFD_ENOMEM, "cudaMalloc(%zu): %s", g->bytes, cudaGetErrorString(e));
+  }
+  if (g->owns && g->base) cudaFree(g->base);
+  g->base = static_cast<char*>(p);
+  g->owns = true;
+  invalidate_graph(g);
+  return upload_tables(g);
+}
+
+cfd_status cfd_array_layout(const cfd_grid* g, int block, int array, long long* offset_bytes,
+                            long long shape[3], long long strides[3], int* elem_bytes) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (block < 0 || block >= g->nblocks) return fail(CFD_EINVAL, "block %d out of range", block);
+  if (array < 0 || array >= kNumArrays) return fail(CFD_EINVAL, "array %d out of range", array);
+  const HostBlock& b = g->hb[block];
+  const int align_e = kAlignBytes / g->es;
+  if (offset_bytes)
+    *offset_bytes = (long long)(b.first_byte + b.array_bytes * array) + (long long)(align_e - g->g) * g->es;
+  if (shape) {
+    shape[0] = b.n[2] + 2 * g->g;
+    shape[1] = b.n[1] + 2 * g->g;
+    shape[2] = b.n[0] + 2 * g->g;
+  }
+  if (strides) {
+    strides[0] = b.pz;
+    strides[1] = b.py;
+    strides[2] = 1;
+  }
+  if (elem_bytes) *elem_bytes = g->es;
+  return CFD_OK;
+}
+
+cfd_status cfd_block_info(const cfd_grid* g, int block, int dims[3], int origin[3], int* ghost) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (block < 0 || block >= g->nblocks) return fail(CFD_EINVAL, "block %d out of range", block);
+  for (int d = 0; d < 3; ++d) {
+    if (dims) dims[d] = g->hb[block].n[d];
+    if (origin) origin[d] = g->hb[block].origin[d];
+  }
+  if (ghost) *ghost = g->g;
+  return CFD_OK;
+}
+
+cfd_status cfd_set_bc(cfd_grid* g, int face, int kind, const double wall_velocity[3]) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (face < 0 || face > 5) return fail(CFD_EINVAL, "face %d out of range 0..5", face);
+  if (kind != CFD_BC_PERIODIC && kind != CFD_BC_WALL) return fail(CFD_EINVAL, "unknown bc kind %d", kind);
+  if (kind == CFD_BC_WALL && g->blockset)
+    return fail(CFD_EUNSUPPORTED, "walls are supported on single-block grids only");
+  double v[3] = {0, 0, 0};
+  if (wall_velocity)
+    for (int c = 0; c < 3; ++c) v[c] = wall_velocity[c];
+  if (kind == CFD_BC_WALL && v[face / 2] != 0.0)
+    return fail(CFD_EINVAL, "wall velocity must be tangential (component %d is normal)", face / 2);
+  g->bc[face] = kind;
+  for (int c = 0; c < 3; ++c) g->wall[face][c] = kind == CFD_BC_WALL ? v[c] : 0.0;
+  invalidate_graph(g);
+  return upload_tables(g);
+}
+
+cfd_status cfd_set_params(cfd_grid* g, double nu, int jacobi_iters, double omega, int order) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (!(nu >= 0.0) || !std::isfinite(nu)) return fail(CFD_EINVAL, "nu must be >= 0");
+  if (jacobi_iters < 0) return fail(CFD_EINVAL, "jacobi_iters must be >= 0");
+  if (!(omega > 0.0 && omega < 2.0)) return fail(CFD_EINVAL, "omega must be in (0, 2)");
+  if (order != 2 && order != 4) return fail(CFD_EINVAL, "order must be 2 or 4");
+  if (order == 4 && g->g < 2) return fail(CFD_EINVAL, "order 4 needs ghost width 2");
+  g->nu = nu;
+  g->iters = jacobi_iters;
+  g->omega = omega;
+  g->order = order;
+  invalidate_graph(g);
+  return CFD_OK;
+}
+
+cfd_status cfd_ghost_fill(cfd_grid* g, unsigned mask) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (mask >> kNumArrays) return fail(CFD_EINVAL, "mask has bits beyond the array ids");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_ghost(g, mask)) != CFD_OK) return s;
+  return join_out(g);
+}
+
+cfd_status cfd_stage(cfd_grid* g, double a, int x_set, double b, int y_set, double c, int out_set) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (y_set < 0 || y_set > 2 || out_set < 0 || out_set > 2 || (a != 0.0 && (x_set < 0 || x_set > 2)))
+    return fail(CFD_EINVAL, "velocity set ids are 0..2");
+  if (out_set == y_set || (a != 0.0 && out_set == x_set))
+    return fail(CFD_EINVAL, "output set must differ from the input sets");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_stage(g, a, x_set, b, y_set, c, out_set)) != CFD_OK) return s;
+  return join_out(g);
+}
+
+cfd_status cfd_rhs_eval(cfd_grid* g) { return cfd_stage(g, 0.0, 0, 0.0, CFD_SET_U, 1.0, CFD_SET_W); }
+
+cfd_status cfd_pressure_solve(cfd_grid* g, double c_dt, int iters, double* residual) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (!(c_dt > 0.0) || iters < 0) return fail(CFD_EINVAL, "need c_dt > 0 and iters >= 0");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_solve(g, c_dt, iters)) != CFD_OK) return s;
+  if (residual) {
+    double out[4];
+    if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
+    *residual = std::sqrt(out[0]);
+    if (out[3] != 0.0) return fail(CFD_ENONFINITE, "residual is not finite");
+  }
+  return join_out(g);
+}
+
+cfd_status cfd_jacobi(cfd_grid* g, int iters) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (iters < 0) return fail(CFD_EINVAL, "iters must be >= 0");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_sweeps(g, iters)) != CFD_OK) return s;
+  return join_out(g);
+}
+
+cfd_status cfd_stats(const cfd_grid* g, long long* kernel_launches) {
+  if (!g || !kernel_launches) return fail(CFD_EINVAL, "null argument");
+  *kernel_launches = g->launches;
+  return CFD_OK;
+}
+
+cfd_status cfd_project(cfd_grid* g, double c_dt, int out_set) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (out_set < 0 || out_set > 2 || out_set == CFD_SET_W) return fail(CFD_EINVAL, "output set must be U or U1");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_project(g, c_dt, out_set)) != CFD_OK) return s;
+  return join_out(g);
+}
+
+cfd_status cfd_rk_step(cfd_grid* g, int stage, double dt) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (stage != 1 && stage != 2) return fail(CFD_EINVAL, "stage must be 1 or 2");
+  if (!(dt > 0.0)) return fail(CFD_EINVAL, "dt must be > 0");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_rk_stage(g, stage, dt)) != CFD_OK) return s;
+  if (stage == 2) {
+    g->t += dt;
+    g->step += 1;
+  }
+  return join_out(g);
+}
+
+cfd_status cfd_step(cfd_grid* g, double dt, int n) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (!(dt > 0.0) || n < 0) return fail(CFD_EINVAL, "need dt > 0 and n >= 0");
+  if (n == 0) return CFD_OK;
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if (!g->graph_valid || g->graph_dt != dt) {
+    if (g->gexec) {
+      cudaGraphExecDestroy(g->gexec);
+      g->gexec = nullptr;
+    }
+    CK(g, cudaStreamBeginCapture(g->own, cudaStreamCaptureModeThreadLocal));
+    const long long before = g->launches;
+    cfd_status s1 = enq_rk_stage(g, 1, dt);
+    cfd_status s2 = s1 == CFD_OK ? enq_rk_stage(g, 2, dt) : s1;
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->own, &graph);
+    if (s2 != CFD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s2;
+    }
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g->gexec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
+    g->graph_valid = true;
+    g->graph_dt = dt;
+    g->graph_nodes = g->launches - before;
+    g->launches = before;
+  }
+  for (int i = 0; i < n; ++i) CK(g, cudaGraphLaunch(g->gexec, g->own));
+  g->launches += n * g->graph_nodes;
+  g->t += n * dt;
+  g->step += n;
+  return join_out(g);
+}
+
+cfd_status cfd_reduce(cfd_grid* g, int set, double* kinetic_energy, double* max_abs_u,
+                      double* max_abs_div) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (set < 0 || set > 2) return fail(CFD_EINVAL, "set must be 0..2");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  double out[4];
+  if ((s = run_reduce(g, 0, set, out)) != CFD_OK) return s;
+  if (kinetic_energy) *kinetic_energy = 0.5 * out[0] * g->h[0] * g->h[1] * g->h[2];
+  if (max_abs_u) *max_abs_u = out[1];
+  if (max_abs_div) *max_abs_div = out[2];
+  if ((s = join_out(g)) != CFD_OK) return s;
+  if (out[3] != 0.0) return fail(CFD_ENONFINITE, "%g non-finite velocity values", out[3]);
+  return CFD_OK;
+}
+
+cfd_status cfd_residual(cfd_grid* g, double* residual) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (!residual) return fail(CFD_EINVAL, "null argument");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  double out[4];
+  if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
+  *residual = std::sqrt(out[0]);
+  if ((s = join_out(g)) != CFD_OK) return s;
+  if (out[3] != 0.0) return fail(CFD_ENONFINITE, "residual is not finite");
+  return CFD_OK;
+}
+
+cfd_status cfd_get_state(const cfd_grid* g, double* t, long long* step) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (t) *t = g->t;
+  if (step) *step = g->step;
+  return CFD_OK;
+}
+
+cfd_status cfd_set_state(cfd_grid* g, double t, long long step) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  g->t = t;
+  g->step = step;
+  return CFD_OK;
+}
+
+cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int to_device) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (!host) return fail(CFD_EINVAL, "null host pointer");
+  if (block < 0 || block >= g->nblocks || array < 0 || array >= kNumArrays)
+    return fail(CFD_EINVAL, "block or array id out of range");
+  const HostBlock& b = g->hb[block];
+  const BlockDev tmp = [&] { build_tables(g); return g->bdev[block]; }();
+  char* dev = g->base + tmp.org[array] * g->es;
+  cudaMemcpy3DParms p = {};
+  cudaPitchedPtr dp = make_cudaPitchedPtr(dev, (size_t)b.py * g->es, (size_t)b.n[0] * g->es,
+                                          (size_t)(b.n[1] + 2 * g->g));
+  cudaPitchedPtr hp = make_cudaPitchedPtr(host, (size_t)b.n[0] * g->es, (size_t)b.n[0] * g->es,
+                                          (size_t)b.n[1]);
+  if (to_device) {
+    p.srcPtr = hp;
+    p.dstPtr = dp;
+  } else {
+    p.srcPtr = dp;
+    p.dstPtr = hp;
+  }
+  p.extent = make_cudaExtent((size_t)b.n[0] * g->es, (size_t)b.n[1], (size_t)b.n[2]);
+  p.kind = cudaMemcpyDefault;
+  if ((s = join_in(g)) != CFD_OK) return s;
+  CK(g, cudaMemcpy3DAsync(&p, g->own));
+  return join_out(g);
+}
+
+cfd_status cfd_check(cfd_grid* g) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (g->sticky) return fail(CFD_ECUDA, "grid is in a failed state after an earlier CUDA error");
+  if (!g->base) return CFD_OK;
+  CK(g, cudaMemcpyAsync(g->h_flag, g->base + g->flag_off, sizeof(int), cudaMemcpyDeviceToHost, g->own));
+  CK(g, cudaStreamSynchronize(g->own));
+  CK(g, cudaGetLastError());
+  if (*g->h_flag != 0) return fail(CFD_ETIMEOUT, "device error flag %d", *g->h_flag);
+  return CFD_OK;
+}
+
+}  // extern "C"

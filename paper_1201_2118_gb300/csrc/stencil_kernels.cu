@@ -1,0 +1,794 @@
+// Stencil kernels of the staggered-grid projection step (sm_103a).
+//
+// All kernels walk a flattened list of tiles over all blocks of the grid
+// (one persistent launch covers every block; tiles are numbered block by
+// block, x fastest, then y, then z chunks), read fields in their storage
+// type, compute in FP32 and store with round-to-nearest.  Fields are
+// addressed as base + org[array] + k*pz + j*py + i with i,j,k relative to the
+// interior origin, so ghost cells have negative or >= n indices.
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "cfd_internal.h"
+
+namespace cfd {
+namespace {
+
+// ------------------------------------------------------------ storage types
+
+template <typename T> __device__ __forceinline__ float ldf(const T* p);
+template <> __device__ __forceinline__ float ldf<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float ldf<__half>(const __half* p) {
+  return __half2float(__ldg(p));
+}
+
+template <typename T> __device__ __forceinline__ T cvt(float x);
+template <> __device__ __forceinline__ float cvt<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
+
+// VX consecutive elements as one aligned vector load / store.
+template <typename T, int VX> struct alignas(sizeof(T) * VX) Vec { T v[VX]; };
+
+__device__ __forceinline__ float tof(float x) { return x; }
+__device__ __forceinline__ float tof(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float tof(__half x) { return __half2float(x); }
+
+template <int VX, typename T>
+__device__ __forceinline__ void ldv(const T* p, float (&out)[VX]) {
+  const Vec<T, VX> x = *reinterpret_cast<const Vec<T, VX>*>(p);
+#pragma unroll
+  for (int e = 0; e < VX; ++e) out[e] = tof(x.v[e]);
+}
+
+template <typename T, int VX>
+__device__ __forceinline__ void stv(T* p, const float (&in)[VX]) {
+  Vec<T, VX> x;
+#pragma unroll
+  for (int e = 0; e < VX; ++e) x.v[e] = cvt<T>(in[e]);
+  *reinterpret_cast<Vec<T, VX>*>(p) = x;
+}
+
+__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+// Tile t -> (block b, tile origin).  b/base form a cursor that only moves
+// forward, since every CTA visits increasing t.
+__device__ __forceinline__ bool locate(const Launch& L, long long t, int tx, int ty, int tz,
+                                       int& b, long long& base, int& i0, int& j0, int& k0) {
+  while (b < L.nblocks) {
+    const int nx = L.blocks[b].n[0], ny = L.blocks[b].n[1], nz = L.blocks[b].n[2];
+    const long long nxT = cdiv(nx, tx), nyT = cdiv(ny, ty), nzT = cdiv(nz, tz);
+    const long long cnt = nxT * nyT * nzT;
+    if (t < base + cnt) {
+      long long l = t - base;
+      i0 = (int)(l % nxT) * tx;
+      l /= nxT;
+      j0 = (int)(l % nyT) * ty;
+      k0 = (int)(l / nyT) * tz;
+      return true;
+    }
+    base += cnt;
+    ++b;
+  }
+  return false;
+}
+
+template <typename T>
+struct Fld {
+  const T* p;
+  int py;
+  long long pz;
+  __device__ __forceinline__ float operator()(int i, int j, int k) const {
+    return ldf<T>(p + (long long)k * pz + (long long)j * py + i);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ Fld<T> fld(const Launch& L, const BlockDev& B, int arr) {
+  return Fld<T>{reinterpret_cast<const T*>(L.base) + B.org[arr], B.py, B.pz};
+}
+
+template <typename T>
+__device__ __forceinline__ T* wptr(const Launch& L, const BlockDev& B, int arr) {
+  return reinterpret_cast<T*>(L.base) + B.org[arr];
+}
+
+// ------------------------------------------------------------------ ghosts
+//
+// One thread per ghost cell.  Ghost cells of a block are enumerated without
+// overlap: z-slabs (k outside, all i, j), y-slabs (k inside, j outside, all
+// i), x-slabs (j, k inside, i outside).  The value is that of the sequential
+// x, y, z passes: the source cell is found axis by axis (neighbour block or
+// mirror image) and the wall rules compose as affine maps v -> A + S v.
+
+struct GhostArrays { int arr[4]; int n; };
+
+template <typename T>
+__global__ void __launch_bounds__(256) k_ghost(Launch L, GhostArrays ga, const long long* prefix,
+                                               long long total) {
+  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= total) return;
+  const int arr = ga.arr[blockIdx.y];
+  const int kind = array_kind(arr);
+  const int g = L.ghost;
+  // block of this ghost cell (binary search over the prefix sums)
+  int lo = 0, hi = L.nblocks - 1;
+  while (lo < hi) {
+    const int mid = (lo + hi + 1) >> 1;
+    if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
+  }
+  const int b = lo;
+  const BlockDev& B = L.blocks[b];
+  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const long long ex = nx + 2 * g, ey = ny + 2 * g;
+  long long l = t - prefix[b];
+  int q[3];
+  const long long zc = 2LL * g * ey * ex, yc = 2LL * g * nz * ex;
+  if (l < zc) {
+    const int s = (int)(l / (ey * ex));
+    const long long rem = l % (ey * ex);
+    q[2] = s < g ? s - g : nz + s - g;
+    q[1] = (int)(rem / ex) - g;
+    q[0] = (int)(rem % ex) - g;
+  } else if ((l -= zc) < yc) {
+    const int s = (int)(l / (nz * ex));
+    const long long rem = l % (nz * ex);
+    q[1] = s < g ? s - g : ny + s - g;
+    q[2] = (int)(rem / ex);
+    q[0] = (int)(rem % ex) - g;
+  } else {
+    l -= yc;
+    const int s = (int)(l / ((long long)nz * ny));
+    const long long rem = l % ((long long)nz * ny);
+    q[0] = s < g ? s - g : nx + s - g;
+    q[2] = (int)(rem / ny);
+    q[1] = (int)(rem % ny);
+  }
+  const int dst[3] = {q[0], q[1], q[2]};
+  int sb = b;
+  float A = 0.f, S = 1.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const BlockDev& C = L.blocks[sb];
+    const int N = C.n[d];
+    int face;
+    if (q[d] < 0) face = 2 * d; else if (q[d] >= N) face = 2 * d + 1; else continue;
+    const bool low = (face == 2 * d);
+    if (C.bc[face] == BC_PERIODIC) {
+      const int nb = C.nbr[face];
+      q[d] = low ? q[d] + L.blocks[nb].n[d] : q[d] - N;
+      sb = nb;
+    } else {
+      q[d] = low ? -1 - q[d] : 2 * N - 1 - q[d];
+      float a, s;
+      if (kind == 3) { a = 0.f; s = 1.f; }
+      else if (kind == d) { a = 0.f; s = 0.f; }
+      else { a = 2.f * C.wall[face][kind]; s = -1.f; }
+      A = a + s * A;
+      S = s * S;
+    }
+  }
+  float v = A;
+  if (S != 0.f) v += S * fld<T>(L, L.blocks[sb], arr)(q[0], q[1], q[2]);
+  T* out = wptr<T>(L, B, arr);
+  out[(long long)dst[2] * B.pz + (long long)dst[1] * B.py + dst[0]] = cvt<T>(v);
+}
+
+// ------------------------------------------------------- RHS + stage combine
+
+template <typename T, int ORDER, int C>
+__device__ __forceinline__ float rhs_comp(const Fld<T> (&f)[3], int i, int j, int k,
+                                          const float (&ih)[3], const float (&ih2)[3],
+                                          float nu) {
+  auto at = [&](int comp, int d1, int o1, int d2, int o2) -> float {
+    int q[3] = {i, j, k};
+    q[d1] += o1;
+    q[d2] += o2;
+    return f[comp](q[0], q[1], q[2]);
+  };
+  const float f0 = f[C](i, j, k);
+  float adv = 0.f, lap = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float p1 = at(C, d, 1, d, 0), m1 = at(C, d, -1, d, 0);
+    float deriv, second;
+    if (ORDER == 2) {
+      deriv = (p1 - m1) * (0.5f * ih[d]);
+      second = (p1 - 2.f * f0 + m1) * ih2[d];
+    } else {
+      const float p2 = at(C, d, 2, d, 0), m2 = at(C, d, -2, d, 0);
+      deriv = (8.f * (p1 - m1) - (p2 - m2)) * (ih[d] * (1.f / 12.f));
+      second = (16.f * (p1 + m1) - 30.f * f0 - (p2 + m2)) * (ih2[d] * (1.f / 12.f));
+    }
+    float vel;
+    if (d == C) {
+      vel = f0;
+    } else if (ORDER == 2) {
+      vel = 0.25f * ((at(d, C, 0, d, -1) + at(d, C, 1, d, -1)) + (at(d, C, 0, d, 0) + at(d, C, 1, d, 0)));
+    } else {
+      const float w4[4] = {-1.f / 16.f, 9.f / 16.f, 9.f / 16.f, -1.f / 16.f};
+      vel = 0.f;
+#pragma unroll
+      for (int ad = 0; ad < 4; ++ad) {
+        float s = 0.f;
+#pragma unroll
+        for (int ac = 0; ac < 4; ++ac) s += w4[ac] * at(d, C, ac - 1, d, ad - 2);
+        vel += w4[ad] * s;
+      }
+    }
+    adv += vel * deriv;
+    lap += second;
+  }
+  return nu * lap - adv;
+}
+
+struct Set3 { int a[3]; };
+
+template <typename T, int ORDER, int TY>
+__global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Set3 xs, float b,
+                                                   Set3 ys, float cdt, Set3 os, float nu) {
+  const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
+  const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
+  int blk = 0;
+  long long base = 0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (i >= B.n[0] || j >= B.n[1]) continue;
+    const Fld<T> y[3] = {fld<T>(L, B, ys.a[0]), fld<T>(L, B, ys.a[1]), fld<T>(L, B, ys.a[2])};
+    const int k1 = min(k0 + zc, B.n[2]);
+    const bool wall[3] = {B.bc[1] == BC_WALL && i == B.n[0] - 1,
+                          B.bc[3] == BC_WALL && j == B.n[1] - 1, B.bc[5] == BC_WALL};
+    for (int k = k0; k < k1; ++k) {
+      float F[3];
+      F[0] = rhs_comp<T, ORDER, 0>(y, i, j, k, ih, ih2, nu);
+      F[1] = rhs_comp<T, ORDER, 1>(y, i, j, k, ih, ih2, nu);
+      F[2] = rhs_comp<T, ORDER, 2>(y, i, j, k, ih, ih2, nu);
+      const long long o = (long long)k * B.pz + (long long)j * B.py + i;
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const bool wf = wall[c] && (c != 2 || k == B.n[2] - 1);
+        float v = b * y[c](i, j, k) + cdt * F[c];
+        if (a != 0.f) v += a * fld<T>(L, B, xs.a[c])(i, j, k);
+        wptr<T>(L, B, os.a[c])[o] = cvt<T>(wf ? 0.f : v);
+      }
+    }
+  }
+}
+
+// --------------------------------------------------------------- divergence
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, float inv_cdt,
+                                                 int r_arr) {
+  int blk = 0;
+  long long base = 0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (i >= B.n[0] || j >= B.n[1]) continue;
+    const Fld<T> u = fld<T>(L, B, ws.a[0]), v = fld<T>(L, B, ws.a[1]), w = fld<T>(L, B, ws.a[2]);
+    T* r = wptr<T>(L, B, r_arr);
+    const int k1 = min(k0 + zc, B.n[2]);
+    for (int k = k0; k < k1; ++k) {
+      const float d = (u(i, j, k) - u(i - 1, j, k)) * L.ih[0] +
+                      (v(i, j, k) - v(i, j - 1, k)) * L.ih[1] +
+                      (w(i, j, k) - w(i, j, k - 1)) * L.ih[2];
+      r[(long long)k * B.pz + (long long)j * B.py + i] = cvt<T>(d * inv_cdt);
+    }
+  }
+}
+
+// --------------------------------------------------------------- projection
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY) k_project(Launch L, int zc, Set3 ws, int p_arr,
+                                                     float cdt, Set3 os) {
+  int blk = 0;
+  long long base = 0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (i >= B.n[0] || j >= B.n[1]) continue;
+    const Fld<T> p = fld<T>(L, B, p_arr);
+    const int k1 = min(k0 + zc, B.n[2]);
+    const bool wx = B.bc[1] == BC_WALL && i == B.n[0] - 1;
+    const bool wy = B.bc[3] == BC_WALL && j == B.n[1] - 1;
+    for (int k = k0; k < k1; ++k) {
+      const long long o = (long long)k * B.pz + (long long)j * B.py + i;
+      const float pc = p(i, j, k);
+      const float g[3] = {(p(i + 1, j, k) - pc) * L.ih[0], (p(i, j + 1, k) - pc) * L.ih[1],
+                          (p(i, j, k + 1) - pc) * L.ih[2]};
+      const bool wf[3] = {wx, wy, B.bc[5] == BC_WALL && k == B.n[2] - 1};
+#pragma unroll
+      for (int c = 0; c < 3; ++c) {
+        const float v = fld<T>(L, B, ws.a[c])(i, j, k) - cdt * g[c];
+        wptr<T>(L, B, os.a[c])[o] = cvt<T>(wf[c] ? 0.f : v);
+      }
+    }
+  }
+}
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY) k_copy(Launch L, int zc, int src, int dst) {
+  int blk = 0;
+  long long base = 0;
+  const int g = L.ghost;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    // copies the full ghosted extent: tiles cover the interior, edge tiles
+    // also take the ghost layers next to them
+    const T* s = reinterpret_cast<const T*>(L.base) + B.org[src];
+    T* d = wptr<T>(L, B, dst);
+    const int k1 = min(k0 + zc, B.n[2]);
+    const int ilo = (i0 == 0) ? -g : i0, jlo = (j0 == 0) ? -g : j0;
+    const int ihi = min(i0 + 32, B.n[0]) + (i0 + 32 >= B.n[0] ? g : 0);
+    const int jhi = min(j0 + TY, B.n[1]) + (j0 + TY >= B.n[1] ? g : 0);
+    const int klo = (k0 == 0) ? -g : k0, khi = k1 + (k1 == B.n[2] ? g : 0);
+    for (int k = klo; k < khi; ++k)
+      for (int jj = jlo + threadIdx.y; jj < jhi; jj += TY)
+        for (int ii = ilo + threadIdx.x; ii < ihi; ii += 32) {
+          const long long o = (long long)k * B.pz + (long long)jj * B.py + ii;
+          d[o] = s[o];
+        }
+  }
+}
+
+// ------------------------------------------------------------------- Jacobi
+//
+// One weighted Jacobi sweep of the 7-point operator, p' = p + w((N p - r)/diag - p),
+// N p = sum_d (p_{+d} + p_{-d}) / h_d^2.  A CTA of 32 x TY threads owns a
+// (32 VX) x TY column of one block and streams it along z: the z-neighbours
+// stay in registers (planes k-1, k, k+1), the x-neighbours come from the
+// neighbouring lane by warp shuffle (one halo load per row end), the
+// y-neighbours from a shared-memory copy of plane k (two halo rows).  The
+// loads of plane k+1 are issued before plane k is computed.
+//
+// Ghost-on-write: the 7-point operators read only the first ghost layer of
+// p at faces, so a thread that writes a face cell also writes its image into
+// that layer (the neighbouring block's ghost for a periodic/neighbour face,
+// the mirror ghost for a zero-gradient wall).  Each such ghost cell has one
+// owner, so there is no separate halo launch per sweep.
+
+template <typename T>
+__device__ __forceinline__ void p_ghost_images(const Launch& L, const BlockDev& B, int dst,
+                                               int i, int j, int k, T val) {
+  const int q[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int face = 2 * d + side;
+      if (q[d] != (side == 0 ? 0 : B.n[d] - 1)) continue;
+      int t[3] = {q[0], q[1], q[2]};
+      const BlockDev* D = &B;
+      if (B.bc[face] == BC_PERIODIC) {
+        D = &L.blocks[B.nbr[face]];
+        t[d] = side == 0 ? D->n[d] : -1;
+      } else {
+        t[d] = side == 0 ? -1 : B.n[d];
+      }
+      wptr<T>(L, *D, dst)[(long long)t[2] * D->pz + (long long)t[1] * D->py + t[0]] = val;
+    }
+  }
+}
+
+template <typename T, int VX, int TY>
+__global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, int dst,
+                                                    int r_arr, float omega, float inv_diag) {
+  constexpr int TX = 32 * VX;
+  __shared__ __align__(16) float sm[TY + 2][TX];
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  int blk = 0;
+  long long base = 0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, TX, TY, zc, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int py = B.py;
+    const long long pz = B.pz;
+    const T* P = reinterpret_cast<const T*>(L.base) + B.org[src];
+    const T* R = reinterpret_cast<const T*>(L.base) + B.org[r_arr];
+    T* Q = wptr<T>(L, B, dst);
+    const int i = i0 + lane * VX;
+    const int j = j0 + ty;
+    const int k1 = min(k0 + zc, nz);
+    // loads stay inside allocated rows: columns up to nx (first ghost) and
+    // rows up to ny (first ghost) are what the interior outputs need
+    const bool ld_col = i <= nx;
+    const bool ld_row = j <= ny;
+    const bool ld = ld_col && ld_row;
+    const bool halo_lo = (ty == 0);                 // row j0 - 1 (>= -1, valid)
+    const bool halo_hi = (ty == TY - 1) && ld_col && (j0 + TY <= ny);
+    const bool xl_ld = (lane == 0) && ld_row;      // column i0 - 1 (>= -1, valid)
+    const bool xr_ld = (lane == 31) && ld_row && (i0 + TX <= nx);
+    const long long row = (long long)j * py + i;
+    const long long row_lo = (long long)(j0 - 1) * py + i;
+    const long long row_hi = (long long)(j0 + TY) * py + i;
+    const long long xl_off = (long long)j * py + (i0 - 1);
+    const long long xr_off = (long long)j * py + (i0 + TX);
+
+    float m[VX], c[VX], q[VX], rr[VX], hl[VX], hh[VX];
+    float xl = 0.f, xr = 0.f;
+#pragma unroll
+    for (int e = 0; e < VX; ++e) m[e] = c[e] = q[e] = rr[e] = hl[e] = hh[e] = 0.f;
+    if (ld) {
+      ldv<VX>(P + (long long)(k0 - 1) * pz + row, m);
+      ldv<VX>(P + (long long)k0 * pz + row, c);
+      ldv<VX>(P + (long long)(k0 + 1) * pz + row, q);
+      ldv<VX>(R + (long long)k0 * pz + row, rr);
+    }
+    if (halo_lo && ld_col) ldv<VX>(P + (long long)k0 * pz + row_lo, hl);
+    if (halo_hi) ldv<VX>(P + (long long)k0 * pz + row_hi, hh);
+    if (xl_ld) xl = ldf<T>(P + (long long)k0 * pz + xl_off);
+    if (xr_ld) xr = ldf<T>(P + (long long)k0 * pz + xr_off);
+
+    for (int k = k0; k < k1; ++k) {
+      // issue the loads of plane k+1 (used next iteration)
+      const bool more = (k + 1 < k1);
+      float qn[VX], rn[VX], hln[VX], hhn[VX];
+      float xln = 0.f, xrn = 0.f;
+#pragma unroll
+      for (int e = 0; e < VX; ++e) qn[e] = rn[e] = hln[e] = hhn[e] = 0.f;
+      if (more) {
+        const long long pk = (long long)(k + 1) * pz;
+        if (ld) {
+          ldv<VX>(P + pk + pz + row, qn);
+          ldv<VX>(R + pk + row, rn);
+        }
+        if (halo_lo && ld_col) ldv<VX>(P + pk + row_lo, hln);
+        if (halo_hi) ldv<VX>(P + pk + row_hi, hhn);
+        if (xl_ld) xln = ldf<T>(P + pk + xl_off);
+        if (xr_ld) xrn = ldf<T>(P + pk + xr_off);
+      }
+      // plane k into shared memory (interior rows + two halo rows)
+      if constexpr (VX == 4) {
+        *reinterpret_cast<float4*>(&sm[ty + 1][lane * 4]) = make_float4(c[0], c[1], c[2], c[3]);
+        if (halo_lo) *reinterpret_cast<float4*>(&sm[0][lane * 4]) = make_float4(hl[0], hl[1], hl[2], hl[3]);
+        if (ty == TY - 1) *reinterpret_cast<float4*>(&sm[TY + 1][lane * 4]) = make_float4(hh[0], hh[1], hh[2], hh[3]);
+      } else if constexpr (VX == 2) {
+        *reinterpret_cast<float2*>(&sm[ty + 1][lane * 2]) = make_float2(c[0], c[1]);
+        if (halo_lo) *reinterpret_cast<float2*>(&sm[0][lane * 2]) = make_float2(hl[0], hl[1]);
+        if (ty == TY - 1) *reinterpret_cast<float2*>(&sm[TY + 1][lane * 2]) = make_float2(hh[0], hh[1]);
+      } else {
+#pragma unroll
+        for (int e = 0; e < VX; ++e) {
+          sm[ty + 1][lane * VX + e] = c[e];
+          if (halo_lo) sm[0][lane * VX + e] = hl[e];
+          if (ty == TY - 1) sm[TY + 1][lane * VX + e] = hh[e];
+        }
+      }
+      float left = __shfl_up_sync(0xffffffffu, c[VX - 1], 1);
+      float right = __shfl_down_sync(0xffffffffu, c[0], 1);
+      if (lane == 0) left = xl;
+      if (lane == 31) right = xr;
+      __syncthreads();
+      float dn[VX], up[VX];
+      if constexpr (VX == 4) {
+        const float4 a4 = *reinterpret_cast<const float4*>(&sm[ty][lane * 4]);
+        const float4 b4 = *reinterpret_cast<const float4*>(&sm[ty + 2][lane * 4]);
+        dn[0] = a4.x; dn[1] = a4.y; dn[2] = a4.z; dn[3] = a4.w;
+        up[0] = b4.x; up[1] = b4.y; up[2] = b4.z; up[3] = b4.w;
+      } else if constexpr (VX == 2) {
+        const float2 a2 = *reinterpret_cast<const float2*>(&sm[ty][lane * 2]);
+        const float2 b2 = *reinterpret_cast<const float2*>(&sm[ty + 2][lane * 2]);
+        dn[0] = a2.x; dn[1] = a2.y;
+        up[0] = b2.x; up[1] = b2.y;
+      } else {
+#pragma unroll
+        for (int e = 0; e < VX; ++e) { dn[e] = sm[ty][lane * VX + e]; up[e] = sm[ty + 2][lane * VX + e]; }
+      }
+      float out[VX];
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        const float xm = e == 0 ? left : c[e - 1];
+        const float xp = e == VX - 1 ? right : c[e + 1];
+        const float nb = (xm + xp) * cx + (dn[e] + up[e]) * cy + (m[e] + q[e]) * cz;
+        out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+      }
+      if (j < ny) {
+        T* qrow = Q + (long long)k * pz + row;
+        if (i + VX <= nx) {
+          stv<T, VX>(qrow, out);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VX; ++e)
+            if (i + e < nx) qrow[e] = cvt<T>(out[e]);
+        }
+        const bool face_k = (k == 0) || (k == nz - 1);
+        const bool face_j = (j == 0) || (j == ny - 1);
+#pragma unroll
+        for (int e = 0; e < VX; ++e) {
+          const int x = i + e;
+          if (x < nx && (face_k || face_j || x == 0 || x == nx - 1))
+            p_ghost_images<T>(L, B, dst, x, j, k, cvt<T>(out[e]));
+        }
+      }
+      __syncthreads();
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        m[e] = c[e];
+        c[e] = q[e];
+        q[e] = qn[e];
+        rr[e] = rn[e];
+        hl[e] = hln[e];
+        hh[e] = hhn[e];
+      }
+      xl = xln;
+      xr = xrn;
+    }
+  }
+}
+
+// --------------------------------------------------------------- reductions
+
+__device__ __forceinline__ double warp_sum(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  return v;
+}
+__device__ __forceinline__ double warp_max(double v) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v = fmax(v, __shfl_down_sync(0xffffffffu, v, o));
+  return v;
+}
+
+// Block-wide reduction of 4 values (sum, max, max, sum) in a fixed tree.
+template <int NT>
+__device__ __forceinline__ void block_reduce4(double (&v)[4], double (*sh)[4]) {
+  const int tid = threadIdx.x + threadIdx.y * blockDim.x;
+  const int w = tid >> 5, ln = tid & 31;
+  v[0] = warp_sum(v[0]);
+  v[1] = warp_max(v[1]);
+  v[2] = warp_max(v[2]);
+  v[3] = warp_sum(v[3]);
+  if (ln == 0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) sh[w][e] = v[e];
+  }
+  __syncthreads();
+  if (w == 0) {
+    constexpr int NW = NT / 32;
+    double a[4] = {0.0, 0.0, 0.0, 0.0};
+    if (ln < NW) {
+#pragma unroll
+      for (int e = 0; e < 4; ++e) a[e] = sh[ln][e];
+    }
+    a[0] = warp_sum(a[0]);
+    a[1] = warp_max(a[1]);
+    a[2] = warp_max(a[2]);
+    a[3] = warp_sum(a[3]);
+#pragma unroll
+    for (int e = 0; e < 4; ++e) v[e] = a[e];
+  }
+}
+
+__device__ __forceinline__ bool finite_f(float x) { return isfinite(x); }
+
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, Set3 set,
+                                                    int p_arr, int r_arr, double* partials) {
+  __shared__ double sh[TY][4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  int blk = 0;
+  long long base = 0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
+    if (i >= B.n[0] || j >= B.n[1]) continue;
+    const int k1 = min(k0 + zc, B.n[2]);
+    if (mode == 0) {
+      const Fld<T> f[3] = {fld<T>(L, B, set.a[0]), fld<T>(L, B, set.a[1]), fld<T>(L, B, set.a[2])};
+      for (int k = k0; k < k1; ++k) {
+        const float x[3] = {f[0](i, j, k), f[1](i, j, k), f[2](i, j, k)};
+        const float xm[3] = {f[0](i - 1, j, k), f[1](i, j - 1, k), f[2](i, j, k - 1)};
+        double div = 0.0;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const double xd = x[c];
+          acc[0] += xd * xd;
+          acc[1] = fmax(acc[1], fabs(xd));
+          div += (xd - (double)xm[c]) * (double)L.ih[c];
+          if (!finite_f(x[c])) acc[3] += 1.0;
+        }
+        acc[2] = fmax(acc[2], fabs(div));
+      }
+    } else {
+      const Fld<T> p = fld<T>(L, B, p_arr), r = fld<T>(L, B, r_arr);
+      for (int k = k0; k < k1; ++k) {
+        const double pc = p(i, j, k);
+        const double lp = ((double)p(i + 1, j, k) - 2.0 * pc + (double)p(i - 1, j, k)) * (double)L.ih2[0] +
+                          ((double)p(i, j + 1, k) - 2.0 * pc + (double)p(i, j - 1, k)) * (double)L.ih2[1] +
+                          ((double)p(i, j, k + 1) - 2.0 * pc + (double)p(i, j, k - 1)) * (double)L.ih2[2];
+        const float rv = r(i, j, k);
+        const double e = lp - (double)rv;
+        acc[0] += e * e;
+        if (!isfinite(e)) acc[3] += 1.0;
+      }
+    }
+  }
+  block_reduce4<32 * TY>(acc, sh);
+  if (threadIdx.x == 0 && threadIdx.y == 0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) partials[4 * blockIdx.x + e] = acc[e];
+  }
+}
+
+__global__ void __launch_bounds__(256) k_reduce_final(const double* partials, int nparts,
+                                                      double* out) {
+  __shared__ double sh[8][4];
+  double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  for (int p = threadIdx.x; p < nparts; p += 256) {
+    acc[0] += partials[4 * p];
+    acc[1] = fmax(acc[1], partials[4 * p + 1]);
+    acc[2] = fmax(acc[2], partials[4 * p + 2]);
+    acc[3] += partials[4 * p + 3];
+  }
+  block_reduce4<256>(acc, sh);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int e = 0; e < 4; ++e) out[e] = acc[e];
+  }
+}
+
+// ------------------------------------------------------------------ helpers
+
+template <typename K>
+int occupancy(K kernel, int threads) {
+  int n = 0;
+  if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kernel, threads, 0) != cudaSuccess) n = 1;
+  return n > 0 ? n : 1;
+}
+
+template <typename K>
+unsigned grid_for(const Launch& L, K kernel, int threads, long long tiles) {
+  const long long cap = (long long)L.sms * occupancy(kernel, threads);
+  long long gsz = tiles < cap ? tiles : cap;
+  return (unsigned)(gsz > 0 ? gsz : 1);
+}
+
+Set3 mk3(const int* s) { return Set3{{s[0], s[1], s[2]}}; }
+
+}  // namespace
+
+long long count_tiles(const Launch& L, int tx, int ty, int tz) {
+  long long n = 0;
+  for (int b = 0; b < L.nblocks; ++b) {
+    const int* d = L.hn[b];
+    n += (long long)((d[0] + tx - 1) / tx) * ((d[1] + ty - 1) / ty) * ((d[2] + tz - 1) / tz);
+  }
+  return n;
+}
+
+#define CFD_DISPATCH_T(dtype, ...)                         \
+  switch (dtype) {                                         \
+    case 0: { using T = float; __VA_ARGS__; } break;       \
+    case 1: { using T = __nv_bfloat16; __VA_ARGS__; } break; \
+    default: { using T = __half; __VA_ARGS__; } break;     \
+  }
+
+cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr, const long long* d_prefix,
+                         long long total) {
+  if (total == 0 || narr == 0) return cudaSuccess;
+  for (int s = 0; s < narr; s += 4) {
+    GhostArrays ga{};
+    ga.n = narr - s < 4 ? narr - s : 4;
+    for (int e = 0; e < ga.n; ++e) ga.arr[e] = arrays[s + e];
+    dim3 grid((unsigned)((total + 255) / 256), (unsigned)ga.n);
+    CFD_DISPATCH_T(L.dtype, k_ghost<T><<<grid, 256, 0, L.stream>>>(L, ga, d_prefix, total));
+  }
+  return cudaGetLastError();
+}
+
+template <typename T, int ORDER, int TY>
+static void run_stage(const Launch& L, int zc, float a, Set3 xs, float b, Set3 ys, float cdt,
+                      Set3 os, float nu) {
+  const long long tiles = count_tiles(L, 32, TY, zc);
+  auto kern = k_stage<T, ORDER, TY>;
+  kern<<<grid_for(L, kern, 32 * TY, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
+}
+
+cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float a,
+                         const int* xset, float b, const int* yset, float cdt, const int* oset,
+                         float nu) {
+  const Set3 xs = xset ? mk3(xset) : Set3{{0, 0, 0}};
+  CFD_DISPATCH_T(L.dtype, {
+    if (order == 4) {
+      if (c.ty == 4) run_stage<T, 4, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+      else run_stage<T, 4, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+    } else {
+      if (c.ty == 4) run_stage<T, 2, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+      else run_stage<T, 2, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+    }
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* wset,
+                              float inv_cdt, int r_arr) {
+  const long long tiles = count_tiles(L, 32, 8, c.zc);
+  CFD_DISPATCH_T(L.dtype, {
+    auto kern = k_div<T, 8>;
+    kern<<<grid_for(L, kern, 256, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, mk3(wset), inv_cdt, r_arr);
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset, int p_arr,
+                           float cdt, const int* oset) {
+  const long long tiles = count_tiles(L, 32, 8, c.zc);
+  CFD_DISPATCH_T(L.dtype, {
+    auto kern = k_project<T, 8>;
+    kern<<<grid_for(L, kern, 256, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, mk3(wset), p_arr, cdt, mk3(oset));
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_copy(const Launch& L, const StencilCfg& c, int src, int dst) {
+  const long long tiles = count_tiles(L, 32, 8, c.zc);
+  CFD_DISPATCH_T(L.dtype, {
+    auto kern = k_copy<T, 8>;
+    kern<<<grid_for(L, kern, 256, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, src, dst);
+  });
+  return cudaGetLastError();
+}
+
+template <typename T, int VX, int TY>
+static void run_jacobi(const Launch& L, int zc, int src, int dst, int r_arr, float omega,
+                       float inv_diag) {
+  const long long tiles = count_tiles(L, 32 * VX, TY, zc);
+  auto kern = k_jacobi<T, VX, TY>;
+  kern<<<grid_for(L, kern, 32 * TY, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, src, dst, r_arr, omega, inv_diag);
+}
+
+cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                          float omega) {
+  const float diag = 2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]);
+  const float inv_diag = 1.f / diag;
+  CFD_DISPATCH_T(L.dtype, {
+    if (c.vx == 4) {
+      if (c.ty == 4) run_jacobi<T, 4, 4>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else if (c.ty == 16) run_jacobi<T, 4, 16>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else run_jacobi<T, 4, 8>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    } else if (c.vx == 2) {
+      if (c.ty == 4) run_jacobi<T, 2, 4>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else run_jacobi<T, 2, 8>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    } else {
+      if (c.ty == 4) run_jacobi<T, 1, 4>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else run_jacobi<T, 1, 8>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    }
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_reduce(const Launch& L, int mode, const int* set, int p_arr, int r_arr,
+                          double* partials, int nparts, double* out) {
+  const int zc = 16;
+  const long long tiles = count_tiles(L, 32, 8, zc);
+  const unsigned grid = (unsigned)(tiles < nparts ? tiles : nparts);
+  const Set3 s = set ? mk3(set) : Set3{{0, 0, 0}};
+  CFD_DISPATCH_T(L.dtype, {
+    k_reduce<T, 8><<<grid, dim3(32, 8), 0, L.stream>>>(L, zc, mode, s, p_arr, r_arr, partials);
+  });
+  k_reduce_final<<<1, 256, 0, L.stream>>>(partials, (int)grid, out);
+  return cudaGetLastError();
+}
+
+}  // namespace cfd

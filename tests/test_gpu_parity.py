@@ -1,0 +1,238 @@
+"""CUDA path against the FP64 oracle, element by element, through the C ABI.
+
+Sizes span several tiles with ragged tails (tiles are 32 x 8 cells for the
+point kernels and (32 vx) x ty for the Jacobi sweep); every array starts as
+NaN so a read of an unfilled ghost or pad cell shows up.  Floating-point
+tolerance: e(f) = max|f_gpu - f_ref| / max|f_ref| <= 1e-5 per step for FP32
+(pressure compared without its mean), <= 1e-3 after a full 100-step run.
+"""
+import math
+
+import numpy as np
+import pytest
+
+import workloads
+from gpu_helpers import make_pair, compare_state, rel_err, rounded, tg_fields
+
+pytestmark = pytest.mark.gpu
+
+RAGGED = (45, 37, 21)
+
+
+def rand_fields(dims, seed, scale=1.0):
+    rng = np.random.default_rng(seed)
+    return {c: scale * rng.uniform(-1, 1, dims[::-1]) for c in "uvwp"}
+
+
+@pytest.mark.parametrize("g", [1, 2])
+def test_ghost_fill_periodic_bitwise(g):
+    from paper_1201_2118_gb300 import U, V, W, P
+    o, grid, u, p = make_pair(RAGGED, ghost=g, fields=rand_fields(RAGGED, 1))
+    for k, a in enumerate((U, V, W)):
+        np.testing.assert_array_equal(grid.download(a, ghosts=True), u[k])
+    np.testing.assert_array_equal(grid.download(P, ghosts=True), p)
+
+
+def test_ghost_fill_cavity():
+    from paper_1201_2118_gb300 import U, V, W, P
+    o, grid, u, p = make_pair(RAGGED, bc="cavity", fields=rand_fields(RAGGED, 2))
+    for k, a in enumerate((U, V, W)):
+        np.testing.assert_allclose(grid.download(a, ghosts=True), u[k], rtol=0, atol=2.5e-7)
+    np.testing.assert_array_equal(grid.download(P, ghosts=True), p)
+
+
+def test_blockset_ghosts_equal_global_periodic_wrap():
+    """64 uneven blocks: every block's ghost cells equal the periodic global
+    field around it (np.pad wrap of the global array)."""
+    from paper_1201_2118_gb300 import Grid, U, mask
+    gd, blocks = workloads.block_tiling(seed=2, lo=8, hi=24)
+    rng = np.random.default_rng(5)
+    glob = rounded({"u": rng.standard_normal(gd[::-1])})["u"]
+    g = 2
+    grid = Grid(ghost=g, h=(0.1, 0.1, 0.1), blocks=[(b["dims"], b["origin"]) for b in blocks],
+                global_dims=gd)
+    grid.fill(float("nan"))
+    per = workloads.split_blocks({"u": glob}, blocks)
+    for b, f in enumerate(per):
+        grid.upload(f, block=b, fill_ghosts=False)
+    grid.ghost_fill(mask(U))
+    padded = np.pad(glob, g, mode="wrap")
+    for b, blk in enumerate(blocks):
+        (nx, ny, nz), (ox, oy, oz) = blk["dims"], blk["origin"]
+        ref = padded[oz:oz + nz + 2 * g, oy:oy + ny + 2 * g, ox:ox + nx + 2 * g]
+        np.testing.assert_array_equal(grid.download(U, block=b, ghosts=True), ref)
+
+
+@pytest.mark.parametrize("order,g", [(2, 1), (4, 2)])
+def test_rhs_eval(order, g):
+    from paper_1201_2118_gb300 import WU, WV, WW
+    fl = rand_fields(RAGGED, 3)
+    o, grid, u, p = make_pair(RAGGED, ghost=g, order=order, nu=0.05, fields=fl)
+    grid.rhs_eval()
+    F = o.rhs(*u)
+    for k, a in enumerate((WU, WV, WW)):
+        assert rel_err(grid.download(a), o.interior(F[k])) < 1e-5
+
+
+def test_rhs_eval_cavity():
+    from paper_1201_2118_gb300 import WU, WV, WW
+    fl = rand_fields(RAGGED, 4)
+    o, grid, u, p = make_pair(RAGGED, bc="cavity", nu=0.05, fields=fl)
+    grid.rhs_eval()
+    F = o.stage(0.0, None, 0.0, u, 1.0)
+    for k, a in enumerate((WU, WV, WW)):
+        assert rel_err(grid.download(a), o.interior(F[k])) < 1e-5
+
+
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+def test_stage2_combine(bc):
+    """out = 1/2 U + 1/2 U1 + c F(U1) with distinct inputs."""
+    from paper_1201_2118_gb300 import WU, WV, WW, U1, V1, W1, SET_U, SET_U1, SET_W, mask
+    fl = rand_fields(RAGGED, 5)
+    o, grid, u, p = make_pair(RAGGED, bc=bc, nu=0.02, fields=fl)
+    f1 = rounded(rand_fields(RAGGED, 6))
+    for k, a in enumerate((U1, V1, W1)):
+        grid.interior(a).copy_(grid.torch.from_numpy(f1["uvw"[k]]).float().cuda())
+    grid.ghost_fill(mask(U1, V1, W1))
+    u1 = [o.ghost_fill(o.embed(f1["uvw"[k]]), k) for k in range(3)]
+    grid.stage(0.5, SET_U, 0.5, SET_U1, 0.013, SET_W)
+    ref = o.stage(0.5, u, 0.5, u1, 0.013)
+    for k, a in enumerate((WU, WV, WW)):
+        assert rel_err(grid.download(a), o.interior(ref[k])) < 1e-5
+
+
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+@pytest.mark.parametrize("iters", [0, 1, 7])
+def test_pressure_solve(bc, iters):
+    from paper_1201_2118_gb300 import P, R, WU, WV, WW, mask
+    fl = rand_fields(RAGGED, 7)
+    o, grid, u, p = make_pair(RAGGED, bc=bc, fields=fl)
+    w = rounded(rand_fields(RAGGED, 8))
+    for k, a in enumerate((WU, WV, WW)):
+        grid.interior(a).copy_(grid.torch.from_numpy(w["uvw"[k]]).float().cuda())
+    grid.ghost_fill(mask(WU, WV, WW))
+    wo = [o.ghost_fill(o.embed(w["uvw"[k]]), k) for k in range(3)]
+    c_dt = 0.037
+    res = grid.pressure_solve(c_dt, iters, residual=True)
+    r = o.divergence(wo, c_dt)
+    assert rel_err(grid.download(R), o.interior(r)) < 1e-5
+    o.jacobi(p, r, iters)
+    assert rel_err(grid.download(P), o.interior(p)) < 1e-5
+    assert res == pytest.approx(o.residual(p, r), rel=1e-4)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+def test_project(bc):
+    from paper_1201_2118_gb300 import U1, V1, W1, WU, WV, WW, SET_U1, mask
+    fl = rand_fields(RAGGED, 9)
+    o, grid, u, p = make_pair(RAGGED, bc=bc, fields=fl)
+    w = rounded(rand_fields(RAGGED, 10))
+    for k, a in enumerate((WU, WV, WW)):
+        grid.interior(a).copy_(grid.torch.from_numpy(w["uvw"[k]]).float().cuda())
+    grid.ghost_fill(mask(WU, WV, WW))
+    wo = [o.ghost_fill(o.embed(w["uvw"[k]]), k) for k in range(3)]
+    grid.project(0.021, SET_U1)
+    ref = o.project(wo, p, 0.021)
+    for k, a in enumerate((U1, V1, W1)):
+        o.ghost_fill(ref[k], k)
+        got = grid.download(a, ghosts=True)
+        assert rel_err(got, ref[k]) < 1e-5
+
+
+def test_reduce_and_residual():
+    from paper_1201_2118_gb300 import SET_U
+    fl = rand_fields(RAGGED, 11)
+    o, grid, u, p = make_pair(RAGGED, fields=fl)
+    ke, um, dm = grid.reduce(SET_U)
+    rke, rum, rdm = o.reduce(u)
+    assert ke == pytest.approx(rke, rel=1e-12)
+    assert um == rum
+    assert dm == pytest.approx(rdm, rel=1e-6)
+
+
+def test_tg32_one_step_and_full_run():
+    """32^3 periodic Taylor-Green, nu=0.01, CFL 0.2, 50 Jacobi sweeps per
+    solve: e <= 1e-5 after one step, <= 1e-3 after 100 steps (graph replay)."""
+    n = 32
+    h = (2 * math.pi / n,) * 3
+    dt = workloads.cfl_dt(h)
+    o, grid, u, p = make_pair((n, n, n), h=h, nu=0.01, fields=tg_fields((n, n, n)))
+    grid.step(dt, 1)
+    o.rk2_step(u, p, dt, 50)
+    compare_state(o, grid, u, p, 1e-5, 1e-5, "step 1")
+    grid.step(dt, 99)
+    o.run(u, p, dt, 50, 99)
+    errs = compare_state(o, grid, u, p, 1e-3, 1e-3, "step 100")
+    t, s = grid.time
+    assert s == 100 and t == pytest.approx(100 * dt)
+    print("tg32 errors after 100 steps", errs)
+
+
+def test_rk_stages_equal_graph_step():
+    """rk_step(1) + rk_step(2) gives bitwise the same state as step(dt, 1)."""
+    from paper_1201_2118_gb300 import U, V, W, P
+    n = (40, 24, 18)
+    fl = workloads.random_div_free(n, (0.2, 0.2, 0.2), seed=3)
+    o, g1, _, _ = make_pair(n, h=(0.2, 0.2, 0.2), fields=fl, iters=9)
+    _, g2, _, _ = make_pair(n, h=(0.2, 0.2, 0.2), fields=fl, iters=9)
+    g1.rk_step(1, 0.01)
+    g1.rk_step(2, 0.01)
+    g2.step(0.01, 1)
+    for a in (U, V, W, P):
+        np.testing.assert_array_equal(g1.download(a), g2.download(a))
+
+
+@pytest.mark.parametrize("n,steps", [(32, 20), (48, 3)])
+def test_cavity_steps(n, steps):
+    """Lid-driven cavity Re=1000 (nu=1e-3), h=1/n, dt from CFL 0.2."""
+    h = (1.0 / n,) * 3
+    dt = workloads.cfl_dt(h)
+    o, grid, u, p = make_pair((n, n, n), bc="cavity", h=h, nu=1e-3,
+                              fields=workloads.ldc_noise(n, seed=1))
+    grid.step(dt, 1)
+    o.rk2_step(u, p, dt, 50)
+    compare_state(o, grid, u, p, 1e-5, 1e-5, "ldc step 1")
+    grid.step(dt, steps - 1)
+    o.run(u, p, dt, 50, steps - 1)
+    compare_state(o, grid, u, p, 1e-4, 1e-3, "ldc step %d" % steps)
+
+
+@pytest.mark.parametrize("order,g", [(2, 1), (4, 2)])
+def test_blockset_step_equals_global_oracle(order, g):
+    """64 uneven periodic blocks stepped together agree with the single-block
+    oracle on the global grid."""
+    from oracle import Oracle
+    from paper_1201_2118_gb300 import Grid, U, V, W, P
+    gd, blocks = workloads.block_tiling(seed=2, lo=8, hi=20)
+    h = (2 * math.pi / 64,) * 3
+    fl = rounded(workloads.random_div_free(gd, h, seed=3))
+    o = Oracle(gd, ghost=g, h=h, nu=0.01, order=order)
+    u, p = o.state(fl)
+    grid = Grid(ghost=g, h=h, blocks=[(b["dims"], b["origin"]) for b in blocks], global_dims=gd)
+    grid.fill(float("nan"))
+    grid.set_params(0.01, 20, 1.0, order)
+    grid.upload_blocks(workloads.split_blocks(fl, blocks))
+    dt = workloads.cfl_dt(h)
+    grid.step(dt, 2)
+    o.run(u, p, dt, 20, 2)
+    for k, a in enumerate((U, V, W, P)):
+        got = np.full(gd[::-1], np.nan)
+        for b, blk in enumerate(blocks):
+            (nx, ny, nz), (ox, oy, oz) = blk["dims"], blk["origin"]
+            got[oz:oz + nz, oy:oy + ny, ox:ox + nx] = grid.download(a, block=b)
+        ref = o.interior(u[k] if k < 3 else p)
+        assert rel_err(got, ref, remove_mean=(k == 3)) < 1e-5, k
+
+
+def test_nan_watchdog_and_errors():
+    from paper_1201_2118_gb300 import CfdError, Grid, U, SET_U
+    grid = Grid((16, 16, 16), ghost=1, h=(0.1, 0.1, 0.1))
+    grid.upload(rand_fields((16, 16, 16), 12))
+    grid.interior(U)[3, 4, 5] = float("inf")
+    with pytest.raises(CfdError) as e:
+        grid.reduce(SET_U)
+    assert e.value.status == 6
+    with pytest.raises(CfdError) as e:
+        grid.set_params(-1.0)
+    assert e.value.status == 1
+    grid.check()
