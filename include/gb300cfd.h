@@ -210,6 +210,43 @@ cfd_status cfd_check(cfd_grid* g);
 /* Last error message of the calling thread (never NULL). */
 const char* cfd_last_error(void);
 
+/* ------------------------------------------------ allocation-free variant */
+
+/* The paper has no counterpart of this entry point; it exists for callers
+ * that cannot allocate device memory when they need the diagnostics: code
+ * running while its stream is being captured into a CUDA graph (cudaMalloc
+ * is not capturable), host frameworks whose device memory belongs to their
+ * own pool allocator, and hooks inside a time loop that must not pay the
+ * device-wide synchronisation of cudaMalloc/cudaFree.
+ *
+ * Same quantities as cfd_reduce, from raw device pointers, allocating
+ * nothing (no cudaMalloc, no cudaFree, no allocating library routine):
+ * u, v, w point at interior element (0,0,0) of three arrays of storage dtype
+ * `dtype` (cfd_dtype) with row pitch pitch_y and plane pitch pitch_z
+ * (elements); the elements at index -1 along x (u), y (v) and z (w) must be
+ * readable (the divergence reads them).  dims = interior (nx, ny, nz),
+ * h = cell size.  out_dev is caller-owned device memory for 4 doubles:
+ * {1/2 sum |u|^2 hx hy hz, max |u_d|, max |D u|, number of non-finite
+ * values}, written asynchronously on `stream` (a cudaStream_t, may be NULL).
+ *
+ * Scratch: per-plane partial sums live in one file-scope static device
+ * array of the library, 4096 planes x 4 doubles (128 KiB), which every GPU
+ * that loads the library keeps until process exit.  nz > 4096 returns
+ * CFD_EINVAL.  All calls share that array and it keeps the last call's
+ * contents (each call overwrites every slot it later reads, so nothing needs
+ * clearing); calls that overlap on the GPU (different streams, or several
+ * host threads) race on it and must be serialised by the caller.
+ * The first call on each device looks up the array's device address (with
+ * that device current); make that first call before any stream capture.
+ * Errors: CFD_EINVAL for bad sizes or pointers, CFD_ECUDA if the launch
+ * fails; the message is in cfd_noalloc_last_error(). */
+cfd_status cfd_reduce_velocity_noalloc(const void* u, const void* v, const void* w, int dtype,
+                                       const int dims[3], long long pitch_y, long long pitch_z,
+                                       const double h[3], double* out_dev, void* stream);
+
+/* Last error message of cfd_reduce_velocity_noalloc on this thread. */
+const char* cfd_noalloc_last_error(void);
+
 #ifdef __cplusplus
 }
 #endif

@@ -48,8 +48,11 @@ SIGNATURES = {
     "cfd_copy_interior": [c_void_p, c_int, c_int, c_void_p, c_int],
     "cfd_check": [c_void_p],
     "cfd_last_error": [],
+    "cfd_reduce_velocity_noalloc": [c_void_p, c_void_p, c_void_p, c_int, P(c_int), c_ll, c_ll,
+                                    P(c_double), c_void_p, c_void_p],
+    "cfd_noalloc_last_error": [],
 }
-RESTYPES = {"cfd_last_error": ctypes.c_char_p}
+RESTYPES = {"cfd_last_error": ctypes.c_char_p, "cfd_noalloc_last_error": ctypes.c_char_p}
 
 STATUS = {0: "CFD_OK", 1: "CFD_EINVAL", 2: "CFD_ENOMEM", 3: "CFD_ECUDA", 4: "CFD_ESTATE",
           5: "CFD_EUNSUPPORTED", 6: "CFD_ENONFINITE", 7: "CFD_ETIMEOUT"}
