@@ -50,6 +50,9 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-secondary", action="store_true",
+                    help="skip the reduced-precision, block-set and adjoint comparisons")
+    ap.add_argument("--precision-steps", type=int, default=20)
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -199,6 +202,145 @@ def run_reference(a):
     print(json.dumps(line), flush=True)
 
 
+# ------------------------------------------------------ secondary measures
+
+def _time_steps(torch, g, dt, warm, steps):
+    for _ in range(warm):
+        g.step(dt, 1)
+    torch.cuda.synchronize()
+    a, b = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    a.record(g.stream)
+    for _ in range(steps):
+        g.step(dt, 1)
+    b.record(g.stream)
+    torch.cuda.synchronize()
+    return a.elapsed_time(b) / steps
+
+
+def measure_precision(torch, steps):
+    """512^3 periodic Taylor-Green (nu = 0.005): step time with FP32, BF16
+    and FP16 storage, and each run's max error per field against the FP32
+    run and against the exact solution after warm-up + timed steps."""
+    import numpy as np
+    from paper_1201_2118_gb300 import Grid, U, V, W, P
+    n = 512
+    h = (2 * math.pi / n,) * 3
+    dt = workloads.cfl_dt(h)
+    nu = workloads.WORKLOADS["tg512"]["nu"]
+    plane = workloads.taylor_green((n, n, 1), h=h)
+    warm = 3
+    out, fields = {}, {}
+    for dt_name in ("f32", "bf16", "f16"):
+        s = torch.cuda.Stream()
+        g = Grid((n, n, n), ghost=1, h=h, dtype=dt_name, stream=s)
+        g.set_params(nu, 50, 1.0, 2)
+        with torch.cuda.stream(s):
+            for arr, c in ((U, "u"), (V, "v"), (W, "w"), (P, "p")):
+                src = torch.from_numpy(plane[c][0]).to(g.tdtype).cuda()
+                g.interior(arr).copy_(src.expand(n, n, n))
+        g.ghost_fill(0b1111)
+        g.autotune(None)
+        ms = _time_steps(torch, g, dt, warm, steps)
+        T = (warm + steps) * dt
+        ex = workloads.taylor_green((n, n, 1), h=h, t=T, nu=nu)
+        with torch.cuda.stream(s):
+            fields[dt_name] = [g.interior(a)[n // 3].double().cpu().numpy() for a in (U, V, P)]
+        err_exact = {}
+        for k, c in enumerate("uvp"):
+            got, ref = fields[dt_name][k], ex[c][0]
+            if c == "p":
+                got, ref = got - got.mean(), ref - ref.mean()
+            err_exact[c] = float(np.abs(got - ref).max() / np.abs(ref).max())
+        out[dt_name] = {"ms_per_step": ms, "glups": n ** 3 / (ms * 1e-3) / 1e9,
+                        "err_vs_exact": err_exact, "jacobi_config": g.kernel_config()[0]}
+        del g
+        torch.cuda.empty_cache()
+    for dt_name in ("bf16", "f16"):
+        e = {}
+        for k, c in enumerate("uvp"):
+            a, b = fields[dt_name][k], fields["f32"][k]
+            if c == "p":
+                a, b = a - a.mean(), b - b.mean()
+            e[c] = float(np.abs(a - b).max() / np.abs(b).max())
+        out[dt_name]["err_vs_f32"] = e
+        out[dt_name]["speedup_vs_f32"] = out["f32"]["ms_per_step"] / out[dt_name]["ms_per_step"]
+    out["workload"] = "512^3 periodic Taylor-Green, nu=0.005, %d timed steps after %d warm-up; " \
+                      "errors on plane z = n/3 after the run" % (steps, warm)
+    return out
+
+
+def measure_blocks(torch):
+    """64 uneven periodic blocks (4x4x4, widths U{16..96}, seed 2), curl-noise
+    start (seed 3), nu = 0.01: batched (one persistent launch per kernel over
+    all blocks, autotuned, graph) against one launch per block per kernel."""
+    from paper_1201_2118_gb300 import Grid
+    cfg = workloads.WORKLOADS["blocks64"]
+    gd, blocks = workloads.block_tiling(seed=cfg["tiling_seed"])
+    h = workloads.workload_h("blocks64")
+    dt = workloads.cfl_dt(h)
+    fl = workloads.random_div_free(gd, h, seed=cfg["ic_seed"])
+    per = workloads.split_blocks(fl, blocks)
+    cells = gd[0] * gd[1] * gd[2]
+    out = {"global_dims": list(gd), "blocks": len(blocks), "cells": cells}
+    for ghost in (1, 2):
+        res = {}
+        for mode in ("batched", "per_block"):
+            s = torch.cuda.Stream()
+            g = Grid(ghost=ghost, h=h, blocks=[(b["dims"], b["origin"]) for b in blocks],
+                     global_dims=gd, stream=s)
+            g.set_params(cfg["nu"], cfg["jacobi_iters"], 1.0, 2 * ghost)
+            g.upload_blocks(per)
+            g.autotune(None)
+            g.set_launch_mode(mode == "per_block")
+            l0 = g.launches
+            ms = _time_steps(torch, g, dt, 3, 10)
+            res[mode] = {"ms_per_step": ms, "glups": cells / (ms * 1e-3) / 1e9,
+                         "launches_per_step": (g.launches - l0) / 13}
+            del g
+        res["speedup_batched_vs_per_block"] = res["per_block"]["ms_per_step"] / res["batched"]["ms_per_step"]
+        out["ghost%d_order%d" % (ghost, 2 * ghost)] = res
+    return out
+
+
+def measure_adjoint(torch):
+    """128^3 periodic curl-noise start (seed 4), 200 RK2 steps, sqrt(T)
+    checkpointing (15): time of the checkpointed forward against the
+    backward (segment recomputation + adjoint steps)."""
+    from paper_1201_2118_gb300 import Rollout, LU, LV, LW, LP
+    cfg = workloads.WORKLOADS["adj128"]
+    n = cfg["dims"]
+    h = workloads.workload_h("adj128")
+    dt = workloads.cfl_dt(h)
+    steps = cfg["steps"]
+    ro = Rollout(n, h, steps, dt, jacobi_iters=cfg["jacobi_iters"], seg=15)
+    g = ro.grid
+    fl = workloads.random_div_free(n, h, seed=cfg["seed"])
+    u0 = [torch.tensor(fl[c], dtype=torch.float32, device="cuda") for c in "uvw"]
+    g.autotune(None)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+    times = {"forward": [], "backward": []}
+    for rep in range(2):
+        a, b, c = ev(), ev(), ev()
+        torch.cuda.synchronize()
+        a.record(g.stream)
+        ro.forward_only(*u0, cfg["nu"])
+        b.record(g.stream)
+        with torch.cuda.stream(g.stream):
+            for arr in (LU, LV, LW):
+                g.interior(arr).fill_(1e-3)
+            g.interior(LP).zero_()
+        g.rollout_backward(dt, steps, ro.seg, ro.store_ptr, ro.nbytes)
+        c.record(g.stream)
+        torch.cuda.synchronize()
+        times["forward"].append(a.elapsed_time(b))
+        times["backward"].append(b.elapsed_time(c))
+    fwd, bwd = min(times["forward"]), min(times["backward"])
+    return {"forward_ms": fwd, "backward_ms": bwd, "backward_vs_forward": bwd / fwd,
+            "forward_ms_per_step": fwd / steps, "backward_ms_per_step": bwd / steps,
+            "checkpoint_every": ro.seg, "steps": steps, "dims": list(n),
+            "note": "backward = recomputation of every segment from its checkpoint + adjoint steps"}
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def run_gpu(a):
@@ -226,6 +368,8 @@ def run_gpu(a):
     g.set_cavity(1.0)
     g.set_params(cfg["nu"], cfg["jacobi_iters"], 1.0, cfg["order"])
     g.upload(workloads.ldc_noise(n, seed=cfg["seed"]))
+    g.autotune(None)
+    jcfg = g.kernel_config()
 
     def barrier():
         if dist is not None:
@@ -320,6 +464,14 @@ def run_gpu(a):
     if rank == 0 and world == 1 and not a.no_cpu_baseline:
         cpu = oracle_sample()
 
+    secondary = None
+    if rank == 0 and world == 1 and not a.no_secondary:
+        del g
+        torch.cuda.empty_cache()
+        secondary = {"precision": measure_precision(torch, a.precision_steps),
+                     "blocks": measure_blocks(torch),
+                     "adjoint": measure_adjoint(torch)}
+
     if rank == 0:
         line = {
             "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": a.steps,
@@ -330,13 +482,15 @@ def run_gpu(a):
                        "rk": "Heun RK2, projection per stage", "ghost": cfg["ghost"],
                        "parallelism": "replicas" if world > 1 else "single GPU",
                        "l2": "inputs larger than L2 (each %d^3 field %.0f MB vs 129 MB L2)"
-                             % (n, cells * g.torch.tensor([], dtype=g.tdtype).element_size() / 1e6)},
+                             % (n, cells * (4 if a.dtype == "f32" else 2) / 1e6)},
             "roofline": roofline,
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
             "clocks": clk.summary(),
             "check": {"kinetic_energy": ke, "max_abs_u": umax, "max_abs_div": divmax},
+            "jacobi_config": jcfg,
+            "secondary": secondary,
             "library": os.path.relpath(library_path(), ROOT),
         }
         print(json.dumps(line), flush=True)

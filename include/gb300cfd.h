@@ -77,13 +77,15 @@ typedef enum { CFD_BC_PERIODIC = 0, CFD_BC_WALL = 1 } cfd_bc;
 
 /* Array ids.  State: U, V, W (velocity) and P (pressure, also the Jacobi
  * warm start).  Work arrays: WU..WW (provisional stage velocity), U1..W1
- * (stage-1 velocity), P2 (Jacobi ping-pong), R (Poisson right-hand side). */
+ * (stage-1 velocity), P2 (Jacobi ping-pong), R (Poisson right-hand side).
+ * Adjoint state: LU, LV, LW, LP = dL/du, dL/dv, dL/dw, dL/dp. */
 typedef enum {
   CFD_U = 0, CFD_V = 1, CFD_W = 2, CFD_P = 3,
   CFD_WU = 4, CFD_WV = 5, CFD_WW = 6,
   CFD_U1 = 7, CFD_V1 = 8, CFD_W1 = 9,
   CFD_P2 = 10, CFD_R = 11,
-  CFD_NUM_ARRAYS = 12
+  CFD_LU = 12, CFD_LV = 13, CFD_LW = 14, CFD_LP = 15,
+  CFD_NUM_ARRAYS = 16
 } cfd_array;
 
 /* Velocity triples for cfd_stage / cfd_project / cfd_reduce. */
@@ -191,6 +193,38 @@ cfd_status cfd_reduce(cfd_grid* g, int set, double* kinetic_energy, double* max_
 /* ||L P - R||_2 over all interior cells, FP64.  Synchronises. */
 cfd_status cfd_residual(cfd_grid* g, double* residual);
 
+/* ------------------------------------------------------------- adjoint */
+
+/* Discrete adjoint of one RK2 step (cfd_step with n = 1) of a single
+ * periodic FP32 block, order 2, ghost width 2 (the transposed advection
+ * reads two cells away).  un and u1 point at element (-g,-g,-g) of three
+ * arrays each, laid out like this grid's arrays (cfd_array_layout) and with
+ * filled ghosts: the forward state at the start of the step and after its
+ * stage-1 projection.  On entry LU, LV, LW, LP hold dL/d(u, p) after the
+ * step (interior), on exit dL/d(u, p) before it.  dL/dnu of the step is
+ * added to *dnu_accum_dev (device memory, one double).  Work arrays W*, U1*,
+ * P, P2, R are overwritten.  Transposes: L^T = L, D^T = -G, G^T = -D; the
+ * transposed Jacobi solve runs the forward sweep kernel (Sec. 4.1's
+ * pressure iteration is symmetric).  CFD_EUNSUPPORTED for other grids. */
+cfd_status cfd_adjoint_step(cfd_grid* g, double dt, const void* const un[3],
+                            const void* const u1[3], double* dnu_accum_dev);
+
+/* sqrt(T) checkpointed rollout for gradients of a final-time loss.
+ * cfd_rollout_bytes: device bytes of the store for nsteps steps with a
+ * checkpoint of (u, v, w, p) every seg steps plus seg recorded steps.
+ * cfd_rollout_forward: nsteps steps from the current state (graph replay),
+ * checkpointing into store.  cfd_rollout_backward: with dL/d(u_T, p_T) in
+ * LU..LP, recomputes each segment from its checkpoint (last segment first),
+ * recording u^n and u1 per step, and runs the adjoint steps in reverse; on
+ * return LU..LP hold dL/d(u_0, p_0) and *dnu = dL/dnu (synchronises).  The
+ * forward kernels are deterministic, so the recomputation reproduces the
+ * forward states bitwise.  U..P are left at the end of the first segment. */
+cfd_status cfd_rollout_bytes(const cfd_grid* g, int nsteps, int seg, size_t* bytes);
+cfd_status cfd_rollout_forward(cfd_grid* g, double dt, int nsteps, int seg, void* store,
+                               size_t bytes);
+cfd_status cfd_rollout_backward(cfd_grid* g, double dt, int nsteps, int seg, void* store,
+                                size_t bytes, double* dnu);
+
 /* Simulation time and step counter (for checkpoint/resume). */
 cfd_status cfd_get_state(const cfd_grid* g, double* t, long long* step);
 cfd_status cfd_set_state(cfd_grid* g, double t, long long step);
@@ -199,6 +233,33 @@ cfd_status cfd_set_state(cfd_grid* g, double t, long long step);
  * (compact (nz, ny, nx), storage dtype; pinned for asynchronous copies)
  * and the device.  to_device != 0: host -> device.  Asynchronous. */
 cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int to_device);
+
+/* Kernel variants.  jacobi = {kind, vx, ty, zc, stages}: kind 0 is the
+ * register/shuffle sweep (vx in {1,2,4} cells per thread along x, ty rows per
+ * CTA in {4,8,16}), kind 1 the TMA-staged sweep (vx 4 with ty in {4,8,16}, or
+ * vx 2 with ty in {8,16},
+ * stages in {4,6} shared-memory planes), kind 2 the direct sweep without
+ * shared memory ((vx, ty, zc) in {(4,4,1), (4,4,2), (4,4,4), (4,8,1), (4,2,4),
+ * (2,4,2), (1,8,1)}, zc = z-planes per CTA); zc = z-planes per tile.
+ * stencil = {ty in {4,8}, zc} for the point kernels.  NULL leaves a part
+ * unchanged.  Results do not depend on the variant. */
+cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[2]);
+cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[2]);
+
+/* Times the candidate variants on this grid (overwrites the work arrays,
+ * keeps U and P) and selects the fastest; with cache_path, reuses or
+ * appends a line keyed by GPU name, dtype, ghost, order and block sizes.
+ * The Cactus driver's auto-tuning of the data distribution (Sec. 1.2),
+ * re-targeted to the kernels' tile shapes.  sweep_us (may be NULL)
+ * receives the chosen Jacobi sweep time in microseconds. */
+cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us);
+
+/* Launch mode of the stencil kernels (RHS/stage, divergence, Jacobi,
+ * projection) on a block set: 0 (default) = one persistent launch walks the
+ * tiles of all blocks; 1 = one launch per block per kernel (the baseline the
+ * batched form is measured against).  Ghost fills stay one launch.  Results
+ * are identical. */
+cfd_status cfd_set_launch_mode(cfd_grid* g, int per_block);
 
 /* Number of kernel launches this grid has enqueued so far (graph replays
  * count every kernel node once per replay). */

@@ -85,6 +85,28 @@ double ora_residual(const ora_grid* G, const double* p, const double* r);
 /* The 7-point operator itself: lp = L p on the interior (test helper). */
 void ora_laplace_p(const ora_grid* G, const double* p, double* lp);
 
+/* ---- discrete adjoint (cfd_oracle_adjoint.c) ---- */
+
+/* Transpose of ora_ghost_fill's linear part: ghost values are added onto
+ * their sources (passes z, y, x) and cleared. */
+void ora_ghost_fold(const ora_grid* G, double* f, int kind);
+
+/* Transpose of ora_stage linearised at y: xbar += a outbar,
+ * ybar += b outbar + c (dF/dy)^T outbar, *nubar += c <outbar, lap y>;
+ * outbar is cleared.  xbar may be NULL when a == 0. */
+void ora_adj_stage(const ora_grid* G, double a, double* const xbar[3], double b,
+                   const double* const y[3], double c, double* const ybar[3],
+                   double* const outbar[3], double* nubar);
+
+/* Transpose of ora_rk2_step linearised at the step's stored states u^n
+ * (start of the step) and u1 (after the stage-1 projection), both with
+ * filled ghosts.  On entry ubar, pbar hold dL/d(u, p) after the step
+ * (interior, ghosts 0); on exit dL/d(u, p) before it.  *nubar accumulates
+ * dL/dnu.  scratch: 11 arrays. */
+void ora_adj_rk2_step(const ora_grid* G, double* const un[3], double* const u1[3], double dt,
+                      int iters, double* const ubar[3], double* pbar, double* nubar,
+                      double* const scratch[11]);
+
 #ifdef __cplusplus
 }
 #endif

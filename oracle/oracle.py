@@ -73,9 +73,16 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = ctypes.c_double if name == "ora_residual" else None
-            if hasattr(lib, "ora_adj_rk2_step"):
-                fn = lib.ora_adj_rk2_step
-                fn.argtypes = [G, P3, _D, ctypes.c_double, ctypes.c_int, P3, _D, _D, _D * 24]
+            adj = {
+                "ora_ghost_fold": [G, _D, ctypes.c_int],
+                "ora_adj_stage": [G, ctypes.c_double, P3, ctypes.c_double, P3, ctypes.c_double,
+                                  P3, P3, _D],
+                "ora_adj_rk2_step": [G, P3, P3, ctypes.c_double, ctypes.c_int, P3, _D, _D,
+                                     _D * 11],
+            }
+            for name, args in adj.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
                 fn.restype = None
             _lib = lib
     return _lib
@@ -211,6 +218,54 @@ class Oracle:
         out = self.zeros()
         self.lib.ora_laplace_p(self._G(), _ptr(p), _ptr(out))
         return out
+
+    # -- discrete adjoint
+    def ghost_fold(self, f, kind):
+        self.lib.ora_ghost_fold(self._G(), _ptr(f), int(kind))
+        return f
+
+    def adj_stage(self, a, xbar, b, y, c, ybar, outbar):
+        nb = ctypes.c_double(0.0)
+        xs = _p3(xbar) if xbar is not None else (_D * 3)()
+        self.lib.ora_adj_stage(self._G(), float(a), xs, float(b), _p3(y), float(c), _p3(ybar),
+                               _p3(outbar), ctypes.byref(nb))
+        return nb.value
+
+    def forward_record(self, u, p, dt, iters, steps):
+        """Runs steps RK2 steps in place and returns the per-step stored
+        states [(u^n, u1), ...] (copies, ghosts filled)."""
+        scratch = [self.zeros() for _ in range(8)]
+        states = []
+        for _ in range(steps):
+            un = [a.copy() for a in u]
+            self.rk2_step(u, p, dt, iters, scratch)
+            states.append((un, [scratch[3].copy(), scratch[4].copy(), scratch[5].copy()]))
+        return states
+
+    def adj_rk2_step(self, un, u1, dt, iters, ubar, pbar, scratch=None):
+        """One adjoint step in place on ubar, pbar; returns dL/dnu of it."""
+        if scratch is None:
+            scratch = [self.zeros() for _ in range(11)]
+        nb = ctypes.c_double(0.0)
+        self.lib.ora_adj_rk2_step(self._G(), _p3(un), _p3(u1), float(dt), int(iters), _p3(ubar),
+                                  _ptr(pbar), ctypes.byref(nb),
+                                  (_D * 11)(*[_ptr(s) for s in scratch]))
+        return nb.value
+
+    def gradient(self, u0, p0, dt, iters, steps, loss_grad):
+        """dL/du0 (interior, 3 arrays), dL/dp0 and dL/dnu of a loss of the
+        final velocity: loss_grad(u_T interiors) -> (L, [dL/du_T interiors])."""
+        u = [a.copy() for a in u0]
+        p = p0.copy()
+        states = self.forward_record(u, p, dt, iters, steps)
+        L, g = loss_grad([self.interior(a) for a in u])
+        ubar = [self.embed(gc) for gc in g]
+        pbar = self.zeros()
+        nubar = 0.0
+        scratch = [self.zeros() for _ in range(11)]
+        for un, u1 in reversed(states):
+            nubar += self.adj_rk2_step(un, u1, dt, iters, ubar, pbar, scratch)
+        return L, [self.interior(a).copy() for a in ubar], self.interior(pbar).copy(), nubar
 
     # -- set-up helper: padded state from interior arrays, ghosts filled
     def state(self, fields):

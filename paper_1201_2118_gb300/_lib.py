@@ -39,6 +39,14 @@ SIGNATURES = {
     "cfd_project": [c_void_p, c_double, c_int],
     "cfd_jacobi": [c_void_p, c_int],
     "cfd_stats": [c_void_p, P(c_ll)],
+    "cfd_set_launch_mode": [c_void_p, c_int],
+    "cfd_set_kernel_config": [c_void_p, P(c_int), P(c_int)],
+    "cfd_get_kernel_config": [c_void_p, P(c_int), P(c_int)],
+    "cfd_autotune": [c_void_p, ctypes.c_char_p, P(c_double)],
+    "cfd_adjoint_step": [c_void_p, c_double, P(c_void_p), P(c_void_p), P(c_double)],
+    "cfd_rollout_bytes": [c_void_p, c_int, c_int, P(c_size_t)],
+    "cfd_rollout_forward": [c_void_p, c_double, c_int, c_int, c_void_p, c_size_t],
+    "cfd_rollout_backward": [c_void_p, c_double, c_int, c_int, c_void_p, c_size_t, P(c_double)],
     "cfd_rk_step": [c_void_p, c_int, c_double],
     "cfd_step": [c_void_p, c_double, c_int],
     "cfd_reduce": [c_void_p, c_int, P(c_double), P(c_double), P(c_double)],

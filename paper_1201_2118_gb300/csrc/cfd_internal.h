@@ -6,7 +6,7 @@
 
 namespace cfd {
 
-constexpr int kNumArrays = 12;   // matches CFD_NUM_ARRAYS
+constexpr int kNumArrays = 16;   // matches CFD_NUM_ARRAYS
 constexpr int kMaxBlocks = 512;
 constexpr int kAlignBytes = 128; // interior x = 0 of every row, and row pitch
 constexpr int kMaxGhost = 2;
@@ -16,12 +16,16 @@ enum Arr {
   A_U = 0, A_V = 1, A_W = 2, A_P = 3,
   A_WU = 4, A_WV = 5, A_WW = 6,
   A_U1 = 7, A_V1 = 8, A_W1 = 9,
-  A_P2 = 10, A_R = 11
+  A_P2 = 10, A_R = 11,
+  A_LU = 12, A_LV = 13, A_LW = 14, A_LP = 15   // adjoint state (dL/du, dL/dp)
 };
 
 // Field kind of each array: 0 u, 1 v, 2 w (velocity components), 3 scalar.
 __host__ __device__ inline int array_kind(int a) {
-  return (a == A_P || a == A_P2 || a == A_R) ? 3 : (a < 3 ? a : (a - 4) % 3);
+  if (a == A_P || a == A_P2 || a == A_R || a == A_LP) return 3;
+  if (a < 3) return a;
+  if (a >= A_LU) return a - A_LU;
+  return (a - 4) % 3;
 }
 
 enum Bc { BC_PERIODIC = 0, BC_WALL = 1 };
@@ -39,8 +43,9 @@ struct BlockDev {
 
 // What every launch needs.
 struct Launch {
-  const BlockDev* blocks;      // device table
-  int nblocks;
+  const BlockDev* blocks;      // device table (all blocks)
+  int b0;                      // first block this launch covers
+  int nblocks;                 // blocks b0 .. b0 + nblocks - 1
   void* base;                  // arena base (arrays addressed by element offsets)
   int dtype;                   // 0 f32, 1 bf16, 2 f16
   int ghost;
@@ -54,10 +59,38 @@ struct Launch {
 };
 
 // Kernel variants (autotuned).
-struct JacobiCfg { int vx, ty, zc; };   // x vector width, warps per CTA (rows), z chunk
+//   kind 0: register/shuffle sweep (any block size, plain loads)
+//   kind 1: TMA-staged sweep (tensor maps per block, S-stage mbarrier ring)
+//   kind 2: direct sweep (no shared memory; zc = z-planes per CTA, TZ)
+struct JacobiCfg { int kind, vx, ty, zc, stages; };
 struct StencilCfg { int ty, zc; };      // rows per CTA (32 x ty threads), z chunk
 
+// One array as a 3D tensor for TMA: start of the allocation, row length
+// (the row pitch, elements), rows per plane and planes.
+struct TmaArray { void* ptr; long long row_elems, rows, planes; };
+constexpr int kTmaMapBytes = 128;
+
+// Encodes the Jacobi tensor maps (per block: P, P2, R) for config c into
+// out_host (narrays x 128 bytes).  False if the driver entry point or an
+// encoding fails.
+bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int dtype,
+                        const JacobiCfg& c);
+cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* maps_dev,
+                              int src_slot, int dst, float omega);
+
 long long count_tiles(const Launch& L, int tx, int ty, int tz);
+
+// Adjoint kernels (FP32 storage, single periodic block, order 2).
+struct AdjSet { int a[3]; };
+struct Ptr3 { const float* p[3]; };  // interior origins of stored forward states
+cudaError_t launch_adj_proj(const Launch& L, const AdjSet& lam, int lp, float c_dt, float r_scale,
+                            int p_out, int r_out);
+cudaError_t launch_adj_wp(const Launch& L, const AdjSet& lam, int bk, int bk1, float coef,
+                          const AdjSet& wout, int lp);
+cudaError_t launch_adj_stage(const Launch& L, const AdjSet& lam, const Ptr3& y, const AdjSet& out,
+                             int acc, float b, float c, int has_x, const AdjSet& x, float a,
+                             float nu, double* partials, int nparts, double* nu_acc,
+                             double nu_coef);
 
 cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr,
                          const long long* d_prefix, long long total);
@@ -68,6 +101,8 @@ cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* w
                               float inv_cdt, int r_arr);
 cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
                           float omega);
+cudaError_t launch_jacobi_direct(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                                 float omega);
 cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset, int p_arr,
                            float cdt, const int* oset);
 cudaError_t launch_copy(const Launch& L, const StencilCfg& c, int src, int dst);

@@ -66,6 +66,9 @@ struct cfd_grid {
   size_t bytes = 0;
   bool owns = false;
   size_t table_off = 0, prefix_off = 0, partial_off = 0, out_off = 0, flag_off = 0;
+  size_t maps_off = 0;            // TMA tensor maps: nblocks x {P, P2, R}
+  size_t adj_off = 0;             // adjoint scalars: [0] dL/dnu accumulator
+  bool maps_ready = false;        // maps encoded for the current Jacobi config
   size_t arrays_off = 0;
   int nparts = 0;
   long long ghost_total = 0;
@@ -78,14 +81,22 @@ struct cfd_grid {
   long long step = 0;
   bool sticky = false;
 
-  JacobiCfg jcfg{4, 8, 32};
+  JacobiCfg jcfg{0, 4, 8, 32, 4};
   StencilCfg scfg{8, 16};
+  bool per_block = false;  // baseline mode: one launch per block per stencil kernel
 
   cudaGraphExec_t gexec = nullptr;
   bool graph_valid = false;
   double graph_dt = 0.0;
   long long graph_nodes = 0;   // kernel launches per replay
   long long launches = 0;      // kernel launches enqueued (incl. replays)
+
+  // rollout graphs: segment recompute and segment adjoint, keyed by length
+  struct SegGraph { cudaGraphExec_t exec = nullptr; long long nodes = 0; int len = 0; };
+  SegGraph rec_graph[2], adj_graph[2];
+  const void* seg_store = nullptr;
+  double seg_dt = 0.0;
+  int seg_len = 0;
 };
 
 namespace {
@@ -127,6 +138,10 @@ void plan_layout(cfd_grid* g) {
   off = round_up(off + sizeof(double) * 4, 256);
   g->flag_off = off;
   off = round_up(off + 256, 256);
+  g->maps_off = off;
+  off = round_up(off + (size_t)kTmaMapBytes * 3 * g->nblocks, 256);
+  g->adj_off = off;
+  off = round_up(off + 8 * sizeof(double), 256);
   g->arrays_off = off;
   for (auto& b : g->hb) {
     b.py = (int)round_up((size_t)align_e + b.n[0] + g->g, align_e);
@@ -172,6 +187,8 @@ void build_tables(cfd_grid* g) {
   }
 }
 
+cfd_status refresh_maps(cfd_grid* g);
+
 cfd_status upload_tables(cfd_grid* g) {
   if (!g->base) return CFD_OK;
   build_tables(g);
@@ -181,12 +198,34 @@ cfd_status upload_tables(cfd_grid* g) {
                         sizeof(long long) * (g->nblocks + 1), cudaMemcpyHostToDevice, g->own));
   CK(g, cudaMemsetAsync(g->base + g->flag_off, 0, 256, g->own));
   CK(g, cudaStreamSynchronize(g->own));
+  return refresh_maps(g);
+}
+
+// Tensor maps of the TMA Jacobi sweep (box sizes depend on the config).
+cfd_status refresh_maps(cfd_grid* g) {
+  g->maps_ready = false;
+  if (g->jcfg.kind != 1 || !g->base) return CFD_OK;
+  std::vector<TmaArray> arrs;
+  const int ids[3] = {A_P, A_P2, A_R};
+  for (const auto& b : g->hb)
+    for (int a : ids)
+      arrs.push_back(TmaArray{g->base + b.first_byte + b.array_bytes * a, b.py,
+                              (long long)b.n[1] + 2 * g->g, b.planes});
+  std::vector<unsigned char> host(arrs.size() * kTmaMapBytes + 64);
+  unsigned char* aligned = host.data() + ((64 - (reinterpret_cast<uintptr_t>(host.data()) % 64)) % 64);
+  if (!encode_jacobi_maps(aligned, arrs.data(), (int)arrs.size(), g->dtype, g->jcfg))
+    return fail(CFD_EUNSUPPORTED, "TMA tensor map encoding failed for this Jacobi config");
+  CK(g, cudaMemcpyAsync(g->base + g->maps_off, aligned, arrs.size() * kTmaMapBytes,
+                        cudaMemcpyHostToDevice, g->own));
+  CK(g, cudaStreamSynchronize(g->own));
+  g->maps_ready = true;
   return CFD_OK;
 }
 
 Launch make_launch(cfd_grid* g) {
   Launch L;
   L.blocks = reinterpret_cast<const BlockDev*>(g->base + g->table_off);
+  L.b0 = 0;
   L.nblocks = g->nblocks;
   L.base = g->base;
   L.dtype = g->dtype;
@@ -229,13 +268,23 @@ cfd_status common_init(cfd_grid* g, int ghost, const double h[3], int storage, v
   g->hn.resize(3 * g->nblocks);
   for (int b = 0; b < g->nblocks; ++b)
     for (int d = 0; d < 3; ++d) g->hn[3 * b + d] = g->hb[b].n[d];
-  if (g->dtype == CFD_F32) g->jcfg = JacobiCfg{4, 8, 32};
-  else g->jcfg = JacobiCfg{4, 8, 32};
+  g->jcfg = JacobiCfg{0, 4, 8, 32, 4};
   plan_layout(g);
   return CFD_OK;
 }
 
+void drop_seg_graphs(cfd_grid* g) {
+  for (int q = 0; q < 2; ++q) {
+    if (g->rec_graph[q].exec) cudaGraphExecDestroy(g->rec_graph[q].exec);
+    if (g->adj_graph[q].exec) cudaGraphExecDestroy(g->adj_graph[q].exec);
+    g->rec_graph[q] = cfd_grid::SegGraph();
+    g->adj_graph[q] = cfd_grid::SegGraph();
+  }
+  g->seg_store = nullptr;
+}
+
 void destroy_handles(cfd_grid* g) {
+  drop_seg_graphs(g);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
   if (g->own) cudaStreamSynchronize(g->own);
   if (g->owns && g->base) cudaFree(g->base);
@@ -259,6 +308,26 @@ cfd_status join_out(cfd_grid* g) {
 
 // ------------------------------------------------------------- enqueuers
 
+// Runs f(L) once over all blocks (one persistent launch walks the tiles of
+// every block), or once per block in the per-block baseline mode.
+template <typename F>
+cfd_status each_launch(cfd_grid* g, F f) {
+  Launch L = make_launch(g);
+  if (!g->per_block) {
+    CK(g, f(L));
+    g->launches += 1;
+    return CFD_OK;
+  }
+  for (int b = 0; b < g->nblocks; ++b) {
+    Launch Lb = L;
+    Lb.b0 = b;
+    Lb.nblocks = 1;
+    CK(g, f(Lb));
+    g->launches += 1;
+  }
+  return CFD_OK;
+}
+
 cfd_status enq_ghost(cfd_grid* g, unsigned mask) {
   int arrs[kNumArrays];
   int n = 0;
@@ -276,22 +345,31 @@ unsigned set_mask(int s) {
 }
 
 cfd_status enq_stage(cfd_grid* g, double a, int xs, double b, int ys, double c, int os) {
-  const Launch L = make_launch(g);
-  CK(g, launch_stage(L, g->scfg, g->order, (float)a, a != 0.0 ? kSets[xs] : nullptr, (float)b,
-                     kSets[ys], (float)c, kSets[os], (float)g->nu));
-  g->launches += 1;
-  return CFD_OK;
+  return each_launch(g, [&](const Launch& L) {
+    return launch_stage(L, g->scfg, g->order, (float)a, a != 0.0 ? kSets[xs] : nullptr, (float)b,
+                        kSets[ys], (float)c, kSets[os], (float)g->nu);
+  });
+}
+
+// One Jacobi sweep src -> dst with the configured variant.
+cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst) {
+  if (g->jcfg.kind == 1 && g->maps_ready)
+    return launch_jacobi_tma(L, g->jcfg, g->base + g->maps_off, src == A_P ? 0 : 1, dst,
+                             (float)g->omega);
+  if (g->jcfg.kind == 2) return launch_jacobi_direct(L, g->jcfg, src, dst, A_R, (float)g->omega);
+  return launch_jacobi(L, g->jcfg, src, dst, A_R, (float)g->omega);
 }
 
 cfd_status enq_sweeps(cfd_grid* g, int iters) {
-  const Launch L = make_launch(g);
   int cur = A_P, oth = A_P2;
+  cfd_status s;
   for (int it = 0; it < iters; ++it) {
-    CK(g, launch_jacobi(L, g->jcfg, cur, oth, A_R, (float)g->omega));
+    if ((s = each_launch(g, [&](const Launch& L) { return sweep(g, L, cur, oth); })) != CFD_OK)
+      return s;
     std::swap(cur, oth);
   }
-  g->launches += iters;
   if (cur != A_P) {
+    const Launch L = make_launch(g);
     CK(g, launch_copy(L, g->scfg, cur, A_P));
     g->launches += 1;
   }
@@ -299,16 +377,18 @@ cfd_status enq_sweeps(cfd_grid* g, int iters) {
 }
 
 cfd_status enq_solve(cfd_grid* g, double c_dt, int iters) {
-  const Launch L = make_launch(g);
-  CK(g, launch_divergence(L, g->scfg, kSets[CFD_SET_W], (float)(1.0 / c_dt), A_R));
-  g->launches += 1;
+  cfd_status s = each_launch(g, [&](const Launch& L) {
+    return launch_divergence(L, g->scfg, kSets[CFD_SET_W], (float)(1.0 / c_dt), A_R);
+  });
+  if (s != CFD_OK) return s;
   return enq_sweeps(g, iters);
 }
 
 cfd_status enq_project(cfd_grid* g, double c_dt, int os) {
-  const Launch L = make_launch(g);
-  CK(g, launch_project(L, g->scfg, kSets[CFD_SET_W], A_P, (float)c_dt, kSets[os]));
-  g->launches += 1;
+  cfd_status s = each_launch(g, [&](const Launch& L) {
+    return launch_project(L, g->scfg, kSets[CFD_SET_W], A_P, (float)c_dt, kSets[os]);
+  });
+  if (s != CFD_OK) return s;
   return enq_ghost(g, set_mask(os));
 }
 
@@ -339,8 +419,110 @@ cfd_status run_reduce(cfd_grid* g, int mode, int set, double out[4]) {
   return CFD_OK;
 }
 
-void invalidate_graph(cfd_grid* g) { g->graph_valid = false; }
+void invalidate_graph(cfd_grid* g) {
+  g->graph_valid = false;
+  drop_seg_graphs(g);
+}
 
+// ------------------------------------------------------------- adjoint
+
+cfd_status adjoint_supported(cfd_grid* g) {
+  if (g->nblocks != 1 || g->dtype != CFD_F32 || g->order != 2 || g->g < 2)
+    return fail(CFD_EUNSUPPORTED,
+                "the adjoint needs one FP32 block, order 2 and ghost width 2");
+  for (int f = 0; f < 6; ++f)
+    if (g->bc[f] != CFD_BC_PERIODIC) return fail(CFD_EUNSUPPORTED, "the adjoint needs periodic faces");
+  return CFD_OK;
+}
+
+// Byte offset of element (-g,-g,-g) within an array's allocation, and of
+// the interior origin.
+size_t ghost_origin_bytes(const cfd_grid* g) { return (size_t)(kAlignBytes / g->es - g->g) * g->es; }
+size_t interior_bytes(const cfd_grid* g) {
+  const HostBlock& b = g->hb[0];
+  return ((size_t)g->g * b.pz + (size_t)g->g * b.py + kAlignBytes / g->es) * g->es;
+}
+char* array_start(cfd_grid* g, int a) { return g->base + g->hb[0].first_byte + g->hb[0].array_bytes * a; }
+
+cfd_status enq_adjoint_step(cfd_grid* g, double dt, const Ptr3& un, const Ptr3& u1, double* nu_acc) {
+  const Launch L = make_launch(g);
+  double diag = 0.0;
+  for (int d = 0; d < 3; ++d) diag += 2.0 / (g->h[d] * g->h[d]);
+  const float r_scale = (float)(-diag / g->omega);
+  double* partials = reinterpret_cast<double*>(g->base + g->partial_off);
+  const AdjSet lu{{A_LU, A_LV, A_LW}}, ws{{A_WU, A_WV, A_WW}}, u1s{{A_U1, A_V1, A_W1}};
+  const unsigned m_lu = (1u << A_LU) | (1u << A_LV) | (1u << A_LW);
+  cfd_status s;
+  for (int stage = 2; stage >= 1; --stage) {
+    const double c_dt = stage == 2 ? 0.5 * dt : dt;
+    const AdjSet& lam_in = stage == 2 ? lu : u1s;
+    if ((s = enq_ghost(g, stage == 2 ? m_lu : set_mask(CFD_SET_U1))) != CFD_OK) return s;
+    CK(g, launch_adj_proj(L, lam_in, A_LP, (float)c_dt, r_scale, A_P, A_R));
+    if ((s = enq_ghost(g, 1u << A_P)) != CFD_OK) return s;
+    int cur = A_P, oth = A_P2;
+    for (int it = 0; it < g->iters; ++it) {
+      CK(g, sweep(g, L, cur, oth));
+      std::swap(cur, oth);
+    }
+    // cur = b_{K+1}, oth = b_K (for K = 0, b_1 in both roles: lam_r = 0 path)
+    CK(g, launch_adj_wp(L, lam_in, g->iters > 0 ? oth : cur, cur,
+                        (float)(g->omega / diag / c_dt), ws, A_LP));
+    if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
+    if (stage == 2)
+      CK(g, launch_adj_stage(L, ws, u1, u1s, 0, 0.5f, (float)(0.5 * dt), 1, lu, 0.5f, (float)g->nu,
+                             partials, g->nparts, nu_acc, 0.5 * dt));
+    else
+      CK(g, launch_adj_stage(L, ws, un, lu, 1, 1.0f, (float)dt, 0, lu, 0.0f, (float)g->nu,
+                             partials, g->nparts, nu_acc, dt));
+    g->launches += 5 + g->iters;
+  }
+  return CFD_OK;
+}
+
+// ------------------------------------------------------------- autotuner
+//
+// Times candidate kernel variants on this grid (the Jacobi sweep, the RHS +
+// stage kernel) and keeps the fastest.  Results are cached in a text file,
+// one line per key "device|dtype|ghost|order|blocks": repeated runs on the
+// same GPU model and grid reuse them without timing.
+
+std::string tune_key(cfd_grid* g) {
+  cudaDeviceProp prop;
+  std::string name = "unknown";
+  if (cudaGetDeviceProperties(&prop, g->device) == cudaSuccess) name = prop.name;
+  for (auto& ch : name)
+    if (ch == ' ' || ch == '|' || ch == '=') ch = '_';
+  std::string dims;
+  for (const auto& b : g->hb)
+    dims += std::to_string(b.n[0]) + "x" + std::to_string(b.n[1]) + "x" + std::to_string(b.n[2]) + ",";
+  unsigned long long hsh = 1469598103934665603ull;  // FNV-1a of the block dims
+  for (char ch : dims) hsh = (hsh ^ (unsigned char)ch) * 1099511628211ull;
+  char buf[160];
+  snprintf(buf, sizeof buf, "%s|dt%d|g%d|o%d|nb%d|%016llx", name.c_str(), g->dtype, g->g, g->order,
+           g->nblocks, hsh);
+  return buf;
+}
+
+cfd_status time_region(cfd_grid* g, int reps, float* ms, int what) {
+  cudaEvent_t a, b;
+  CK(g, cudaEventCreate(&a));
+  CK(g, cudaEventCreate(&b));
+  CK(g, cudaEventRecord(a, g->own));
+  cfd_status s = CFD_OK;
+  for (int r = 0; r < reps && s == CFD_OK; ++r)
+    s = what == 0 ? enq_sweeps(g, 2) : enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, 1e-3, CFD_SET_W);
+  CK(g, cudaEventRecord(b, g->own));
+  CK(g, cudaEventSynchronize(b));
+  CK(g, cudaEventElapsedTime(ms, a, b));
+  cudaEventDestroy(a);
+  cudaEventDestroy(b);
+  return s;
+}
+
+}  // namespace
+
+namespace {
+cfd_status ensure_step_graph(cfd_grid* g, double dt);
 }  // namespace
 
 // =================================================================== C ABI
@@ -596,6 +778,143 @@ cfd_status cfd_jacobi(cfd_grid* g, int iters) {
   return join_out(g);
 }
 
+cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[2]) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (jacobi) {
+    const JacobiCfg c{jacobi[0], jacobi[1], jacobi[2], jacobi[3], jacobi[4]};
+    const bool ok0 = c.kind == 0 && (c.vx == 1 || c.vx == 2 || c.vx == 4) &&
+                     (c.ty == 4 || c.ty == 8 || (c.ty == 16 && c.vx == 4));
+    const bool ok1 = c.kind == 1 && ((c.vx == 4 && (c.ty == 4 || c.ty == 8 || c.ty == 16) &&
+                                      (c.stages == 4 || c.stages == 6)) ||
+                                     (c.vx == 2 && (c.ty == 8 || c.ty == 16) && c.stages == 4));
+    const bool ok2 = c.kind == 2 && ((c.vx == 4 && ((c.ty == 4 && (c.zc == 1 || c.zc == 2 || c.zc == 4)) ||
+                                                      (c.ty == 8 && c.zc == 1) || (c.ty == 2 && c.zc == 4))) ||
+                                     (c.vx == 2 && c.ty == 4 && c.zc == 2) ||
+                                     (c.vx == 1 && c.ty == 8 && c.zc == 1));
+    if (!(ok0 || ok1 || ok2) || c.zc < 1) return fail(CFD_EINVAL, "unsupported Jacobi config");
+    g->jcfg = c;
+    cfd_status s = refresh_maps(g);
+    if (s != CFD_OK) {
+      g->jcfg.kind = 0;
+      return s;
+    }
+  }
+  if (stencil) {
+    if ((stencil[0] != 4 && stencil[0] != 8) || stencil[1] < 1)
+      return fail(CFD_EINVAL, "unsupported stencil config");
+    g->scfg = StencilCfg{stencil[0], stencil[1]};
+  }
+  invalidate_graph(g);
+  return CFD_OK;
+}
+
+cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  const std::string key = tune_key(g);
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "r")) {
+      char line[512];
+      while (fgets(line, sizeof line, f)) {
+        char k[256];
+        int j[5], st[2];
+        double us = 0.0;
+        if (sscanf(line, "key=%255s jacobi=%d,%d,%d,%d,%d stencil=%d,%d sweep_us=%lf", k, &j[0], &j[1],
+                   &j[2], &j[3], &j[4], &st[0], &st[1], &us) == 9 && key == k) {
+          fclose(f);
+          if (sweep_us) *sweep_us = us;
+          return cfd_set_kernel_config(g, j, st);
+        }
+      }
+      fclose(f);
+    }
+  }
+  if ((s = join_in(g)) != CFD_OK) return s;
+  const Launch L = make_launch(g);
+  CK(g, launch_copy(L, g->scfg, A_P, A_U1));  // keep the solver's warm start
+  std::vector<JacobiCfg> cands;
+  for (int zc : {16, 32, 64}) {
+    for (int ty : {4, 8}) cands.push_back({0, 4, ty, zc, 4});
+    cands.push_back({0, 4, 16, zc, 4});
+    cands.push_back({0, 1, 8, zc, 4});
+  }
+  cands.push_back({0, 2, 8, 32, 4});
+  for (const JacobiCfg& d : {JacobiCfg{2, 4, 4, 1, 0}, JacobiCfg{2, 4, 4, 2, 0}, JacobiCfg{2, 4, 8, 1, 0},
+                             JacobiCfg{2, 4, 2, 4, 0}, JacobiCfg{2, 4, 4, 4, 0}, JacobiCfg{2, 2, 4, 2, 0},
+                             JacobiCfg{2, 1, 8, 1, 0}})
+    cands.push_back(d);
+  for (int zc : {16, 32, 64}) {
+    for (int ty : {4, 8, 16})
+      for (int st : {4, 6}) cands.push_back({1, 4, ty, zc, st});
+    cands.push_back({1, 2, 16, zc, 4});
+  }
+  const JacobiCfg saved = g->jcfg;
+  JacobiCfg best = saved;
+  float best_ms = 1e30f;
+  for (const auto& c : cands) {
+    g->jcfg = c;
+    if (refresh_maps(g) != CFD_OK || (c.kind == 1 && !g->maps_ready)) continue;
+    float ms = 0.f;
+    if ((s = time_region(g, 1, &ms, 0)) != CFD_OK) return s;  // warm-up
+    if ((s = time_region(g, 5, &ms, 0)) != CFD_OK) return s;
+    if (ms < best_ms) {
+      best_ms = ms;
+      best = c;
+    }
+  }
+  g->jcfg = best;
+  if ((s = refresh_maps(g)) != CFD_OK) return s;
+  CK(g, launch_copy(L, g->scfg, A_U1, A_P));
+  StencilCfg sbest = g->scfg;
+  float sbest_ms = 1e30f;
+  for (int ty : {4, 8})
+    for (int zc : {8, 16, 32}) {
+      g->scfg = StencilCfg{ty, zc};
+      float ms = 0.f;
+      if ((s = time_region(g, 1, &ms, 1)) != CFD_OK) return s;
+      if ((s = time_region(g, 3, &ms, 1)) != CFD_OK) return s;
+      if (ms < sbest_ms) {
+        sbest_ms = ms;
+        sbest = g->scfg;
+      }
+    }
+  g->scfg = sbest;
+  invalidate_graph(g);
+  const double us = best_ms * 1000.0 / 10.0;
+  if (sweep_us) *sweep_us = us;
+  if (cache_path) {
+    if (FILE* f = fopen(cache_path, "a")) {
+      fprintf(f, "key=%s jacobi=%d,%d,%d,%d,%d stencil=%d,%d sweep_us=%.3f\n", key.c_str(), best.kind,
+              best.vx, best.ty, best.zc, best.stages, sbest.ty, sbest.zc, us);
+      fclose(f);
+    }
+  }
+  return join_out(g);
+}
+
+cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[2]) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (jacobi) {
+    jacobi[0] = g->jcfg.kind == 1 && !g->maps_ready ? 0 : g->jcfg.kind;
+    jacobi[1] = g->jcfg.vx;
+    jacobi[2] = g->jcfg.ty;
+    jacobi[3] = g->jcfg.zc;
+    jacobi[4] = g->jcfg.stages;
+  }
+  if (stencil) {
+    stencil[0] = g->scfg.ty;
+    stencil[1] = g->scfg.zc;
+  }
+  return CFD_OK;
+}
+
+cfd_status cfd_set_launch_mode(cfd_grid* g, int per_block) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  g->per_block = per_block != 0;
+  invalidate_graph(g);
+  return CFD_OK;
+}
+
 cfd_status cfd_stats(const cfd_grid* g, long long* kernel_launches) {
   if (!g || !kernel_launches) return fail(CFD_EINVAL, "null argument");
   *kernel_launches = g->launches;
@@ -631,30 +950,7 @@ cfd_status cfd_step(cfd_grid* g, double dt, int n) {
   if (!(dt > 0.0) || n < 0) return fail(CFD_EINVAL, "need dt > 0 and n >= 0");
   if (n == 0) return CFD_OK;
   if ((s = join_in(g)) != CFD_OK) return s;
-  if (!g->graph_valid || g->graph_dt != dt) {
-    if (g->gexec) {
-      cudaGraphExecDestroy(g->gexec);
-      g->gexec = nullptr;
-    }
-    CK(g, cudaStreamBeginCapture(g->own, cudaStreamCaptureModeThreadLocal));
-    const long long before = g->launches;
-    cfd_status s1 = enq_rk_stage(g, 1, dt);
-    cfd_status s2 = s1 == CFD_OK ? enq_rk_stage(g, 2, dt) : s1;
-    cudaGraph_t graph = nullptr;
-    cudaError_t e = cudaStreamEndCapture(g->own, &graph);
-    if (s2 != CFD_OK) {
-      if (graph) cudaGraphDestroy(graph);
-      return s2;
-    }
-    if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamEndCapture");
-    e = cudaGraphInstantiate(&g->gexec, graph, 0);
-    cudaGraphDestroy(graph);
-    if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
-    g->graph_valid = true;
-    g->graph_dt = dt;
-    g->graph_nodes = g->launches - before;
-    g->launches = before;
-  }
+  if ((s = ensure_step_graph(g, dt)) != CFD_OK) return s;
   for (int i = 0; i < n; ++i) CK(g, cudaGraphLaunch(g->gexec, g->own));
   g->launches += n * g->graph_nodes;
   g->t += n * dt;
@@ -689,6 +985,195 @@ cfd_status cfd_residual(cfd_grid* g, double* residual) {
   if ((s = join_out(g)) != CFD_OK) return s;
   if (out[3] != 0.0) return fail(CFD_ENONFINITE, "residual is not finite");
   return CFD_OK;
+}
+
+cfd_status cfd_adjoint_step(cfd_grid* g, double dt, const void* const un[3],
+                            const void* const u1[3], double* dnu_accum_dev) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if ((s = adjoint_supported(g)) != CFD_OK) return s;
+  if (!un || !u1 || !dnu_accum_dev || !(dt > 0.0)) return fail(CFD_EINVAL, "bad argument");
+  Ptr3 pn, p1;
+  const size_t shift = interior_bytes(g) - ghost_origin_bytes(g);
+  for (int c = 0; c < 3; ++c) {
+    if (!un[c] || !u1[c]) return fail(CFD_EINVAL, "null state pointer");
+    pn.p[c] = reinterpret_cast<const float*>(static_cast<const char*>(un[c]) + shift);
+    p1.p[c] = reinterpret_cast<const float*>(static_cast<const char*>(u1[c]) + shift);
+  }
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_adjoint_step(g, dt, pn, p1, dnu_accum_dev)) != CFD_OK) return s;
+  return join_out(g);
+}
+
+cfd_status cfd_rollout_bytes(const cfd_grid* g, int nsteps, int seg, size_t* bytes) {
+  if (!g || !bytes || nsteps < 1 || seg < 1) return fail(CFD_EINVAL, "bad argument");
+  const size_t nck = (size_t)(nsteps + seg - 1) / seg;
+  *bytes = g->hb[0].array_bytes * (4 * nck + 6 * (size_t)seg);
+  return CFD_OK;
+}
+
+}  // extern "C"
+
+namespace {
+
+char* store_array(const cfd_grid* g, void* store, size_t slot) {
+  return static_cast<char*>(store) + g->hb[0].array_bytes * slot;
+}
+
+cfd_status copy_arrays(cfd_grid* g, char* const* dst, char* const* src, int n) {
+  for (int i = 0; i < n; ++i)
+    CK(g, cudaMemcpyAsync(dst[i], src[i], g->hb[0].array_bytes, cudaMemcpyDeviceToDevice, g->own));
+  return CFD_OK;
+}
+
+cfd_status ensure_step_graph(cfd_grid* g, double dt) {
+  if (g->graph_valid && g->graph_dt == dt) return CFD_OK;
+  if (g->gexec) {
+    cudaGraphExecDestroy(g->gexec);
+    g->gexec = nullptr;
+  }
+  CK(g, cudaStreamBeginCapture(g->own, cudaStreamCaptureModeThreadLocal));
+  const long long before = g->launches;
+  cfd_status s1 = enq_rk_stage(g, 1, dt);
+  cfd_status s2 = s1 == CFD_OK ? enq_rk_stage(g, 2, dt) : s1;
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->own, &graph);
+  if (s2 != CFD_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s2;
+  }
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&g->gexec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
+  g->graph_valid = true;
+  g->graph_dt = dt;
+  g->graph_nodes = g->launches - before;
+  g->launches = before;
+  return CFD_OK;
+}
+
+// Recompute len steps from the current state, recording (u^n, u1) of step m
+// in store slots; or the len adjoint steps in reverse.  Captured once per
+// (store, dt, len) and replayed.
+cfd_status seg_graph(cfd_grid* g, bool adjoint, int len, int seg, size_t nck, void* store,
+                     double dt, cfd_grid::SegGraph** out) {
+  if (g->seg_store != store || g->seg_dt != dt || g->seg_len != seg) {
+    drop_seg_graphs(g);
+    g->seg_store = store;
+    g->seg_dt = dt;
+    g->seg_len = seg;
+  }
+  cfd_grid::SegGraph* slots = adjoint ? g->adj_graph : g->rec_graph;
+  for (int q = 0; q < 2; ++q)
+    if (slots[q].exec && slots[q].len == len) {
+      *out = &slots[q];
+      return CFD_OK;
+    }
+  cfd_grid::SegGraph* tgt = slots[0].exec ? &slots[1] : &slots[0];
+  if (tgt->exec) cudaGraphExecDestroy(tgt->exec);
+  CK(g, cudaStreamBeginCapture(g->own, cudaStreamCaptureModeThreadLocal));
+  const long long before = g->launches;
+  cfd_status s = CFD_OK;
+  double* nu_acc = reinterpret_cast<double*>(g->base + g->adj_off);
+  const size_t shift = interior_bytes(g);
+  for (int i = 0; i < len && s == CFD_OK; ++i) {
+    const int m = adjoint ? len - 1 - i : i;
+    char* rec[6];
+    for (int c = 0; c < 6; ++c) rec[c] = store_array(g, store, 4 * nck + 6 * (size_t)m + c);
+    if (!adjoint) {
+      char* u[3] = {array_start(g, A_U), array_start(g, A_V), array_start(g, A_W)};
+      char* u1[3] = {array_start(g, A_U1), array_start(g, A_V1), array_start(g, A_W1)};
+      if ((s = copy_arrays(g, rec, u, 3)) != CFD_OK) break;
+      if ((s = enq_rk_stage(g, 1, dt)) != CFD_OK) break;
+      if ((s = copy_arrays(g, rec + 3, u1, 3)) != CFD_OK) break;
+      s = enq_rk_stage(g, 2, dt);
+    } else {
+      Ptr3 pn, p1;
+      for (int c = 0; c < 3; ++c) {
+        pn.p[c] = reinterpret_cast<const float*>(rec[c] + shift);
+        p1.p[c] = reinterpret_cast<const float*>(rec[3 + c] + shift);
+      }
+      s = enq_adjoint_step(g, dt, pn, p1, nu_acc);
+    }
+  }
+  cudaGraph_t graph = nullptr;
+  cudaError_t e = cudaStreamEndCapture(g->own, &graph);
+  if (s != CFD_OK) {
+    if (graph) cudaGraphDestroy(graph);
+    return s;
+  }
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&tgt->exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
+  tgt->nodes = g->launches - before;
+  tgt->len = len;
+  g->launches = before;
+  *out = tgt;
+  return CFD_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+cfd_status cfd_rollout_forward(cfd_grid* g, double dt, int nsteps, int seg, void* store,
+                               size_t bytes) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if ((s = adjoint_supported(g)) != CFD_OK) return s;
+  size_t need = 0;
+  if ((s = cfd_rollout_bytes(g, nsteps, seg, &need)) != CFD_OK) return s;
+  if (!store || bytes < need || !(dt > 0.0)) return fail(CFD_EINVAL, "store too small or bad dt");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = ensure_step_graph(g, dt)) != CFD_OK) return s;
+  char* st[4] = {array_start(g, A_U), array_start(g, A_V), array_start(g, A_W), array_start(g, A_P)};
+  for (int n = 0; n < nsteps; ++n) {
+    if (n % seg == 0) {
+      char* ck[4];
+      for (int c = 0; c < 4; ++c) ck[c] = store_array(g, store, 4 * (size_t)(n / seg) + c);
+      if ((s = copy_arrays(g, ck, st, 4)) != CFD_OK) return s;
+    }
+    CK(g, cudaGraphLaunch(g->gexec, g->own));
+    g->launches += g->graph_nodes;
+  }
+  g->t += nsteps * dt;
+  g->step += nsteps;
+  return join_out(g);
+}
+
+cfd_status cfd_rollout_backward(cfd_grid* g, double dt, int nsteps, int seg, void* store,
+                                size_t bytes, double* dnu) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if ((s = adjoint_supported(g)) != CFD_OK) return s;
+  size_t need = 0;
+  if ((s = cfd_rollout_bytes(g, nsteps, seg, &need)) != CFD_OK) return s;
+  if (!store || bytes < need || !(dt > 0.0)) return fail(CFD_EINVAL, "store too small or bad dt");
+  const size_t nck = (size_t)(nsteps + seg - 1) / seg;
+  if ((s = join_in(g)) != CFD_OK) return s;
+  double* nu_acc = reinterpret_cast<double*>(g->base + g->adj_off);
+  CK(g, cudaMemsetAsync(nu_acc, 0, sizeof(double), g->own));
+  char* st[4] = {array_start(g, A_U), array_start(g, A_V), array_start(g, A_W), array_start(g, A_P)};
+  for (long long sg = (long long)nck - 1; sg >= 0; --sg) {
+    const int n0 = (int)sg * seg, len = std::min(seg, nsteps - n0);
+    char* ck[4];
+    for (int c = 0; c < 4; ++c) ck[c] = store_array(g, store, 4 * (size_t)sg + c);
+    if ((s = copy_arrays(g, st, ck, 4)) != CFD_OK) return s;
+    cfd_grid::SegGraph* rg = nullptr;
+    if ((s = seg_graph(g, false, len, seg, nck, store, dt, &rg)) != CFD_OK) return s;
+    CK(g, cudaGraphLaunch(rg->exec, g->own));
+    g->launches += rg->nodes;
+    cfd_grid::SegGraph* ag = nullptr;
+    if ((s = seg_graph(g, true, len, seg, nck, store, dt, &ag)) != CFD_OK) return s;
+    CK(g, cudaGraphLaunch(ag->exec, g->own));
+    g->launches += ag->nodes;
+  }
+  CK(g, cudaMemcpyAsync(g->h_out, nu_acc, sizeof(double), cudaMemcpyDeviceToHost, g->own));
+  CK(g, cudaStreamSynchronize(g->own));
+  if (dnu) *dnu = g->h_out[0];
+  return join_out(g);
 }
 
 cfd_status cfd_get_state(const cfd_grid* g, double* t, long long* step) {

@@ -1,0 +1,399 @@
+// Weighted Jacobi sweep of the 7-point pressure operator with TMA staging.
+//
+// Same arithmetic as the register/shuffle sweep: p' = p + w((N p - r)/diag - p).
+// A CTA owns a TX x TY column of one block and walks it along z.  One thread
+// issues cp.async.bulk.tensor loads of each z-plane of p (with a one-cell
+// halo in y and a 16-byte-aligned halo in x) and of r into a ring of S
+// shared-memory stages completed through mbarriers; S - 2 planes are in
+// flight while a plane is computed, with no registers held for them.  Each
+// thread owns VX consecutive x cells of one row: it keeps their z-1 and z
+// values in registers, reads z+1, the y neighbours and r from shared memory as
+// VX-wide vectors, and takes the x neighbours from the adjacent lanes by warp
+// shuffle (the row-end lanes read the halo column).  The output is written with
+// plain coalesced stores plus the ghost-on-write images of face cells.
+//
+// Every mbarrier wait is bounded (2 s of %globaltimer); on a timeout the CTA
+// sets the grid's device error flag, waits (bounded) for its own loads still
+// in flight and returns.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+#include <cudaTypedefs.h>
+
+#include <cstring>
+
+#include "cfd_internal.h"
+
+namespace cfd {
+namespace {
+
+__device__ __forceinline__ float tof(float x) { return x; }
+__device__ __forceinline__ float tof(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float tof(__half x) { return __half2float(x); }
+
+template <typename T> __device__ __forceinline__ T cvt(float x);
+template <> __device__ __forceinline__ float cvt<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
+
+template <typename T, int VX> struct alignas(sizeof(T) * VX) Vec { T v[VX]; };
+
+template <int VX, typename T>
+__device__ __forceinline__ void ldv(const T* p, float (&out)[VX]) {
+  const Vec<T, VX> x = *reinterpret_cast<const Vec<T, VX>*>(p);
+#pragma unroll
+  for (int e = 0; e < VX; ++e) out[e] = tof(x.v[e]);
+}
+
+template <typename T, int VX>
+__device__ __forceinline__ void stv(T* p, const float (&in)[VX]) {
+  Vec<T, VX> x;
+#pragma unroll
+  for (int e = 0; e < VX; ++e) x.v[e] = cvt<T>(in[e]);
+  *reinterpret_cast<Vec<T, VX>*>(p) = x;
+}
+
+__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
+
+__device__ __forceinline__ bool locate(const Launch& L, long long t, int tx, int ty, int tz,
+                                       int& b, long long& base, int& i0, int& j0, int& k0) {
+  while (b < L.b0 + L.nblocks) {
+    const int nx = L.blocks[b].n[0], ny = L.blocks[b].n[1], nz = L.blocks[b].n[2];
+    const long long nxT = cdiv(nx, tx), nyT = cdiv(ny, ty), nzT = cdiv(nz, tz);
+    const long long cnt = nxT * nyT * nzT;
+    if (t < base + cnt) {
+      long long l = t - base;
+      i0 = (int)(l % nxT) * tx;
+      l /= nxT;
+      j0 = (int)(l % nyT) * ty;
+      k0 = (int)(l / nyT) * tz;
+      return true;
+    }
+    base += cnt;
+    ++b;
+  }
+  return false;
+}
+
+// ------------------------------------------------------------- PTX helpers
+
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_fence_init() {
+  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ unsigned long long gtimer() {
+  unsigned long long t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+constexpr unsigned long long kWaitLimitNs = 2000000000ull;
+
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  if (mbar_try_wait(bar, parity)) return true;
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait(bar, parity))
+    if (gtimer() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
+                                            int z, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
+      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
+      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
+      : "memory");
+}
+
+template <typename T>
+__device__ __forceinline__ void p_ghost_images(const Launch& L, const BlockDev& B, int dst, int i,
+                                               int j, int k, T val) {
+  const int q[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int face = 2 * d + side;
+      if (q[d] != (side == 0 ? 0 : B.n[d] - 1)) continue;
+      int t[3] = {q[0], q[1], q[2]};
+      const BlockDev* D = &B;
+      if (B.bc[face] == BC_PERIODIC) {
+        D = &L.blocks[B.nbr[face]];
+        t[d] = side == 0 ? D->n[d] : -1;
+      } else {
+        t[d] = side == 0 ? -1 : B.n[d];
+      }
+      T* out = reinterpret_cast<T*>(L.base) + D->org[dst];
+      out[(long long)t[2] * D->pz + (long long)t[1] * D->py + t[0]] = val;
+    }
+  }
+}
+
+template <typename T, int VX, int TY>
+struct TmaGeom {
+  static constexpr int TX = 32 * VX;
+  static constexpr int HX = 16 / (int)sizeof(T);
+  static constexpr int PW = TX + 2 * HX;
+  static constexpr int PH = TY + 2;
+  static constexpr int PBYTES = PW * PH * (int)sizeof(T);
+  static constexpr int RBYTES = TX * TY * (int)sizeof(T);
+  static constexpr int PSTRIDE = (PBYTES + 127) / 128 * 128;
+  static constexpr int RSTRIDE = (RBYTES + 127) / 128 * 128;
+  static constexpr int STAGE = PSTRIDE + RSTRIDE;
+};
+
+template <typename T, int VX, int TY, int S>
+__global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensorMap* maps, int zc,
+                                                        int src_slot, int dst, float omega,
+                                                        float inv_diag) {
+  using Gm = TmaGeom<T, VX, TY>;
+  constexpr int TX = Gm::TX, HX = Gm::HX, PW = Gm::PW;
+  extern __shared__ __align__(128) unsigned char smem[];
+  // S stages of (p box, r box), then the S mbarriers
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S * Gm::STAGE);
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const int tid = ty * 32 + lane;
+  if (smem_u32(smem) & 127u) {  // TMA destinations need 128-byte alignment
+    if (tid == 0) atomicOr(L.err_flag, 4);
+    return;
+  }
+  if (tid == 0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) mbar_init(smem_u32(&full[s]), 1);
+    mbar_fence_init();
+  }
+  __syncthreads();
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  const int g = L.ghost;
+  constexpr int xo = kAlignBytes / (int)sizeof(T);
+  uint32_t parity = 0;
+  int sbase = 0;
+  int blk = L.b0;
+  long long base = 0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, TX, TY, zc, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int k1 = min(k0 + zc, nz);
+    const int np = k1 - k0 + 2;  // planes k0-1 .. k1
+    const CUtensorMap* mp = maps + 3 * blk + src_slot;
+    const CUtensorMap* mr = maps + 3 * blk + 2;
+    const int px = xo + i0 - HX, pyc = g + j0 - 1, rx = xo + i0, ry = g + j0;
+    int next_q = 0;
+    auto issue = [&](int q) {
+      const int s = (sbase + q) % S;
+      const int z = g + k0 - 1 + q;
+      const bool need_r = (q >= 1 && q <= np - 2);
+      const uint32_t bar = smem_u32(&full[s]);
+      mbar_expect_tx(bar, Gm::PBYTES + (need_r ? Gm::RBYTES : 0));
+      tma_load_3d(smem_u32(smem + s * Gm::STAGE), mp, px, pyc, z, bar);
+      if (need_r) tma_load_3d(smem_u32(smem + s * Gm::STAGE + Gm::PSTRIDE), mr, rx, ry, z, bar);
+    };
+    const int first = np < S ? np : S;
+    if (tid == 0)
+      for (int q = 0; q < first; ++q) issue(q);
+    next_q = first;
+    int waited = 0;  // planes 0..waited-1 have completed
+    bool bad = false;
+    auto wait_plane = [&](int q) {
+      const int s = (sbase + q) % S;
+      bad |= !mbar_wait(smem_u32(&full[s]), (parity >> s) & 1u);
+      parity ^= 1u << s;
+      waited = q + 1;
+    };
+    wait_plane(0);
+    wait_plane(1);
+    const int j = j0 + ty;
+    const int xl = lane * VX;                 // first tile-local x of this thread
+    const int row = (ty + 1) * PW + HX + xl;  // its centre in a p box (VX-aligned)
+    float m[VX], c[VX];
+    {
+      const T* P0 = reinterpret_cast<const T*>(smem + ((sbase + 0) % S) * Gm::STAGE);
+      const T* P1 = reinterpret_cast<const T*>(smem + ((sbase + 1) % S) * Gm::STAGE);
+      ldv<VX>(P0 + row, m);
+      ldv<VX>(P1 + row, c);
+    }
+    T* Q = reinterpret_cast<T*>(L.base) + B.org[dst];
+    const int x0 = i0 + xl;
+    const bool full_vec = x0 + VX <= nx;
+    const bool x_face = (x0 == 0) || (x0 <= nx - 1 && nx - 1 < x0 + VX);
+    for (int k = k0; k < k1; ++k) {
+      const int q = k - k0 + 1;
+      wait_plane(q + 1);
+      const T* Pq = reinterpret_cast<const T*>(smem + ((sbase + q) % S) * Gm::STAGE);
+      const T* Pn = reinterpret_cast<const T*>(smem + ((sbase + q + 1) % S) * Gm::STAGE);
+      const T* Rq = reinterpret_cast<const T*>(smem + ((sbase + q) % S) * Gm::STAGE + Gm::PSTRIDE);
+      float zp[VX], up[VX], dn[VX], rr[VX];
+      ldv<VX>(Pn + row, zp);
+      ldv<VX>(Pq + row + PW, up);
+      ldv<VX>(Pq + row - PW, dn);
+      ldv<VX>(Rq + ty * TX + xl, rr);
+      float left = __shfl_up_sync(0xffffffffu, c[VX - 1], 1);
+      float right = __shfl_down_sync(0xffffffffu, c[0], 1);
+      if (lane == 0) left = tof(Pq[row - 1]);
+      if (lane == 31) right = tof(Pq[row + VX]);
+      float out[VX];
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        const float xm = e == 0 ? left : c[e - 1];
+        const float xp = e == VX - 1 ? right : c[e + 1];
+        const float nb = (xm + xp) * cx + (dn[e] + up[e]) * cy + (m[e] + zp[e]) * cz;
+        out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+      }
+      if (j < ny && x0 < nx) {
+        T* qrow = Q + (long long)k * B.pz + (long long)j * B.py + x0;
+        if (full_vec) {
+          stv<T, VX>(qrow, out);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VX; ++e)
+            if (x0 + e < nx) qrow[e] = cvt<T>(out[e]);
+        }
+        if (x_face || j == 0 || j == ny - 1 || k == 0 || k == nz - 1) {
+#pragma unroll
+          for (int e = 0; e < VX; ++e)
+            if (x0 + e < nx) p_ghost_images<T>(L, B, dst, x0 + e, j, k, cvt<T>(out[e]));
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        m[e] = c[e];
+        c[e] = zp[e];
+      }
+      if (__syncthreads_or(bad)) {
+        // a plane never arrived: flag it, drain our own loads, give up
+        if (tid == 0) {
+          atomicOr(L.err_flag, 2);
+          for (int qq = waited; qq < next_q; ++qq) {
+            const int s = (sbase + qq) % S;
+            mbar_wait(smem_u32(&full[s]), (parity >> s) & 1u);
+            parity ^= 1u << s;
+          }
+        }
+        __syncthreads();
+        return;
+      }
+      // planes 0..q are no longer read: refill their stages
+      const int limit = q + S;
+      if (tid == 0)
+        for (int qq = next_q; qq < np && qq <= limit; ++qq) issue(qq);
+      next_q = max(next_q, min(np, limit + 1));
+    }
+    sbase = (sbase + np) % S;
+  }
+}
+
+template <typename T, int VX, int TY, int S>
+cudaError_t run(const Launch& L, const JacobiCfg& c, const void* maps, int src_slot, int dst,
+                float omega, float inv_diag) {
+  using Gm = TmaGeom<T, VX, TY>;
+  auto kern = k_jacobi_tma<T, VX, TY, S>;
+  const int smem = S * Gm::STAGE + 8 * S;
+  static int occ = -1;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * TY, smem) != cudaSuccess || occ < 1)
+      occ = 1;
+  }
+  const long long tiles = count_tiles(L, Gm::TX, TY, c.zc);
+  long long grid = (long long)L.sms * occ;
+  if (tiles < grid) grid = tiles;
+  kern<<<(unsigned)(grid > 0 ? grid : 1), dim3(32, TY), smem, L.stream>>>(
+      L, static_cast<const CUtensorMap*>(maps), c.zc, src_slot, dst, omega, inv_diag);
+  return cudaGetLastError();
+}
+
+PFN_cuTensorMapEncodeTiled_v12000 encoder() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  if (!fn) {
+    void* p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault,
+                                         &q) == cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  }
+  return fn;
+}
+
+}  // namespace
+
+int tma_box_x(int dtype, int vx, int halo) {
+  const int es = dtype == 0 ? 4 : 2;
+  return 32 * vx + (halo ? 2 * (16 / es) : 0);
+}
+
+bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int dtype,
+                        const JacobiCfg& c) {
+  auto enc = encoder();
+  if (!enc) return false;
+  const int es = dtype == 0 ? 4 : 2;
+  const CUtensorMapDataType dt = dtype == 0 ? CU_TENSOR_MAP_DATA_TYPE_FLOAT32
+                                 : dtype == 1 ? CU_TENSOR_MAP_DATA_TYPE_BFLOAT16
+                                              : CU_TENSOR_MAP_DATA_TYPE_FLOAT16;
+  CUtensorMap* maps = static_cast<CUtensorMap*>(out_host);
+  for (int a = 0; a < narrays; ++a) {
+    const TmaArray& A = arrays[a];
+    const bool is_r = (a % 3) == 2;
+    cuuint64_t dims[3] = {(cuuint64_t)A.row_elems, (cuuint64_t)A.rows, (cuuint64_t)A.planes};
+    cuuint64_t strides[2] = {(cuuint64_t)A.row_elems * es, (cuuint64_t)A.row_elems * A.rows * es};
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_x(dtype, c.vx, !is_r),
+                         (cuuint32_t)(c.ty + (is_r ? 0 : 2)), 1};
+    cuuint32_t estr[3] = {1, 1, 1};
+    memset(&maps[a], 0, sizeof(CUtensorMap));
+    CUresult r = enc(&maps[a], dt, 3, A.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
+    if (r != CUDA_SUCCESS) return false;
+  }
+  return true;
+}
+
+#define CFD_DISPATCH_T(dtype, ...)                           \
+  switch (dtype) {                                           \
+    case 0: { using T = float; __VA_ARGS__; } break;         \
+    case 1: { using T = __nv_bfloat16; __VA_ARGS__; } break; \
+    default: { using T = __half; __VA_ARGS__; } break;       \
+  }
+
+cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* maps_dev,
+                              int src_slot, int dst, float omega) {
+  const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+  cudaError_t e = cudaErrorInvalidValue;
+  CFD_DISPATCH_T(L.dtype, {
+    if (c.vx == 4 && c.ty == 4 && c.stages == 4) e = run<T, 4, 4, 4>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 4) e = run<T, 4, 4, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 8 && c.stages == 4) e = run<T, 4, 8, 4>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 8) e = run<T, 4, 8, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 16 && c.stages == 4) e = run<T, 4, 16, 4>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 16) e = run<T, 4, 16, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.vx == 2 && c.ty == 16) e = run<T, 2, 16, 4>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else e = run<T, 2, 8, 4>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+  });
+  return e;
+}
+
+}  // namespace cfd

@@ -60,7 +60,7 @@ __device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
 // forward, since every CTA visits increasing t.
 __device__ __forceinline__ bool locate(const Launch& L, long long t, int tx, int ty, int tz,
                                        int& b, long long& base, int& i0, int& j0, int& k0) {
-  while (b < L.nblocks) {
+  while (b < L.b0 + L.nblocks) {
     const int nx = L.blocks[b].n[0], ny = L.blocks[b].n[1], nz = L.blocks[b].n[2];
     const long long nxT = cdiv(nx, tx), nyT = cdiv(ny, ty), nzT = cdiv(nz, tz);
     const long long cnt = nxT * nyT * nzT;
@@ -234,7 +234,7 @@ __global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Se
                                                    Set3 ys, float cdt, Set3 os, float nu) {
   const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
   const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
-  int blk = 0;
+  int blk = L.b0;
   long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Se
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, float inv_cdt,
                                                  int r_arr) {
-  int blk = 0;
+  int blk = L.b0;
   long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
@@ -293,7 +293,7 @@ __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, floa
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_project(Launch L, int zc, Set3 ws, int p_arr,
                                                      float cdt, Set3 os) {
-  int blk = 0;
+  int blk = L.b0;
   long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
@@ -322,7 +322,7 @@ __global__ void __launch_bounds__(32 * TY) k_project(Launch L, int zc, Set3 ws, 
 
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_copy(Launch L, int zc, int src, int dst) {
-  int blk = 0;
+  int blk = L.b0;
   long long base = 0;
   const int g = L.ghost;
   for (long long t = blockIdx.x;; t += gridDim.x) {
@@ -393,7 +393,7 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, i
   __shared__ __align__(16) float sm[TY + 2][TX];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
-  int blk = 0;
+  int blk = L.b0;
   long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
@@ -535,6 +535,79 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, i
   }
 }
 
+// Direct sweep: one thread per VX consecutive cells of one row, every
+// neighbour loaded straight from global memory (x neighbours by shuffle).
+// No shared memory and no barrier: each CTA (32 x TY x TZ threads) covers a
+// (32 VX) x TY x TZ tile and all its loads are independent, so the memory
+// system sees as many requests in flight as an elementwise kernel; the
+// y and z neighbours are served by L1/L2 (neighbouring rows and planes are
+// read by the same or nearby CTAs).
+
+template <typename T, int VX, int TY, int TZ>
+__global__ void __launch_bounds__(32 * TY * TZ) k_jacobi_direct(Launch L, int src, int dst,
+                                                               int r_arr, float omega,
+                                                               float inv_diag) {
+  constexpr int TX = 32 * VX;
+  const int lane = threadIdx.x;
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  int blk = L.b0;
+  long long base = 0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!locate(L, t, TX, TY, TZ, blk, base, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int j = j0 + threadIdx.y, k = k0 + threadIdx.z;
+    if (j >= ny || k >= nz) continue;  // uniform per warp: a warp is one row
+    const int py = B.py;
+    const long long pz = B.pz;
+    const T* P = reinterpret_cast<const T*>(L.base) + B.org[src];
+    const T* R = reinterpret_cast<const T*>(L.base) + B.org[r_arr];
+    const int i = i0 + lane * VX;
+    const long long rowo = (long long)k * pz + (long long)j * py;
+    const long long o = rowo + i;
+    float c[VX], ym[VX], yp[VX], zm[VX], zp[VX], rr[VX];
+#pragma unroll
+    for (int e = 0; e < VX; ++e) c[e] = ym[e] = yp[e] = zm[e] = zp[e] = rr[e] = 0.f;
+    if (i <= nx) {  // columns up to nx (first ghost) stay inside the row
+      ldv<VX>(P + o, c);
+      ldv<VX>(P + o - py, ym);
+      ldv<VX>(P + o + py, yp);
+      ldv<VX>(P + o - pz, zm);
+      ldv<VX>(P + o + pz, zp);
+      ldv<VX>(R + o, rr);
+    }
+    float left = __shfl_up_sync(0xffffffffu, c[VX - 1], 1);
+    float right = __shfl_down_sync(0xffffffffu, c[0], 1);
+    if (lane == 0) left = ldf<T>(P + rowo + i0 - 1);
+    if (lane == 31) right = (i0 + TX <= nx) ? ldf<T>(P + rowo + i0 + TX) : 0.f;
+    if (i >= nx) continue;
+    float out[VX];
+#pragma unroll
+    for (int e = 0; e < VX; ++e) {
+      const float xm = e == 0 ? left : c[e - 1];
+      const float xp = e == VX - 1 ? right : c[e + 1];
+      const float nb = (xm + xp) * cx + (ym[e] + yp[e]) * cy + (zm[e] + zp[e]) * cz;
+      out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+    }
+    T* qrow = wptr<T>(L, B, dst) + o;
+    if (i + VX <= nx) {
+      stv<T, VX>(qrow, out);
+    } else {
+#pragma unroll
+      for (int e = 0; e < VX; ++e)
+        if (i + e < nx) qrow[e] = cvt<T>(out[e]);
+    }
+    const bool face = (i == 0) || (nx - 1 < i + VX) || j == 0 || j == ny - 1 || k == 0 ||
+                      k == nz - 1;
+    if (face) {
+#pragma unroll
+      for (int e = 0; e < VX; ++e)
+        if (i + e < nx) p_ghost_images<T>(L, B, dst, i + e, j, k, cvt<T>(out[e]));
+    }
+  }
+}
+
 // --------------------------------------------------------------- reductions
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -585,7 +658,7 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
                                                     int p_arr, int r_arr, double* partials) {
   __shared__ double sh[TY][4];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
-  int blk = 0;
+  int blk = L.b0;
   long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
@@ -657,9 +730,8 @@ int occupancy(K kernel, int threads) {
   return n > 0 ? n : 1;
 }
 
-template <typename K>
-unsigned grid_for(const Launch& L, K kernel, int threads, long long tiles) {
-  const long long cap = (long long)L.sms * occupancy(kernel, threads);
+unsigned grid_for(const Launch& L, int occ, long long tiles) {
+  const long long cap = (long long)L.sms * occ;
   long long gsz = tiles < cap ? tiles : cap;
   return (unsigned)(gsz > 0 ? gsz : 1);
 }
@@ -670,7 +742,7 @@ Set3 mk3(const int* s) { return Set3{{s[0], s[1], s[2]}}; }
 
 long long count_tiles(const Launch& L, int tx, int ty, int tz) {
   long long n = 0;
-  for (int b = 0; b < L.nblocks; ++b) {
+  for (int b = L.b0; b < L.b0 + L.nblocks; ++b) {
     const int* d = L.hn[b];
     n += (long long)((d[0] + tx - 1) / tx) * ((d[1] + ty - 1) / ty) * ((d[2] + tz - 1) / tz);
   }
@@ -702,7 +774,8 @@ static void run_stage(const Launch& L, int zc, float a, Set3 xs, float b, Set3 y
                       Set3 os, float nu) {
   const long long tiles = count_tiles(L, 32, TY, zc);
   auto kern = k_stage<T, ORDER, TY>;
-  kern<<<grid_for(L, kern, 32 * TY, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
+  static const int occ = occupancy(kern, 32 * TY);
+  kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
 }
 
 cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float a,
@@ -726,7 +799,8 @@ cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* w
   const long long tiles = count_tiles(L, 32, 8, c.zc);
   CFD_DISPATCH_T(L.dtype, {
     auto kern = k_div<T, 8>;
-    kern<<<grid_for(L, kern, 256, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, mk3(wset), inv_cdt, r_arr);
+    static const int occ = occupancy(kern, 256);
+    kern<<<grid_for(L, occ, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, mk3(wset), inv_cdt, r_arr);
   });
   return cudaGetLastError();
 }
@@ -736,7 +810,8 @@ cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset
   const long long tiles = count_tiles(L, 32, 8, c.zc);
   CFD_DISPATCH_T(L.dtype, {
     auto kern = k_project<T, 8>;
-    kern<<<grid_for(L, kern, 256, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, mk3(wset), p_arr, cdt, mk3(oset));
+    static const int occ = occupancy(kern, 256);
+    kern<<<grid_for(L, occ, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, mk3(wset), p_arr, cdt, mk3(oset));
   });
   return cudaGetLastError();
 }
@@ -745,7 +820,8 @@ cudaError_t launch_copy(const Launch& L, const StencilCfg& c, int src, int dst) 
   const long long tiles = count_tiles(L, 32, 8, c.zc);
   CFD_DISPATCH_T(L.dtype, {
     auto kern = k_copy<T, 8>;
-    kern<<<grid_for(L, kern, 256, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, src, dst);
+    static const int occ = occupancy(kern, 256);
+    kern<<<grid_for(L, occ, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, src, dst);
   });
   return cudaGetLastError();
 }
@@ -755,7 +831,8 @@ static void run_jacobi(const Launch& L, int zc, int src, int dst, int r_arr, flo
                        float inv_diag) {
   const long long tiles = count_tiles(L, 32 * VX, TY, zc);
   auto kern = k_jacobi<T, VX, TY>;
-  kern<<<grid_for(L, kern, 32 * TY, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, src, dst, r_arr, omega, inv_diag);
+  static const int occ = occupancy(kern, 32 * TY);
+  kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, src, dst, r_arr, omega, inv_diag);
 }
 
 cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
@@ -774,6 +851,33 @@ cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst,
       if (c.ty == 4) run_jacobi<T, 1, 4>(L, c.zc, src, dst, r_arr, omega, inv_diag);
       else run_jacobi<T, 1, 8>(L, c.zc, src, dst, r_arr, omega, inv_diag);
     }
+  });
+  return cudaGetLastError();
+}
+
+template <typename T, int VX, int TY, int TZ>
+static void run_jacobi_direct(const Launch& L, int src, int dst, int r_arr, float omega,
+                              float inv_diag) {
+  const long long tiles = count_tiles(L, 32 * VX, TY, TZ);
+  auto kern = k_jacobi_direct<T, VX, TY, TZ>;
+  static const int occ = occupancy(kern, 32 * TY * TZ);
+  // enough CTAs for several waves; each walks tiles with a grid stride
+  const long long cap = (long long)L.sms * occ * 16;
+  const unsigned grid = (unsigned)(tiles < cap ? tiles : cap);
+  kern<<<grid > 0 ? grid : 1, dim3(32, TY, TZ), 0, L.stream>>>(L, src, dst, r_arr, omega, inv_diag);
+}
+
+cudaError_t launch_jacobi_direct(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                                 float omega) {
+  const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+  CFD_DISPATCH_T(L.dtype, {
+    if (c.vx == 4 && c.ty == 4 && c.zc == 2) run_jacobi_direct<T, 4, 4, 2>(L, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 8 && c.zc == 1) run_jacobi_direct<T, 4, 8, 1>(L, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 2 && c.zc == 4) run_jacobi_direct<T, 4, 2, 4>(L, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 4 && c.ty == 4 && c.zc == 4) run_jacobi_direct<T, 4, 4, 4>(L, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 2 && c.ty == 4 && c.zc == 2) run_jacobi_direct<T, 2, 4, 2>(L, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 1 && c.ty == 8 && c.zc == 1) run_jacobi_direct<T, 1, 8, 1>(L, src, dst, r_arr, omega, inv_diag);
+    else run_jacobi_direct<T, 4, 4, 1>(L, src, dst, r_arr, omega, inv_diag);
   });
   return cudaGetLastError();
 }

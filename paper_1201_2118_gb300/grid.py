@@ -13,7 +13,8 @@ import numpy as np
 
 from ._lib import call, ints, doubles, c_void_p, c_size_t, c_ll, c_int, c_double
 
-U, V, W, P, WU, WV, WW, U1, V1, W1, P2, R = range(12)
+U, V, W, P, WU, WV, WW, U1, V1, W1, P2, R, LU, LV, LW, LP = range(16)
+NUM_ARRAYS = 16
 SET_U, SET_W, SET_U1 = 0, 1, 2
 PERIODIC, WALL = 0, 1
 DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
@@ -131,7 +132,7 @@ class Grid:
         """Sets every byte of every array to one value (NaN canaries in tests)."""
         with self.torch.cuda.stream(self.stream):
             for b in range(self.nblocks):
-                for a in range(12):
+                for a in range(NUM_ARRAYS):
                     self.array(a, b).fill_(value)
 
     # --------------------------------------------------------------- setup
@@ -171,6 +172,24 @@ class Grid:
         call("cfd_stats", self.handle, ctypes.byref(n))
         return n.value
 
+    def set_kernel_config(self, jacobi=None, stencil=None):
+        call("cfd_set_kernel_config", self.handle, ints(*jacobi) if jacobi else None,
+             ints(*stencil) if stencil else None)
+
+    def set_launch_mode(self, per_block: bool):
+        call("cfd_set_launch_mode", self.handle, 1 if per_block else 0)
+
+    def kernel_config(self):
+        j, s = (c_int * 5)(), (c_int * 2)()
+        call("cfd_get_kernel_config", self.handle, j, s)
+        return tuple(j), tuple(s)
+
+    def autotune(self, cache_path=None) -> float:
+        us = c_double()
+        call("cfd_autotune", self.handle, cache_path.encode() if cache_path else None,
+             ctypes.byref(us))
+        return us.value
+
     def project(self, c_dt: float, out_set: int):
         call("cfd_project", self.handle, float(c_dt), int(out_set))
 
@@ -194,6 +213,25 @@ class Grid:
     def copy_interior(self, array_id: int, host_ptr: int, to_device: bool, block: int = 0):
         call("cfd_copy_interior", self.handle, int(block), int(array_id), c_void_p(host_ptr),
              1 if to_device else 0)
+
+    def adjoint_step(self, dt: float, un_ptrs, u1_ptrs, dnu_dev_ptr: int):
+        call("cfd_adjoint_step", self.handle, float(dt), (c_void_p * 3)(*un_ptrs),
+             (c_void_p * 3)(*u1_ptrs), ctypes.cast(c_void_p(dnu_dev_ptr), ctypes.POINTER(c_double)))
+
+    def rollout_bytes(self, nsteps: int, seg: int) -> int:
+        n = c_size_t()
+        call("cfd_rollout_bytes", self.handle, int(nsteps), int(seg), ctypes.byref(n))
+        return n.value
+
+    def rollout_forward(self, dt, nsteps, seg, store_ptr, nbytes):
+        call("cfd_rollout_forward", self.handle, float(dt), int(nsteps), int(seg),
+             c_void_p(store_ptr), int(nbytes))
+
+    def rollout_backward(self, dt, nsteps, seg, store_ptr, nbytes) -> float:
+        d = c_double()
+        call("cfd_rollout_backward", self.handle, float(dt), int(nsteps), int(seg),
+             c_void_p(store_ptr), int(nbytes), ctypes.byref(d))
+        return d.value
 
     def check(self):
         call("cfd_check", self.handle)
