@@ -53,6 +53,8 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the reduced-precision, block-set and adjoint comparisons")
     ap.add_argument("--precision-steps", type=int, default=20)
+    ap.add_argument("--tune-cache", default=None,
+                    help="autotuner cache file (reused when it holds this GPU and grid)")
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
@@ -368,7 +370,7 @@ def run_gpu(a):
     g.set_cavity(1.0)
     g.set_params(cfg["nu"], cfg["jacobi_iters"], 1.0, cfg["order"])
     g.upload(workloads.ldc_noise(n, seed=cfg["seed"]))
-    g.autotune(None)
+    g.autotune(a.tune_cache)
     jcfg = g.kernel_config()
 
     def barrier():

@@ -240,11 +240,18 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
  * vx 2 with ty in {8,16},
  * stages in {4,6} shared-memory planes), kind 2 the direct sweep without
  * shared memory ((vx, ty, zc) in {(4,4,1), (4,4,2), (4,4,4), (4,8,1), (4,2,4),
- * (2,4,2), (1,8,1)}, zc = z-planes per CTA); zc = z-planes per tile.
- * stencil = {ty in {4,8}, zc} for the point kernels.  NULL leaves a part
- * unchanged.  Results do not depend on the variant. */
-cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[2]);
-cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[2]);
+ * (2,4,2), (1,8,1)}, zc = z-planes per CTA), kind 3 the cp.async-staged
+ * sweep (vx 4 for FP32, 8 for 16-bit storage; ty in {4,8} with stages in
+ * {5,6}, or ty 2 with 6 stages), kind 4 the warp-streaming sweep (ty 4;
+ * vx 4 with stages = planes prefetched ahead in {1,2,3}, or vx in {1,2} with
+ * stages in {2,3}); zc = z-planes per tile.
+ * stencil = {ty in {4,8}, zc, tile_tz in {0,2,4}} for the point kernels: rows
+ * per CTA, z chunk, and for the RHS + stage kernel either neighbour reads
+ * through L1 (tile_tz 0) or a shared-memory box of 32 x 8 x tile_tz cells
+ * plus halo.  NULL leaves a part unchanged.  Results do not depend on the
+ * variant. */
+cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[3]);
+cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[3]);
 
 /* Times the candidate variants on this grid (overwrites the work arrays,
  * keeps U and P) and selects the fastest; with cache_path, reuses or

@@ -15,33 +15,13 @@
 #include <cuda_fp16.h>
 
 #include "cfd_internal.h"
+#include "tiles.cuh"
 
 namespace cfd {
 namespace {
 
 __device__ __forceinline__ float ldg(const float* p) { return __ldg(p); }
 
-__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
-
-__device__ __forceinline__ bool locate(const Launch& L, long long t, int tx, int ty, int tz,
-                                       int& b, long long& base, int& i0, int& j0, int& k0) {
-  while (b < L.b0 + L.nblocks) {
-    const int nx = L.blocks[b].n[0], ny = L.blocks[b].n[1], nz = L.blocks[b].n[2];
-    const long long nxT = cdiv(nx, tx), nyT = cdiv(ny, ty), nzT = cdiv(nz, tz);
-    const long long cnt = nxT * nyT * nzT;
-    if (t < base + cnt) {
-      long long l = t - base;
-      i0 = (int)(l % nxT) * tx;
-      l /= nxT;
-      j0 = (int)(l % nyT) * ty;
-      k0 = (int)(l / nyT) * tz;
-      return true;
-    }
-    base += cnt;
-    ++b;
-  }
-  return false;
-}
 
 struct F3 {
   const float* p;
@@ -58,11 +38,12 @@ constexpr int kTY = 8, kZC = 16;
 // Jacobi right-hand side R = -(diag/w) lam_p2.
 __global__ void __launch_bounds__(32 * kTY) k_adj_proj(Launch L, AdjSet lam, int lp, float c_dt,
                                                        float r_scale, int p_out, int r_out) {
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, kTY, kZC);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, kTY, kZC, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, kTY, kZC, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
@@ -86,11 +67,12 @@ __global__ void __launch_bounds__(32 * kTY) k_adj_proj(Launch L, AdjSet lam, int
 // lam_W = lam_u + coef G b_K (coef = (w/diag)/c_dt);  lam_p = b_{K+1} - b_K.
 __global__ void __launch_bounds__(32 * kTY) k_adj_wp(Launch L, AdjSet lam, int bk, int bk1,
                                                      float coef, AdjSet wout, int lp) {
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, kTY, kZC);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, kTY, kZC, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, kTY, kZC, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
@@ -187,11 +169,12 @@ __global__ void __launch_bounds__(32 * kTY) k_adj_stage(Launch L, AdjSet lam_set
   const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
   const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
   double dot = 0.0;
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, kTY, kZC);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, kTY, kZC, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, kTY, kZC, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;

@@ -41,6 +41,8 @@ struct BlockDev {
   float wall[6][3];            // wall velocity per face
 };
 
+static_assert(sizeof(BlockDev) % 8 == 0, "the block table is copied as words");
+
 // What every launch needs.
 struct Launch {
   const BlockDev* blocks;      // device table (all blocks)
@@ -62,8 +64,14 @@ struct Launch {
 //   kind 0: register/shuffle sweep (any block size, plain loads)
 //   kind 1: TMA-staged sweep (tensor maps per block, S-stage mbarrier ring)
 //   kind 2: direct sweep (no shared memory; zc = z-planes per CTA, TZ)
+//   kind 3: cp.async-staged sweep (per-thread async copies, S-stage ring)
+//   kind 4: warp-streaming sweep (independent warps, register ring of
+//           stages = planes prefetched ahead)
 struct JacobiCfg { int kind, vx, ty, zc, stages; };
-struct StencilCfg { int ty, zc; };      // rows per CTA (32 x ty threads), z chunk
+// Point kernels: rows per CTA (32 x ty threads) and z chunk; the RHS + stage
+// kernel either reads neighbours through L1 (tile_tz = 0) or from a
+// shared-memory box of 32 x 8 x tile_tz cells plus halo (tile_tz = 2 or 4).
+struct StencilCfg { int ty, zc, tile_tz; };
 
 // One array as a 3D tensor for TMA: start of the allocation, row length
 // (the row pitch, elements), rows per plane and planes.
@@ -101,6 +109,10 @@ cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* w
                               float inv_cdt, int r_arr);
 cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
                           float omega);
+cudaError_t launch_jacobi_warp(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                               float omega);
+cudaError_t launch_jacobi_async(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                                float omega);
 cudaError_t launch_jacobi_direct(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
                                  float omega);
 cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset, int p_arr,

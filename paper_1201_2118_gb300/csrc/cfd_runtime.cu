@@ -82,7 +82,7 @@ struct cfd_grid {
   bool sticky = false;
 
   JacobiCfg jcfg{0, 4, 8, 32, 4};
-  StencilCfg scfg{8, 16};
+  StencilCfg scfg{8, 16, 0};
   bool per_block = false;  // baseline mode: one launch per block per stencil kernel
 
   cudaGraphExec_t gexec = nullptr;
@@ -151,6 +151,7 @@ void plan_layout(cfd_grid* g) {
     b.first_byte = off;
     off += b.array_bytes * kNumArrays;
   }
+  off += 256;  // tail pad: a 4-byte halo copy next to the very last row stays inside
   g->bytes = off;
   // ghost-cell enumeration prefix (z-slabs, y-slabs, x-slabs per block)
   g->ghost_prefix.assign(g->nblocks + 1, 0);
@@ -336,7 +337,7 @@ cfd_status enq_ghost(cfd_grid* g, unsigned mask) {
   const Launch L = make_launch(g);
   CK(g, launch_ghost(L, arrs, n, reinterpret_cast<const long long*>(g->base + g->prefix_off),
                      g->ghost_total));
-  g->launches += (n + 3) / 4;
+  g->launches += n > 0 ? 1 : 0;
   return CFD_OK;
 }
 
@@ -357,6 +358,8 @@ cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst) {
     return launch_jacobi_tma(L, g->jcfg, g->base + g->maps_off, src == A_P ? 0 : 1, dst,
                              (float)g->omega);
   if (g->jcfg.kind == 2) return launch_jacobi_direct(L, g->jcfg, src, dst, A_R, (float)g->omega);
+  if (g->jcfg.kind == 3) return launch_jacobi_async(L, g->jcfg, src, dst, A_R, (float)g->omega);
+  if (g->jcfg.kind == 4) return launch_jacobi_warp(L, g->jcfg, src, dst, A_R, (float)g->omega);
   return launch_jacobi(L, g->jcfg, src, dst, A_R, (float)g->omega);
 }
 
@@ -778,7 +781,7 @@ cfd_status cfd_jacobi(cfd_grid* g, int iters) {
   return join_out(g);
 }
 
-cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[2]) {
+cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[3]) {
   if (!g) return fail(CFD_EINVAL, "null grid");
   if (jacobi) {
     const JacobiCfg c{jacobi[0], jacobi[1], jacobi[2], jacobi[3], jacobi[4]};
@@ -791,7 +794,13 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
                                                       (c.ty == 8 && c.zc == 1) || (c.ty == 2 && c.zc == 4))) ||
                                      (c.vx == 2 && c.ty == 4 && c.zc == 2) ||
                                      (c.vx == 1 && c.ty == 8 && c.zc == 1));
-    if (!(ok0 || ok1 || ok2) || c.zc < 1) return fail(CFD_EINVAL, "unsupported Jacobi config");
+    const bool ok3 = c.kind == 3 && c.vx == (g->dtype == CFD_F32 ? 4 : 8) &&
+                     (((c.ty == 4 || c.ty == 8) && (c.stages == 5 || c.stages == 6)) ||
+                      (c.ty == 2 && c.stages == 6));
+    const bool ok4 = c.kind == 4 && c.ty == 4 &&
+                     ((c.vx == 4 && c.stages >= 1 && c.stages <= 3) ||
+                      ((c.vx == 1 || c.vx == 2) && (c.stages == 2 || c.stages == 3)));
+    if (!(ok0 || ok1 || ok2 || ok3 || ok4) || c.zc < 1) return fail(CFD_EINVAL, "unsupported Jacobi config");
     g->jcfg = c;
     cfd_status s = refresh_maps(g);
     if (s != CFD_OK) {
@@ -800,9 +809,10 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
     }
   }
   if (stencil) {
-    if ((stencil[0] != 4 && stencil[0] != 8) || stencil[1] < 1)
+    if ((stencil[0] != 4 && stencil[0] != 8) || stencil[1] < 1 ||
+        (stencil[2] != 0 && stencil[2] != 2 && stencil[2] != 4))
       return fail(CFD_EINVAL, "unsupported stencil config");
-    g->scfg = StencilCfg{stencil[0], stencil[1]};
+    g->scfg = StencilCfg{stencil[0], stencil[1], stencil[2]};
   }
   invalidate_graph(g);
   return CFD_OK;
@@ -817,10 +827,10 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
       char line[512];
       while (fgets(line, sizeof line, f)) {
         char k[256];
-        int j[5], st[2];
+        int j[5], st[3];
         double us = 0.0;
-        if (sscanf(line, "key=%255s jacobi=%d,%d,%d,%d,%d stencil=%d,%d sweep_us=%lf", k, &j[0], &j[1],
-                   &j[2], &j[3], &j[4], &st[0], &st[1], &us) == 9 && key == k) {
+        if (sscanf(line, "key=%255s jacobi=%d,%d,%d,%d,%d stencil=%d,%d,%d sweep_us=%lf", k, &j[0],
+                   &j[1], &j[2], &j[3], &j[4], &st[0], &st[1], &st[2], &us) == 10 && key == k) {
           fclose(f);
           if (sweep_us) *sweep_us = us;
           return cfd_set_kernel_config(g, j, st);
@@ -839,6 +849,17 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
     cands.push_back({0, 1, 8, zc, 4});
   }
   cands.push_back({0, 2, 8, 32, 4});
+  for (int zc : {8, 16, 32, 64})
+    for (const JacobiCfg& d : {JacobiCfg{4, 4, 4, zc, 1}, JacobiCfg{4, 4, 4, zc, 2},
+                               JacobiCfg{4, 4, 4, zc, 3}, JacobiCfg{4, 2, 4, zc, 2},
+                               JacobiCfg{4, 1, 4, zc, 2}, JacobiCfg{4, 1, 4, zc, 3}})
+      cands.push_back(d);
+  const int avx = g->dtype == CFD_F32 ? 4 : 8;
+  for (int zc : {16, 32, 64})
+    for (const JacobiCfg& d : {JacobiCfg{3, avx, 4, zc, 5}, JacobiCfg{3, avx, 4, zc, 6},
+                               JacobiCfg{3, avx, 8, zc, 5}, JacobiCfg{3, avx, 8, zc, 6},
+                               JacobiCfg{3, avx, 2, zc, 6}})
+      cands.push_back(d);
   for (const JacobiCfg& d : {JacobiCfg{2, 4, 4, 1, 0}, JacobiCfg{2, 4, 4, 2, 0}, JacobiCfg{2, 4, 8, 1, 0},
                              JacobiCfg{2, 4, 2, 4, 0}, JacobiCfg{2, 4, 4, 4, 0}, JacobiCfg{2, 2, 4, 2, 0},
                              JacobiCfg{2, 1, 8, 1, 0}})
@@ -867,9 +888,10 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   CK(g, launch_copy(L, g->scfg, A_U1, A_P));
   StencilCfg sbest = g->scfg;
   float sbest_ms = 1e30f;
+  for (int tz : {0, 2, 4})
   for (int ty : {4, 8})
     for (int zc : {8, 16, 32}) {
-      g->scfg = StencilCfg{ty, zc};
+      g->scfg = StencilCfg{ty, zc, tz};
       float ms = 0.f;
       if ((s = time_region(g, 1, &ms, 1)) != CFD_OK) return s;
       if ((s = time_region(g, 3, &ms, 1)) != CFD_OK) return s;
@@ -884,15 +906,15 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   if (sweep_us) *sweep_us = us;
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "a")) {
-      fprintf(f, "key=%s jacobi=%d,%d,%d,%d,%d stencil=%d,%d sweep_us=%.3f\n", key.c_str(), best.kind,
-              best.vx, best.ty, best.zc, best.stages, sbest.ty, sbest.zc, us);
+      fprintf(f, "key=%s jacobi=%d,%d,%d,%d,%d stencil=%d,%d,%d sweep_us=%.3f\n", key.c_str(),
+              best.kind, best.vx, best.ty, best.zc, best.stages, sbest.ty, sbest.zc, sbest.tile_tz, us);
       fclose(f);
     }
   }
   return join_out(g);
 }
 
-cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[2]) {
+cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[3]) {
   if (!g) return fail(CFD_EINVAL, "null grid");
   if (jacobi) {
     jacobi[0] = g->jcfg.kind == 1 && !g->maps_ready ? 0 : g->jcfg.kind;
@@ -904,6 +926,7 @@ cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[2
   if (stencil) {
     stencil[0] = g->scfg.ty;
     stencil[1] = g->scfg.zc;
+    stencil[2] = g->scfg.tile_tz;
   }
   return CFD_OK;
 }

@@ -23,6 +23,7 @@
 #include <cstring>
 
 #include "cfd_internal.h"
+#include "tiles.cuh"
 
 namespace cfd {
 namespace {
@@ -55,27 +56,6 @@ __device__ __forceinline__ void stv(T* p, const float (&in)[VX]) {
   *reinterpret_cast<Vec<T, VX>*>(p) = x;
 }
 
-__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
-
-__device__ __forceinline__ bool locate(const Launch& L, long long t, int tx, int ty, int tz,
-                                       int& b, long long& base, int& i0, int& j0, int& k0) {
-  while (b < L.b0 + L.nblocks) {
-    const int nx = L.blocks[b].n[0], ny = L.blocks[b].n[1], nz = L.blocks[b].n[2];
-    const long long nxT = cdiv(nx, tx), nyT = cdiv(ny, ty), nzT = cdiv(nz, tz);
-    const long long cnt = nxT * nyT * nzT;
-    if (t < base + cnt) {
-      long long l = t - base;
-      i0 = (int)(l % nxT) * tx;
-      l /= nxT;
-      j0 = (int)(l % nyT) * ty;
-      k0 = (int)(l / nyT) * tz;
-      return true;
-    }
-    base += cnt;
-    ++b;
-  }
-  return false;
-}
 
 // ------------------------------------------------------------- PTX helpers
 
@@ -189,11 +169,12 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
   constexpr int xo = kAlignBytes / (int)sizeof(T);
   uint32_t parity = 0;
   int sbase = 0;
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, zc);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, TX, TY, zc, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
     const int k1 = min(k0 + zc, nz);
@@ -235,10 +216,17 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
       ldv<VX>(P0 + row, m);
       ldv<VX>(P1 + row, c);
     }
+    // block fields in registers: the output stores may alias the block table
+    // as far as the compiler knows, which would force a reload per plane
+    const long long pzl = B.pz;
+    const int pyl = B.py;
     T* Q = reinterpret_cast<T*>(L.base) + B.org[dst];
     const int x0 = i0 + xl;
     const bool full_vec = x0 + VX <= nx;
     const bool x_face = (x0 == 0) || (x0 <= nx - 1 && nx - 1 < x0 + VX);
+    const bool row_ok = j < ny && x0 < nx;
+    const bool face_xj = x_face || j == 0 || j == ny - 1;
+    T* qrow = Q + (long long)(k0 - 1) * pzl + (long long)j * pyl + x0;
     for (int k = k0; k < k1; ++k) {
       const int q = k - k0 + 1;
       wait_plane(q + 1);
@@ -262,8 +250,8 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
         const float nb = (xm + xp) * cx + (dn[e] + up[e]) * cy + (m[e] + zp[e]) * cz;
         out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
       }
-      if (j < ny && x0 < nx) {
-        T* qrow = Q + (long long)k * B.pz + (long long)j * B.py + x0;
+      qrow += pzl;
+      if (row_ok) {
         if (full_vec) {
           stv<T, VX>(qrow, out);
         } else {
@@ -271,7 +259,7 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
           for (int e = 0; e < VX; ++e)
             if (x0 + e < nx) qrow[e] = cvt<T>(out[e]);
         }
-        if (x_face || j == 0 || j == ny - 1 || k == 0 || k == nz - 1) {
+        if (face_xj || k == 0 || k == nz - 1) {
 #pragma unroll
           for (int e = 0; e < VX; ++e)
             if (x0 + e < nx) p_ghost_images<T>(L, B, dst, x0 + e, j, k, cvt<T>(out[e]));

@@ -10,6 +10,7 @@
 #include <cuda_fp16.h>
 
 #include "cfd_internal.h"
+#include "tiles.cuh"
 
 namespace cfd {
 namespace {
@@ -54,30 +55,6 @@ __device__ __forceinline__ void stv(T* p, const float (&in)[VX]) {
   *reinterpret_cast<Vec<T, VX>*>(p) = x;
 }
 
-__device__ __forceinline__ int cdiv(int a, int b) { return (a + b - 1) / b; }
-
-// Tile t -> (block b, tile origin).  b/base form a cursor that only moves
-// forward, since every CTA visits increasing t.
-__device__ __forceinline__ bool locate(const Launch& L, long long t, int tx, int ty, int tz,
-                                       int& b, long long& base, int& i0, int& j0, int& k0) {
-  while (b < L.b0 + L.nblocks) {
-    const int nx = L.blocks[b].n[0], ny = L.blocks[b].n[1], nz = L.blocks[b].n[2];
-    const long long nxT = cdiv(nx, tx), nyT = cdiv(ny, ty), nzT = cdiv(nz, tz);
-    const long long cnt = nxT * nyT * nzT;
-    if (t < base + cnt) {
-      long long l = t - base;
-      i0 = (int)(l % nxT) * tx;
-      l /= nxT;
-      j0 = (int)(l % nyT) * ty;
-      k0 = (int)(l / nyT) * tz;
-      return true;
-    }
-    base += cnt;
-    ++b;
-  }
-  return false;
-}
-
 template <typename T>
 struct Fld {
   const T* p;
@@ -106,83 +83,102 @@ __device__ __forceinline__ T* wptr(const Launch& L, const BlockDev& B, int arr) 
 // x, y, z passes: the source cell is found axis by axis (neighbour block or
 // mirror image) and the wall rules compose as affine maps v -> A + S v.
 
-struct GhostArrays { int arr[4]; int n; };
+struct GhostArrays { int arr[kNumArrays]; int n; };
 
 template <typename T>
 __global__ void __launch_bounds__(256) k_ghost(Launch L, GhostArrays ga, const long long* prefix,
                                                long long total) {
-  const long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= total) return;
-  const int arr = ga.arr[blockIdx.y];
-  const int kind = array_kind(arr);
+  // the block table and the enumeration prefix, once per CTA, in shared
+  // memory: every ghost cell resolves its source through several of them
+  extern __shared__ __align__(16) unsigned char gsm[];
+  BlockDev* sb = reinterpret_cast<BlockDev*>(gsm);
+  long long* spre = reinterpret_cast<long long*>(gsm + (size_t)L.nblocks * sizeof(BlockDev));
+  {
+    const int words = L.nblocks * (int)(sizeof(BlockDev) / 4);
+    const int* src = reinterpret_cast<const int*>(L.blocks);
+    for (int w = threadIdx.x; w < words; w += blockDim.x) reinterpret_cast<int*>(sb)[w] = src[w];
+    for (int b = threadIdx.x; b <= L.nblocks; b += blockDim.x) spre[b] = prefix[b];
+  }
+  __syncthreads();
   const int g = L.ghost;
-  // block of this ghost cell (binary search over the prefix sums)
-  int lo = 0, hi = L.nblocks - 1;
-  while (lo < hi) {
-    const int mid = (lo + hi + 1) >> 1;
-    if (prefix[mid] <= t) lo = mid; else hi = mid - 1;
-  }
-  const int b = lo;
-  const BlockDev& B = L.blocks[b];
-  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
-  const long long ex = nx + 2 * g, ey = ny + 2 * g;
-  long long l = t - prefix[b];
-  int q[3];
-  const long long zc = 2LL * g * ey * ex, yc = 2LL * g * nz * ex;
-  if (l < zc) {
-    const int s = (int)(l / (ey * ex));
-    const long long rem = l % (ey * ex);
-    q[2] = s < g ? s - g : nz + s - g;
-    q[1] = (int)(rem / ex) - g;
-    q[0] = (int)(rem % ex) - g;
-  } else if ((l -= zc) < yc) {
-    const int s = (int)(l / (nz * ex));
-    const long long rem = l % (nz * ex);
-    q[1] = s < g ? s - g : ny + s - g;
-    q[2] = (int)(rem / ex);
-    q[0] = (int)(rem % ex) - g;
-  } else {
-    l -= yc;
-    const int s = (int)(l / ((long long)nz * ny));
-    const long long rem = l % ((long long)nz * ny);
-    q[0] = s < g ? s - g : nx + s - g;
-    q[2] = (int)(rem / ny);
-    q[1] = (int)(rem % ny);
-  }
-  const int dst[3] = {q[0], q[1], q[2]};
-  int sb = b;
-  float A = 0.f, S = 1.f;
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const BlockDev& C = L.blocks[sb];
-    const int N = C.n[d];
-    int face;
-    if (q[d] < 0) face = 2 * d; else if (q[d] >= N) face = 2 * d + 1; else continue;
-    const bool low = (face == 2 * d);
-    if (C.bc[face] == BC_PERIODIC) {
-      const int nb = C.nbr[face];
-      q[d] = low ? q[d] + L.blocks[nb].n[d] : q[d] - N;
-      sb = nb;
-    } else {
-      q[d] = low ? -1 - q[d] : 2 * N - 1 - q[d];
-      float a, s;
-      if (kind == 3) { a = 0.f; s = 1.f; }
-      else if (kind == d) { a = 0.f; s = 0.f; }
-      else { a = 2.f * C.wall[face][kind]; s = -1.f; }
-      A = a + s * A;
-      S = s * S;
+  const long long all = total * ga.n;
+  for (long long tt = (long long)blockIdx.x * blockDim.x + threadIdx.x; tt < all;
+       tt += (long long)gridDim.x * blockDim.x) {
+    const int arr = ga.arr[tt / total];
+    const long long t = tt % total;
+    const int kind = array_kind(arr);
+    // block of this ghost cell (binary search over the prefix sums)
+    int lo = 0, hi = L.nblocks - 1;
+    while (lo < hi) {
+      const int mid = (lo + hi + 1) >> 1;
+      if (spre[mid] <= t) lo = mid; else hi = mid - 1;
     }
+    const int b = lo;
+    const BlockDev& B = sb[b];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const long long ex = nx + 2 * g, ey = ny + 2 * g;
+    long long l = t - spre[b];
+    int q[3];
+    const long long zc = 2LL * g * ey * ex, yc = 2LL * g * nz * ex;
+    if (l < zc) {
+      const int s2 = (int)(l / (ey * ex));
+      const long long rem = l % (ey * ex);
+      q[2] = s2 < g ? s2 - g : nz + s2 - g;
+      q[1] = (int)(rem / ex) - g;
+      q[0] = (int)(rem % ex) - g;
+    } else if ((l -= zc) < yc) {
+      const int s2 = (int)(l / (nz * ex));
+      const long long rem = l % (nz * ex);
+      q[1] = s2 < g ? s2 - g : ny + s2 - g;
+      q[2] = (int)(rem / ex);
+      q[0] = (int)(rem % ex) - g;
+    } else {
+      l -= yc;
+      const int s2 = (int)(l / ((long long)nz * ny));
+      const long long rem = l % ((long long)nz * ny);
+      q[0] = s2 < g ? s2 - g : nx + s2 - g;
+      q[2] = (int)(rem / ny);
+      q[1] = (int)(rem % ny);
+    }
+    const int dst[3] = {q[0], q[1], q[2]};
+    int sbk = b;
+    float A = 0.f, S = 1.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const BlockDev& C = sb[sbk];
+      const int N = C.n[d];
+      int face;
+      if (q[d] < 0) face = 2 * d; else if (q[d] >= N) face = 2 * d + 1; else continue;
+      const bool low = (face == 2 * d);
+      if (C.bc[face] == BC_PERIODIC) {
+        const int nb = C.nbr[face];
+        q[d] = low ? q[d] + sb[nb].n[d] : q[d] - N;
+        sbk = nb;
+      } else {
+        q[d] = low ? -1 - q[d] : 2 * N - 1 - q[d];
+        float a, s1;
+        if (kind == 3) { a = 0.f; s1 = 1.f; }
+        else if (kind == d) { a = 0.f; s1 = 0.f; }
+        else { a = 2.f * C.wall[face][kind]; s1 = -1.f; }
+        A = a + s1 * A;
+        S = s1 * S;
+      }
+    }
+    float v = A;
+    if (S != 0.f) {
+      const BlockDev& Sd = sb[sbk];
+      v += S * ldf<T>(reinterpret_cast<const T*>(L.base) + Sd.org[arr] + (long long)q[2] * Sd.pz +
+                      (long long)q[1] * Sd.py + q[0]);
+    }
+    T* out = reinterpret_cast<T*>(L.base) + B.org[arr];
+    out[(long long)dst[2] * B.pz + (long long)dst[1] * B.py + dst[0]] = cvt<T>(v);
   }
-  float v = A;
-  if (S != 0.f) v += S * fld<T>(L, L.blocks[sb], arr)(q[0], q[1], q[2]);
-  T* out = wptr<T>(L, B, arr);
-  out[(long long)dst[2] * B.pz + (long long)dst[1] * B.py + dst[0]] = cvt<T>(v);
 }
 
 // ------------------------------------------------------- RHS + stage combine
 
-template <typename T, int ORDER, int C>
-__device__ __forceinline__ float rhs_comp(const Fld<T> (&f)[3], int i, int j, int k,
+template <typename F, int ORDER, int C>
+__device__ __forceinline__ float rhs_comp(const F (&f)[3], int i, int j, int k,
                                           const float (&ih)[3], const float (&ih2)[3],
                                           float nu) {
   auto at = [&](int comp, int d1, int o1, int d2, int o2) -> float {
@@ -234,11 +230,12 @@ __global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Se
                                                    Set3 ys, float cdt, Set3 os, float nu) {
   const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
   const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, TY, zc);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
@@ -248,9 +245,9 @@ __global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Se
                           B.bc[3] == BC_WALL && j == B.n[1] - 1, B.bc[5] == BC_WALL};
     for (int k = k0; k < k1; ++k) {
       float F[3];
-      F[0] = rhs_comp<T, ORDER, 0>(y, i, j, k, ih, ih2, nu);
-      F[1] = rhs_comp<T, ORDER, 1>(y, i, j, k, ih, ih2, nu);
-      F[2] = rhs_comp<T, ORDER, 2>(y, i, j, k, ih, ih2, nu);
+      F[0] = rhs_comp<Fld<T>, ORDER, 0>(y, i, j, k, ih, ih2, nu);
+      F[1] = rhs_comp<Fld<T>, ORDER, 1>(y, i, j, k, ih, ih2, nu);
+      F[2] = rhs_comp<Fld<T>, ORDER, 2>(y, i, j, k, ih, ih2, nu);
       const long long o = (long long)k * B.pz + (long long)j * B.py + i;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -263,16 +260,92 @@ __global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Se
   }
 }
 
+// Shared-memory tiled RHS + stage: a CTA loads a (32 + 2H) x (8 + 2H) x
+// (TZ + 2H) box of u, v, w (H = 1 for order 2, 2 for order 4) once, then
+// evaluates the same rhs_comp arithmetic from shared memory for its
+// 32 x 8 x TZ cells.
+
+template <int SX, int SY>
+struct SFld {
+  const float* t;
+  int i0, j0, k0;  // grid index of tile element (0,0,0)
+  __device__ __forceinline__ float operator()(int i, int j, int k) const {
+    return t[((k - k0) * SY + (j - j0)) * SX + (i - i0)];
+  }
+};
+
+template <typename T, int ORDER, int TZ>
+__global__ void __launch_bounds__(256) k_stage_tile(Launch L, float a, Set3 xs, float b, Set3 ys,
+                                                    float cdt, Set3 os, float nu) {
+  constexpr int H = ORDER == 2 ? 1 : 2;
+  constexpr int BX = 32, BY = 8, BZ = TZ;
+  constexpr int SX = BX + 2 * H, SY = BY + 2 * H, SZ = BZ + 2 * H;
+  constexpr int NT = SX * SY * SZ;
+  __shared__ float tile[3][NT];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, BX, BY, BZ);
+  const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
+  const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
+  const int tid = threadIdx.x;
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, BX, BY, BZ, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int g = L.ghost;
+    const int py = B.py;
+    const long long pz = B.pz;
+    // box load; cells beyond the allocated extent (partial tiles) are skipped
+    const int xmax = nx + g - 1, ymax = ny + g - 1, zmax = nz + g - 1;
+#pragma unroll
+    for (int c = 0; c < 3; ++c) {
+      const T* src = reinterpret_cast<const T*>(L.base) + B.org[ys.a[c]];
+      for (int idx = tid; idx < NT; idx += 256) {
+        const int xx = idx % SX, yy = (idx / SX) % SY, zz = idx / (SX * SY);
+        const int i = i0 - H + xx, j = j0 - H + yy, k = k0 - H + zz;
+        if (i <= xmax && j <= ymax && k <= zmax)
+          tile[c][idx] = ldf<T>(src + (long long)k * pz + (long long)j * py + i);
+      }
+    }
+    __syncthreads();
+    const SFld<SX, SY> f[3] = {{tile[0], i0 - H, j0 - H, k0 - H}, {tile[1], i0 - H, j0 - H, k0 - H},
+                               {tile[2], i0 - H, j0 - H, k0 - H}};
+    const int i = i0 + (tid & 31), j = j0 + (tid >> 5);
+    if (i < nx && j < ny) {
+      const bool wall[3] = {B.bc[1] == BC_WALL && i == nx - 1, B.bc[3] == BC_WALL && j == ny - 1,
+                            B.bc[5] == BC_WALL};
+      const int k1 = min(k0 + BZ, nz);
+      for (int k = k0; k < k1; ++k) {
+        float F[3];
+        F[0] = rhs_comp<SFld<SX, SY>, ORDER, 0>(f, i, j, k, ih, ih2, nu);
+        F[1] = rhs_comp<SFld<SX, SY>, ORDER, 1>(f, i, j, k, ih, ih2, nu);
+        F[2] = rhs_comp<SFld<SX, SY>, ORDER, 2>(f, i, j, k, ih, ih2, nu);
+        const long long o = (long long)k * pz + (long long)j * py + i;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const bool wf = wall[c] && (c != 2 || k == nz - 1);
+          float v = b * f[c](i, j, k) + cdt * F[c];
+          if (a != 0.f) v += a * ldf<T>(reinterpret_cast<const T*>(L.base) + B.org[xs.a[c]] + o);
+          reinterpret_cast<T*>(L.base)[B.org[os.a[c]] + o] = cvt<T>(wf ? 0.f : v);
+        }
+      }
+    }
+    __syncthreads();  // the next tile overwrites the box
+  }
+}
+
 // --------------------------------------------------------------- divergence
 
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, float inv_cdt,
                                                  int r_arr) {
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, TY, zc);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
@@ -293,11 +366,12 @@ __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, floa
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_project(Launch L, int zc, Set3 ws, int p_arr,
                                                      float cdt, Set3 os) {
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, TY, zc);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
@@ -322,12 +396,13 @@ __global__ void __launch_bounds__(32 * TY) k_project(Launch L, int zc, Set3 ws, 
 
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_copy(Launch L, int zc, int src, int dst) {
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, TY, zc);
   int blk = L.b0;
-  long long base = 0;
   const int g = L.ghost;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     // copies the full ghosted extent: tiles cover the interior, edge tiles
     // also take the ghost layers next to them
@@ -393,11 +468,12 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, i
   __shared__ __align__(16) float sm[TY + 2][TX];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, zc);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, TX, TY, zc, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
     const int py = B.py;
@@ -535,6 +611,293 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, i
   }
 }
 
+// cp.async-staged sweep: every thread copies its own 16-byte pieces of the
+// next planes of p (with the x and y halo) and r into an S-stage shared
+// memory ring (cp.async.commit_group / wait_group), so S - 4 planes are in
+// flight without holding registers; one barrier per plane.  A plane stage is
+// (TY + 2) rows of PW = TX + 2 HX elements of p (HX = 16 bytes of halo pad
+// on each side; the x halo cells sit next to the interior) and TY x TX of r.
+
+__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_async4(void* smem, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(
+                   static_cast<uint32_t>(__cvta_generic_to_shared(smem))),
+               "l"(gmem)
+               : "memory");
+}
+__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+
+template <int BYTES>
+__device__ __forceinline__ void cp_async_n(void* smem, const void* gmem) {
+  if constexpr (BYTES == 16) cp_async16(smem, gmem);
+  else if constexpr (BYTES == 8) cp_async8(smem, gmem);
+  else cp_async4(smem, gmem);
+}
+
+template <typename T, int VX, int TY, int S>
+struct AsyncGeom {
+  static constexpr int TX = 32 * VX;
+  static constexpr int HX = 16 / (int)sizeof(T);
+  static constexpr int PW = TX + 2 * HX;
+  static constexpr int PELEMS = (TY + 2) * PW;
+  static constexpr int RELEMS = TY * TX;
+  static constexpr int STAGE_BYTES = ((PELEMS + RELEMS) * (int)sizeof(T) + 127) / 128 * 128;
+  static constexpr int SMEM = S * STAGE_BYTES;
+};
+
+template <typename T, int VX, int TY, int S>
+__global__ void __launch_bounds__(32 * TY) k_jacobi_async(Launch L, int zc, int src, int dst,
+                                                          int r_arr, float omega,
+                                                          float inv_diag) {
+  using Gm = AsyncGeom<T, VX, TY, S>;
+  constexpr int TX = Gm::TX, HX = Gm::HX, PW = Gm::PW;
+  constexpr int VB = VX * (int)sizeof(T);          // bytes per thread vector
+  constexpr int XB = sizeof(T) == 4 ? 4 : 4;       // x-halo copy: 1 float or 2 halves
+  constexpr int XE = XB / (int)sizeof(T);          // elements in an x-halo copy
+  static_assert(S >= 4, "ring needs at least 4 stages");
+  extern __shared__ __align__(128) unsigned char smem[];
+  const int lane = threadIdx.x, ty = threadIdx.y;
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, zc);
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int py = B.py;
+    const long long pz = B.pz;
+    const int i = i0 + lane * VX;
+    const int j = j0 + ty;
+    const int k1 = min(k0 + zc, nz);
+    const int np = k1 - k0 + 2;  // planes k0 - 1 .. k1
+    const T* P0 = reinterpret_cast<const T*>(L.base) + B.org[src];
+    const T* R0 = reinterpret_cast<const T*>(L.base) + B.org[r_arr];
+    // what this thread copies for every plane
+    const bool cp_row = i <= nx && j <= ny;
+    const bool cp_r = i <= nx && j < ny;
+    const bool cp_lo = ty == 0 && i <= nx;                         // row j0 - 1
+    const bool cp_hi = ty == TY - 1 && i <= nx && j0 + TY <= ny;   // row j0 + TY
+    const bool cp_xl = lane == 0 && j <= ny;                        // x = i0 - XE .. i0 - 1
+    const bool cp_xr = lane == 31 && j <= ny && i0 + TX <= nx;      // x = i0 + TX ..
+    const long long g_row = (long long)j * py + i;
+    const int s_row = (ty + 1) * PW + HX + lane * VX;
+    auto stage_p = [&](int q) { return reinterpret_cast<T*>(smem + (q % S) * Gm::STAGE_BYTES); };
+    auto stage_r = [&](int q) { return stage_p(q) + Gm::PELEMS; };
+    auto issue = [&](int q) {
+      if (q < np) {
+        const long long gz = (long long)(k0 - 1 + q) * pz;
+        T* sp = stage_p(q);
+        if (cp_row) cp_async_n<VB>(sp + s_row, P0 + gz + g_row);
+        if (cp_lo) cp_async_n<VB>(sp + HX + lane * VX, P0 + gz + g_row - (long long)(ty + 1) * py);
+        if (cp_hi) cp_async_n<VB>(sp + (TY + 1) * PW + HX + lane * VX, P0 + gz + g_row + py);
+        if (cp_xl) cp_async_n<XB>(sp + (ty + 1) * PW + HX - XE, P0 + gz + (long long)j * py + i0 - XE);
+        if (cp_xr) cp_async_n<XB>(sp + (ty + 1) * PW + HX + TX, P0 + gz + (long long)j * py + i0 + TX);
+        if (cp_r && q >= 1 && q <= np - 2)
+          cp_async_n<VB>(stage_r(q) + ty * TX + lane * VX, R0 + gz + g_row);
+      }
+      cp_commit();
+    };
+    for (int q = 0; q < S - 1; ++q) issue(q);
+    T* qo = wptr<T>(L, B, dst) + (long long)k0 * pz + g_row;
+    const bool out_row = j < ny && i < nx;
+    const bool full_vec = i + VX <= nx;
+    const bool face_xj = (i == 0) || (i <= nx - 1 && nx - 1 < i + VX) || j == 0 || j == ny - 1;
+    for (int q = 1; q <= np - 2; ++q) {
+      cp_wait<S - 4>();  // this thread's copies of plane q + 1 have landed
+      __syncthreads();   // everyone's have; plane q - 2 is no longer read
+      issue(q + S - 2);
+      const T* Pm = stage_p(q - 1);
+      const T* Pc = stage_p(q);
+      const T* Pp = stage_p(q + 1);
+      float c[VX], up[VX], dn[VX], zm[VX], zp[VX], rr[VX];
+      ldv<VX>(Pc + s_row, c);
+      ldv<VX>(Pc + s_row + PW, up);
+      ldv<VX>(Pc + s_row - PW, dn);
+      ldv<VX>(Pm + s_row, zm);
+      ldv<VX>(Pp + s_row, zp);
+      ldv<VX>(stage_r(q) + ty * TX + lane * VX, rr);
+      const float left = tof(Pc[s_row - 1]), right = tof(Pc[s_row + VX]);
+      float out[VX];
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        const float xm = e == 0 ? left : c[e - 1];
+        const float xp = e == VX - 1 ? right : c[e + 1];
+        const float nb = (xm + xp) * cx + (dn[e] + up[e]) * cy + (zm[e] + zp[e]) * cz;
+        out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+      }
+      const int k = k0 + q - 1;
+      if (out_row) {
+        if (full_vec) {
+          stv<T, VX>(qo, out);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VX; ++e)
+            if (i + e < nx) qo[e] = cvt<T>(out[e]);
+        }
+        if (face_xj || k == 0 || k == nz - 1) {
+#pragma unroll
+          for (int e = 0; e < VX; ++e)
+            if (i + e < nx) p_ghost_images<T>(L, B, dst, i + e, j, k, cvt<T>(out[e]));
+        }
+      }
+      qo += pz;
+    }
+    cp_wait<0>();
+    __syncthreads();  // the next tile refills the ring
+  }
+}
+
+// Warp-streaming sweep: every warp owns one row segment (32 VX cells) of a
+// tile and walks it along z on its own, with no shared memory and no
+// barrier.  For each plane it needs a bundle: the row (centre), the rows
+// above and below (y neighbours, served by L1/L2) and r, plus the two x-halo
+// cells at the row ends; z neighbours are the centre rows of the bundles of
+// the previous and next planes.  Bundles live in a ring of NR = PF + 2
+// register slots whose slot index is a compile-time constant in every
+// unrolled step, so the ring never moves data; the loads of the bundle PF
+// planes ahead are issued before each plane is computed.
+
+template <typename T, int VX>
+struct Bundle {
+  float p[VX], ym[VX], yp[VX], r[VX];
+  float xl, xr;
+};
+
+template <typename T, int VX>
+__device__ __forceinline__ void load_bundle(Bundle<T, VX>& b, const T* P, const T* R,
+                                            long long o, int py, bool ld, bool ldr,
+                                            bool ldl, long long xl_o, bool ldrgt,
+                                            long long xr_o) {
+  if (ld) {
+    ldv<VX>(P + o, b.p);
+    ldv<VX>(P + o - py, b.ym);
+    ldv<VX>(P + o + py, b.yp);
+  }
+  if (ldr) ldv<VX>(R + o, b.r);
+  if (ldl) b.xl = ldf<T>(P + xl_o);
+  if (ldrgt) b.xr = ldf<T>(P + xr_o);
+}
+
+template <typename T, int VX, int TY, int PF>
+__global__ void __launch_bounds__(32 * TY) k_jacobi_warp(Launch L, int zc, int src, int dst,
+                                                         int r_arr, float omega, float inv_diag) {
+  constexpr int TX = 32 * VX;
+  constexpr int NR = PF + 2;
+  const int lane = threadIdx.x;
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, zc);
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int j = j0 + threadIdx.y;
+    if (j >= ny) continue;  // uniform per warp
+    const int py = B.py;
+    const long long pz = B.pz;
+    const T* P = reinterpret_cast<const T*>(L.base) + B.org[src];
+    const T* R = reinterpret_cast<const T*>(L.base) + B.org[r_arr];
+    T* Q = reinterpret_cast<T*>(L.base) + B.org[dst];
+    const int i = i0 + lane * VX;
+    const int k1 = min(k0 + zc, nz);
+    const long long row = (long long)j * py + i;
+    const long long rowx = (long long)j * py;
+    const bool ld = i <= nx;
+    const bool ldl = lane == 0;
+    const bool ldrgt = lane == 31 && i0 + TX <= nx;
+    const bool out_row = i < nx;
+    const bool full_vec = i + VX <= nx;
+    const bool face_xj = (i == 0) || (i <= nx - 1 && nx - 1 < i + VX) || j == 0 || j == ny - 1;
+    Bundle<T, VX> ring[NR];
+#pragma unroll
+    for (int s = 0; s < NR; ++s) {
+#pragma unroll
+      for (int e = 0; e < VX; ++e) ring[s].p[e] = ring[s].ym[e] = ring[s].yp[e] = ring[s].r[e] = 0.f;
+      ring[s].xl = ring[s].xr = 0.f;
+    }
+    // planes k0 - 1 .. k0 + PF into slots (plane + 1) % NR  (plane k0 - 1 -> slot k0 % NR ...)
+    // slot of plane z is (z - k0 + 1) % NR
+#pragma unroll
+    for (int s = 0; s <= PF + 1; ++s) {
+      const int z = k0 - 1 + s;
+      if (z <= k1) {
+        const long long o = (long long)z * pz + row;
+        load_bundle<T, VX>(ring[s], P, R, o, py, ld, ld && z >= k0 && z < k1, ldl,
+                           (long long)z * pz + rowx + i0 - 1, ldrgt, (long long)z * pz + rowx + i0 + TX);
+      }
+    }
+    for (int kb = k0; kb < k1; kb += NR) {
+#pragma unroll
+      for (int st = 0; st < NR; ++st) {
+        const int k = kb + st;
+        if (k < k1) {
+          // plane k is in slot (k - k0 + 1) % NR = (st + 1 + kb - k0) % NR; kb - k0 is a multiple of NR
+          constexpr int dummy = 0;
+          (void)dummy;
+          Bundle<T, VX>& cb = ring[(st + 1) % NR];
+          const Bundle<T, VX>& mb = ring[st % NR];
+          const Bundle<T, VX>& pb = ring[(st + 2) % NR];
+          float left = __shfl_up_sync(0xffffffffu, cb.p[VX - 1], 1);
+          float right = __shfl_down_sync(0xffffffffu, cb.p[0], 1);
+          if (lane == 0) left = cb.xl;
+          if (lane == 31) right = cb.xr;
+          float out[VX];
+#pragma unroll
+          for (int e = 0; e < VX; ++e) {
+            const float xm = e == 0 ? left : cb.p[e - 1];
+            const float xp = e == VX - 1 ? right : cb.p[e + 1];
+            const float nb = (xm + xp) * cx + (cb.ym[e] + cb.yp[e]) * cy + (mb.p[e] + pb.p[e]) * cz;
+            out[e] = cb.p[e] + omega * ((nb - cb.r[e]) * inv_diag - cb.p[e]);
+          }
+          if (out_row) {
+            T* qo = Q + (long long)k * pz + row;
+            if (full_vec) {
+              stv<T, VX>(qo, out);
+            } else {
+#pragma unroll
+              for (int e = 0; e < VX; ++e)
+                if (i + e < nx) qo[e] = cvt<T>(out[e]);
+            }
+            if (face_xj || k == 0 || k == nz - 1) {
+#pragma unroll
+              for (int e = 0; e < VX; ++e)
+                if (i + e < nx) p_ghost_images<T>(L, B, dst, i + e, j, k, cvt<T>(out[e]));
+            }
+          }
+          // slot of plane k - 1 (mb) is free: load plane k + PF + 1 into it
+          const int z = k + PF + 1;
+          if (z <= k1) {
+            Bundle<T, VX>& nbnd = ring[st % NR];
+            const long long o = (long long)z * pz + row;
+            load_bundle<T, VX>(nbnd, P, R, o, py, ld, ld && z < k1, ldl,
+                               (long long)z * pz + rowx + i0 - 1, ldrgt,
+                               (long long)z * pz + rowx + i0 + TX);
+          }
+        }
+      }
+    }
+  }
+}
+
 // Direct sweep: one thread per VX consecutive cells of one row, every
 // neighbour loaded straight from global memory (x neighbours by shuffle).
 // No shared memory and no barrier: each CTA (32 x TY x TZ threads) covers a
@@ -550,11 +913,12 @@ __global__ void __launch_bounds__(32 * TY * TZ) k_jacobi_direct(Launch L, int sr
   constexpr int TX = 32 * VX;
   const int lane = threadIdx.x;
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, TZ);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, TX, TY, TZ, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, TX, TY, TZ, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
     const int j = j0 + threadIdx.y, k = k0 + threadIdx.z;
@@ -658,11 +1022,12 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
                                                     int p_arr, int r_arr, double* partials) {
   __shared__ double sh[TY][4];
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, TY, zc);
   int blk = L.b0;
-  long long base = 0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
-    if (!locate(L, t, 32, TY, zc, blk, base, i0, j0, k0)) break;
+    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
@@ -756,17 +1121,44 @@ long long count_tiles(const Launch& L, int tx, int ty, int tz) {
     default: { using T = __half; __VA_ARGS__; } break;     \
   }
 
+template <typename T>
+static cudaError_t run_ghost(const Launch& L, const GhostArrays& ga, const long long* d_prefix,
+                             long long total) {
+  const size_t smem = (size_t)L.nblocks * sizeof(BlockDev) + sizeof(long long) * (L.nblocks + 1);
+  static size_t set_for = 48 * 1024;
+  if (smem > set_for) {
+    cudaError_t e = cudaFuncSetAttribute(k_ghost<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                         (int)smem);
+    if (e != cudaSuccess) return e;
+    set_for = smem;
+  }
+  const long long work = total * ga.n;
+  long long grid = (work + 255) / 256;
+  const long long cap = (long long)L.sms * 8;
+  if (grid > cap) grid = cap;
+  k_ghost<T><<<(unsigned)grid, 256, smem, L.stream>>>(L, ga, d_prefix, total);
+  return cudaGetLastError();
+}
+
 cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr, const long long* d_prefix,
                          long long total) {
   if (total == 0 || narr == 0) return cudaSuccess;
-  for (int s = 0; s < narr; s += 4) {
-    GhostArrays ga{};
-    ga.n = narr - s < 4 ? narr - s : 4;
-    for (int e = 0; e < ga.n; ++e) ga.arr[e] = arrays[s + e];
-    dim3 grid((unsigned)((total + 255) / 256), (unsigned)ga.n);
-    CFD_DISPATCH_T(L.dtype, k_ghost<T><<<grid, 256, 0, L.stream>>>(L, ga, d_prefix, total));
-  }
+  GhostArrays ga{};
+  ga.n = narr;
+  for (int e = 0; e < narr; ++e) ga.arr[e] = arrays[e];
+  cudaError_t e = cudaSuccess;
+  CFD_DISPATCH_T(L.dtype, e = run_ghost<T>(L, ga, d_prefix, total));
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
+}
+
+template <typename T, int ORDER, int TZ>
+static void run_stage_tile(const Launch& L, float a, Set3 xs, float b, Set3 ys, float cdt, Set3 os,
+                           float nu) {
+  const long long tiles = count_tiles(L, 32, 8, TZ);
+  auto kern = k_stage_tile<T, ORDER, TZ>;
+  static const int occ = occupancy(kern, 256);
+  kern<<<grid_for(L, occ, tiles), 256, 0, L.stream>>>(L, a, xs, b, ys, cdt, os, nu);
 }
 
 template <typename T, int ORDER, int TY>
@@ -782,6 +1174,18 @@ cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float 
                          const int* xset, float b, const int* yset, float cdt, const int* oset,
                          float nu) {
   const Set3 xs = xset ? mk3(xset) : Set3{{0, 0, 0}};
+  if (c.tile_tz == 2 || c.tile_tz == 4) {
+    CFD_DISPATCH_T(L.dtype, {
+      if (order == 4) {
+        if (c.tile_tz == 2) run_stage_tile<T, 4, 2>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+        else run_stage_tile<T, 4, 4>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+      } else {
+        if (c.tile_tz == 2) run_stage_tile<T, 2, 2>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+        else run_stage_tile<T, 2, 4>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+      }
+    });
+    return cudaGetLastError();
+  }
   CFD_DISPATCH_T(L.dtype, {
     if (order == 4) {
       if (c.ty == 4) run_stage<T, 4, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
@@ -853,6 +1257,79 @@ cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst,
     }
   });
   return cudaGetLastError();
+}
+
+template <typename T, int VX, int TY, int PF>
+static void run_jacobi_warp(const Launch& L, int zc, int src, int dst, int r_arr, float omega,
+                            float inv_diag) {
+  const long long tiles = count_tiles(L, 32 * VX, TY, zc);
+  auto kern = k_jacobi_warp<T, VX, TY, PF>;
+  static const int occ = occupancy(kern, 32 * TY);
+  kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, src, dst, r_arr, omega,
+                                                                inv_diag);
+}
+
+cudaError_t launch_jacobi_warp(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                               float omega) {
+  const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+  CFD_DISPATCH_T(L.dtype, {
+    if (c.vx == 4 && c.stages == 1) run_jacobi_warp<T, 4, 4, 1>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 4 && c.stages == 2) run_jacobi_warp<T, 4, 4, 2>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 2 && c.stages == 2) run_jacobi_warp<T, 2, 4, 2>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 1 && c.stages == 2) run_jacobi_warp<T, 1, 4, 2>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 1) run_jacobi_warp<T, 1, 4, 3>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    else if (c.vx == 2) run_jacobi_warp<T, 2, 4, 3>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    else run_jacobi_warp<T, 4, 4, 3>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+  });
+  return cudaGetLastError();
+}
+
+template <typename T, int VX, int TY, int S>
+static cudaError_t run_jacobi_async(const Launch& L, int zc, int src, int dst, int r_arr,
+                                    float omega, float inv_diag) {
+  using Gm = AsyncGeom<T, VX, TY, S>;
+  auto kern = k_jacobi_async<T, VX, TY, S>;
+  static int occ = -1;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, Gm::SMEM);
+    if (e != cudaSuccess) return e;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * TY, Gm::SMEM) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+  }
+  const long long tiles = count_tiles(L, Gm::TX, TY, zc);
+  kern<<<grid_for(L, occ, tiles), dim3(32, TY), Gm::SMEM, L.stream>>>(L, zc, src, dst, r_arr, omega,
+                                                                       inv_diag);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_jacobi_async(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                                float omega) {
+  const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+  cudaError_t e = cudaErrorInvalidValue;
+  switch (L.dtype) {
+    case 0: {
+      using T = float;
+      if (c.ty == 4 && c.stages == 5) e = run_jacobi_async<T, 4, 4, 5>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else if (c.ty == 4 && c.stages == 6) e = run_jacobi_async<T, 4, 4, 6>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else if (c.ty == 8 && c.stages == 5) e = run_jacobi_async<T, 4, 8, 5>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else if (c.ty == 8) e = run_jacobi_async<T, 4, 8, 6>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      else e = run_jacobi_async<T, 4, 2, 6>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    } break;
+    default: {
+      // 16-bit storage: 8 cells per thread keeps the copies at 16 bytes
+      auto go = [&](auto tag) {
+        using T = decltype(tag);
+        if (c.ty == 4 && c.stages == 5) return run_jacobi_async<T, 8, 4, 5>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+        if (c.ty == 4 && c.stages == 6) return run_jacobi_async<T, 8, 4, 6>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+        if (c.ty == 8 && c.stages == 5) return run_jacobi_async<T, 8, 8, 5>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+        if (c.ty == 8) return run_jacobi_async<T, 8, 8, 6>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+        return run_jacobi_async<T, 8, 2, 6>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+      };
+      e = L.dtype == 1 ? go(__nv_bfloat16()) : go(__half());
+    } break;
+  }
+  return e;
 }
 
 template <typename T, int VX, int TY, int TZ>

@@ -180,7 +180,7 @@ class Grid:
         call("cfd_set_launch_mode", self.handle, 1 if per_block else 0)
 
     def kernel_config(self):
-        j, s = (c_int * 5)(), (c_int * 2)()
+        j, s = (c_int * 5)(), (c_int * 3)()
         call("cfd_get_kernel_config", self.handle, j, s)
         return tuple(j), tuple(s)
 

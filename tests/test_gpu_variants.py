@@ -22,6 +22,8 @@ JACOBI_CONFIGS = [
     (1, 4, 8, 32, 4), (1, 4, 8, 64, 6), (1, 4, 16, 32, 4), (1, 4, 16, 128, 6), (1, 2, 8, 16, 4),
     (1, 2, 16, 32, 4), (1, 4, 4, 16, 6), (1, 4, 4, 32, 4), (2, 4, 4, 1, 0), (2, 4, 4, 2, 0),
     (2, 4, 8, 1, 0), (2, 4, 2, 4, 0), (2, 2, 4, 2, 0), (2, 1, 8, 1, 0),
+    (3, 4, 4, 32, 5), (3, 4, 8, 16, 6), (3, 4, 2, 32, 6), (3, 4, 4, 64, 6),
+    (4, 4, 4, 16, 1), (4, 4, 4, 32, 2), (4, 4, 4, 7, 3), (4, 1, 4, 8, 2), (4, 2, 4, 13, 3),
 ]
 SIZES = [(45, 37, 21), (150, 77, 40)]
 
@@ -60,7 +62,8 @@ def test_jacobi_variant_matches_oracle(cfg, dims, bc):
 
 
 @pytest.mark.parametrize("cfg", [(1, 4, 8, 32, 4), (1, 2, 8, 16, 4), (0, 1, 8, 16, 4),
-                                 (2, 4, 4, 2, 0), (2, 1, 8, 1, 0)])
+                                 (2, 4, 4, 2, 0), (2, 1, 8, 1, 0), (3, 4, 4, 32, 5),
+                                 (4, 1, 4, 16, 3), (4, 4, 4, 8, 2)])
 def test_jacobi_variant_on_block_set(cfg):
     from oracle import Oracle
     from paper_1201_2118_gb300 import Grid, P, R, WU, WV, WW, mask
@@ -193,3 +196,50 @@ def test_per_block_launch_mode_is_bitwise_identical(g):
         res.append([grid.download(a, block=b) for b in range(len(blocks)) for a in (U, V, W, P)])
     for x, y in zip(*res):
         np.testing.assert_array_equal(x, y)
+
+
+@pytest.mark.parametrize("dtype", ["bf16", "f16"])
+@pytest.mark.parametrize("cfg", [(3, 8, 4, 32, 5), (3, 8, 8, 16, 6), (3, 8, 2, 64, 6),
+                                 (1, 4, 8, 32, 6), (2, 4, 4, 2, 0), (4, 4, 4, 16, 2)])
+def test_16bit_jacobi_variants_agree_with_register_sweep(dtype, cfg):
+    """Every 16-bit sweep variant computes the same FP32 expression and
+    rounds once, so it matches the register sweep to one rounding step."""
+    from paper_1201_2118_gb300 import P, WU, WV, WW, mask
+    dims = (300, 77, 40)
+    half_ulp = 2.0 ** (-8 if dtype == "bf16" else -11)
+    res = []
+    for c in ((0, 4, 4, 32, 4), cfg):
+        o, g, u, p = make_pair(dims, bc="cavity", fields=rand(dims, 5), dtype=dtype)
+        g.set_kernel_config(jacobi=c)
+        assert g.kernel_config()[0] == c
+        w = rand(dims, 6)
+        for k, a in enumerate((WU, WV, WW)):
+            g.interior(a).copy_(g.torch.from_numpy(w["uvw"[k]]).to(g.tdtype).cuda())
+        g.ghost_fill(mask(WU, WV, WW))
+        g.pressure_solve(0.05, 5)
+        res.append(g.download(P, ghosts=True))
+        g.check()
+    a, b = res
+    inner = (slice(1, -1),) * 3
+    assert (np.abs(a[inner] - b[inner]) <= 2 * half_ulp * np.abs(b[inner]) + 1e-30).all()
+
+
+@pytest.mark.parametrize("stencil", [(8, 16, 2), (4, 8, 4), (8, 32, 0)])
+@pytest.mark.parametrize("order,g,bc", [(2, 1, "periodic"), (4, 2, "periodic"), (2, 1, "cavity")])
+def test_stage_variants_match_oracle(stencil, order, g, bc):
+    """RHS + stage kernels (L1 neighbours or shared-memory box) against the
+    oracle, stage-2 form with distinct inputs, ragged multi-tile grid."""
+    from paper_1201_2118_gb300 import WU, WV, WW, U1, V1, W1, SET_U, SET_U1, SET_W, mask
+    dims = (70, 37, 21)
+    o, grid, u, p = make_pair(dims, ghost=g, order=order, bc=bc, nu=0.03, fields=rand(dims, 7))
+    grid.set_kernel_config(stencil=stencil)
+    assert grid.kernel_config()[1] == stencil
+    f1 = rounded(rand(dims, 8))
+    for k, a in enumerate((U1, V1, W1)):
+        grid.interior(a).copy_(grid.torch.from_numpy(f1["uvw"[k]]).float().cuda())
+    grid.ghost_fill(mask(U1, V1, W1))
+    u1 = [o.ghost_fill(o.embed(f1["uvw"[k]]), k) for k in range(3)]
+    grid.stage(0.5, SET_U, 0.5, SET_U1, 0.013, SET_W)
+    ref = o.stage(0.5, u, 0.5, u1, 0.013)
+    for k, a in enumerate((WU, WV, WW)):
+        assert rel_err(grid.download(a), o.interior(ref[k])) < 1e-5
