@@ -136,15 +136,16 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 
-def traffic_for(kernel_hash: str, cells: int):
+def traffic_for(kernel_hash: str, cells: int, config):
     """DRAM bytes per Jacobi launch from the committed ncu summary, scaled to
-    this launch's cells; None when the kernel changed since the capture."""
+    this launch's cells; None when the kernel source or the variant differs
+    from the captured one."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except Exception:
         return None
-    if t.get("kernel_sha256") != kernel_hash:
+    if t.get("kernel_sha256") != kernel_hash or list(t.get("config", [])) != list(config):
         return None
     return t["dram_bytes_per_cell"] * cells
 
@@ -202,6 +203,20 @@ def run_reference(a):
             "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0,
                     "d2h_bytes_per_step": 0}}
     print(json.dumps(line), flush=True)
+
+
+def aggregate(ms_local: float, cells: int, dist=None, device="cpu"):
+    """Slowest rank's time and the whole-job throughput of N replicas:
+    value = N * cells / max_rank(ms) (GLUP/s)."""
+    import torch
+    world = 1
+    ms = ms_local
+    if dist is not None and dist.is_initialized():
+        world = dist.get_world_size()
+        t = torch.tensor([ms_local], dtype=torch.float64, device=device)
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        ms = float(t.item())
+    return ms, world * cells / (ms * 1e-3) / 1e9
 
 
 # ------------------------------------------------------ secondary measures
@@ -398,15 +413,15 @@ def run_gpu(a):
     launches = g.launches - l0
     ms = e0.elapsed_time(e1) / a.steps
     g.check()
-    if dist is not None:
-        t = torch.tensor([ms], device="cuda", dtype=torch.float64)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        ms = float(t.item())
-    value = world * cells / (ms * 1e-3) / 1e9
+    ms, value = aggregate(ms, cells, dist, "cuda")
     ke, umax, divmax = g.reduce(0)
 
     # ---- dominant kernel: the Jacobi sweep, timed alone on the grid's stream
+    # (a fused launch of kind 5 does two sweeps; its compulsory traffic is
+    # still one read of p and r and one write of p per launch)
     sweeps = 100
+    fused = jcfg[0][0] == 5
+    per_launch = 2 if fused else 1
     j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g.jacobi(4)
     torch.cuda.synchronize()
@@ -414,17 +429,20 @@ def run_gpu(a):
     g.jacobi(sweeps)
     j1.record(stream)
     torch.cuda.synchronize()
-    sweep_ms = j0.elapsed_time(j1) / sweeps
+    launch_ms = j0.elapsed_time(j1) / (sweeps // per_launch)
     bytes_per_launch = JACOBI_BYTES_PER_CELL[a.dtype] * cells
-    achieved = bytes_per_launch / (sweep_ms * 1e-3) / 1e9
+    achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = traffic_for(file_hash(KERNEL_SRC), cells)
+    traffic = traffic_for(file_hash(KERNEL_SRC), cells, jcfg[0])
+    kname = ("k_jacobi2 (two fused weighted Jacobi sweeps per launch" if fused else
+             "Jacobi sweep kernel (one weighted Jacobi sweep per launch") + \
+        ", config %s, %d^3, %s)" % (list(jcfg[0]), n, a.dtype)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                "frac": achieved / peak, "traffic": traffic,
-                "kernel": "k_jacobi (one weighted Jacobi sweep, %d^3, %s)" % (n, a.dtype),
-                "bytes_per_launch": bytes_per_launch, "launch_ms": sweep_ms,
+                "frac": achieved / peak, "traffic": traffic, "kernel": kname,
+                "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
+                "sweeps_per_launch": per_launch,
                 "peak_source": "%s hbm_gbs (burst copy)" % peak_kind,
-                "sweep_glups": cells / (sweep_ms * 1e-3) / 1e9}
+                "sweep_glups": per_launch * cells / (launch_ms * 1e-3) / 1e9}
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -451,12 +469,9 @@ def run_gpu(a):
         x1.record(stream)
         torch.cuda.synchronize()
         ems = x0.elapsed_time(x1) / k_e2e
-        if dist is not None:
-            t = torch.tensor([ems], device="cuda", dtype=torch.float64)
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ems = float(t.item())
+        ems, e2e_value = aggregate(ems, cells, dist, "cuda")
         es = host_in[0].element_size()
-        e2e = {"value": world * cells / (ems * 1e-3) / 1e9, "unit": UNIT,
+        e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * cells * es, "d2h_bytes_per_step": 4 * cells * es,
                "ms_per_step": ems, "steps": k_e2e,
                "api": "cfd_copy_interior (pinned host -> device, u,v,w,p) + cfd_step + "

@@ -242,9 +242,10 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
  * shared memory ((vx, ty, zc) in {(4,4,1), (4,4,2), (4,4,4), (4,8,1), (4,2,4),
  * (2,4,2), (1,8,1)}, zc = z-planes per CTA), kind 3 the cp.async-staged
  * sweep (vx 4 for FP32, 8 for 16-bit storage; ty in {4,8} with stages in
- * {5,6}, or ty 2 with 6 stages), kind 4 the warp-streaming sweep (ty 4;
- * vx 4 with stages = planes prefetched ahead in {1,2,3}, or vx in {1,2} with
- * stages in {2,3}); zc = z-planes per tile.
+ * {5,6}, or ty 2 with 6 stages), kind 5 two fused sweeps per launch (temporal blocking;
+ * ty in {4,8}; used on single-block grids with nx % 128 == 0 and
+ * ny % ty == 0, other grids and odd sweep counts take single sweeps);
+ * zc = z-planes per tile.
  * stencil = {ty in {4,8}, zc, tile_tz in {0,2,4}} for the point kernels: rows
  * per CTA, z chunk, and for the RHS + stage kernel either neighbour reads
  * through L1 (tile_tz 0) or a shared-memory box of 32 x 8 x tile_tz cells

@@ -65,8 +65,8 @@ struct Launch {
 //   kind 1: TMA-staged sweep (tensor maps per block, S-stage mbarrier ring)
 //   kind 2: direct sweep (no shared memory; zc = z-planes per CTA, TZ)
 //   kind 3: cp.async-staged sweep (per-thread async copies, S-stage ring)
-//   kind 4: warp-streaming sweep (independent warps, register ring of
-//           stages = planes prefetched ahead)
+//   kind 5: two fused sweeps per launch (temporal blocking, single block,
+//           nx % 128 == 0, ny % ty == 0); odd counts end with one kind-0 sweep
 struct JacobiCfg { int kind, vx, ty, zc, stages; };
 // Point kernels: rows per CTA (32 x ty threads) and z chunk; the RHS + stage
 // kernel either reads neighbours through L1 (tile_tz = 0) or from a
@@ -109,8 +109,8 @@ cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* w
                               float inv_cdt, int r_arr);
 cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
                           float omega);
-cudaError_t launch_jacobi_warp(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
-                               float omega);
+cudaError_t launch_jacobi2(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                           float omega);
 cudaError_t launch_jacobi_async(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
                                 float omega);
 cudaError_t launch_jacobi_direct(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,

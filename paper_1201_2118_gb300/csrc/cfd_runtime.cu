@@ -352,20 +352,42 @@ cfd_status enq_stage(cfd_grid* g, double a, int xs, double b, int ys, double c, 
   });
 }
 
-// One Jacobi sweep src -> dst with the configured variant.
+// Fused two-sweep launches apply (single block, tiles dividing x and y).
+bool fused_ok(const cfd_grid* g) {
+  return g->jcfg.kind == 5 && g->nblocks == 1 && g->hb[0].n[0] % 128 == 0 &&
+         g->hb[0].n[1] % g->jcfg.ty == 0 && g->hb[0].n[1] >= 2 && g->hb[0].n[2] >= 2;
+}
+
+// One Jacobi sweep src -> dst with the configured variant (the fused
+// variant's single sweeps use the register/shuffle kernel).
 cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst) {
+  if (g->jcfg.kind == 5) return launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, src, dst, A_R, (float)g->omega);
   if (g->jcfg.kind == 1 && g->maps_ready)
     return launch_jacobi_tma(L, g->jcfg, g->base + g->maps_off, src == A_P ? 0 : 1, dst,
                              (float)g->omega);
   if (g->jcfg.kind == 2) return launch_jacobi_direct(L, g->jcfg, src, dst, A_R, (float)g->omega);
   if (g->jcfg.kind == 3) return launch_jacobi_async(L, g->jcfg, src, dst, A_R, (float)g->omega);
-  if (g->jcfg.kind == 4) return launch_jacobi_warp(L, g->jcfg, src, dst, A_R, (float)g->omega);
+
   return launch_jacobi(L, g->jcfg, src, dst, A_R, (float)g->omega);
 }
 
 cfd_status enq_sweeps(cfd_grid* g, int iters) {
   int cur = A_P, oth = A_P2;
   cfd_status s;
+  if (fused_ok(g)) {
+    const Launch L = make_launch(g);
+    for (int it = 0; it + 1 < iters; it += 2) {
+      CK(g, launch_jacobi2(L, g->jcfg, cur, oth, A_R, (float)g->omega));
+      g->launches += 1;
+      std::swap(cur, oth);
+    }
+    if (iters % 2) {
+      CK(g, sweep(g, L, cur, oth));
+      g->launches += 1;
+      std::swap(cur, oth);
+    }
+    iters = 0;
+  }
   for (int it = 0; it < iters; ++it) {
     if ((s = each_launch(g, [&](const Launch& L) { return sweep(g, L, cur, oth); })) != CFD_OK)
       return s;
@@ -797,10 +819,9 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
     const bool ok3 = c.kind == 3 && c.vx == (g->dtype == CFD_F32 ? 4 : 8) &&
                      (((c.ty == 4 || c.ty == 8) && (c.stages == 5 || c.stages == 6)) ||
                       (c.ty == 2 && c.stages == 6));
-    const bool ok4 = c.kind == 4 && c.ty == 4 &&
-                     ((c.vx == 4 && c.stages >= 1 && c.stages <= 3) ||
-                      ((c.vx == 1 || c.vx == 2) && (c.stages == 2 || c.stages == 3)));
-    if (!(ok0 || ok1 || ok2 || ok3 || ok4) || c.zc < 1) return fail(CFD_EINVAL, "unsupported Jacobi config");
+    const bool ok5 = c.kind == 5 && (c.ty == 4 || c.ty == 8);
+    if (!(ok0 || ok1 || ok2 || ok3 || ok5) || c.zc < 1)
+      return fail(CFD_EINVAL, "unsupported Jacobi config");
     g->jcfg = c;
     cfd_status s = refresh_maps(g);
     if (s != CFD_OK) {
@@ -849,11 +870,9 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
     cands.push_back({0, 1, 8, zc, 4});
   }
   cands.push_back({0, 2, 8, 32, 4});
-  for (int zc : {8, 16, 32, 64})
-    for (const JacobiCfg& d : {JacobiCfg{4, 4, 4, zc, 1}, JacobiCfg{4, 4, 4, zc, 2},
-                               JacobiCfg{4, 4, 4, zc, 3}, JacobiCfg{4, 2, 4, zc, 2},
-                               JacobiCfg{4, 1, 4, zc, 2}, JacobiCfg{4, 1, 4, zc, 3}})
-      cands.push_back(d);
+  if (g->nblocks == 1)
+    for (int zc : {16, 32, 64, 128})
+      for (int ty : {4, 8}) cands.push_back({5, 4, ty, zc, 0});
   const int avx = g->dtype == CFD_F32 ? 4 : 8;
   for (int zc : {16, 32, 64})
     for (const JacobiCfg& d : {JacobiCfg{3, avx, 4, zc, 5}, JacobiCfg{3, avx, 4, zc, 6},

@@ -764,137 +764,192 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_async(Launch L, int zc, int 
   }
 }
 
-// Warp-streaming sweep: every warp owns one row segment (32 VX cells) of a
-// tile and walks it along z on its own, with no shared memory and no
-// barrier.  For each plane it needs a bundle: the row (centre), the rows
-// above and below (y neighbours, served by L1/L2) and r, plus the two x-halo
-// cells at the row ends; z neighbours are the centre rows of the bundles of
-// the previous and next planes.  Bundles live in a ring of NR = PF + 2
-// register slots whose slot index is a compile-time constant in every
-// unrolled step, so the ring never moves data; the loads of the bundle PF
-// planes ahead are issued before each plane is computed.
+// Two fused Jacobi sweeps per pass (temporal blocking): p2 = J(J(p0, r), r).
+// A CTA of TY + 4 warps owns a 128 x TY column of a single block and walks
+// it along z.  Warp w loads row j0 - 2 + w of p0 (128 cells, 4 per lane, and
+// two halo cells on each side) and, one plane ahead, of r; sweep 1 is
+// evaluated on the (128 + 2) x (TY + 2) ring-extended tile, sweep 2 on the
+// tile itself.  Cells beyond the domain are read through the boundary map
+// (periodic wrap, or the mirror image for a zero-gradient wall), which makes
+// the ring's sweep-1 values equal to their ghost images, so no ghost layer
+// of the intermediate sweep is needed.  Shared memory: 3 planes of p0,
+// 3 planes of p1, 2 planes of r; rows are 136 elements with the 128
+// interior cells at 4..131 (16-byte aligned) and the halo at 2, 3, 132, 133.
 
-template <typename T, int VX>
-struct Bundle {
-  float p[VX], ym[VX], yp[VX], r[VX];
-  float xl, xr;
-};
-
-template <typename T, int VX>
-__device__ __forceinline__ void load_bundle(Bundle<T, VX>& b, const T* P, const T* R,
-                                            long long o, int py, bool ld, bool ldr,
-                                            bool ldl, long long xl_o, bool ldrgt,
-                                            long long xr_o) {
-  if (ld) {
-    ldv<VX>(P + o, b.p);
-    ldv<VX>(P + o - py, b.ym);
-    ldv<VX>(P + o + py, b.yp);
-  }
-  if (ldr) ldv<VX>(R + o, b.r);
-  if (ldl) b.xl = ldf<T>(P + xl_o);
-  if (ldrgt) b.xr = ldf<T>(P + xr_o);
+__device__ __forceinline__ int map_coord(int x, int n, bool periodic) {
+  if (x >= 0 && x < n) return x;
+  if (periodic) return x < 0 ? x + n : x - n;
+  return x < 0 ? -1 - x : 2 * n - 1 - x;
 }
 
-template <typename T, int VX, int TY, int PF>
-__global__ void __launch_bounds__(32 * TY) k_jacobi_warp(Launch L, int zc, int src, int dst,
-                                                         int r_arr, float omega, float inv_diag) {
-  constexpr int TX = 32 * VX;
-  constexpr int NR = PF + 2;
-  const int lane = threadIdx.x;
-  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+template <typename T, int TY>
+__global__ void __launch_bounds__(32 * (TY + 4)) k_jacobi2(Launch L, int zc, int src, int dst,
+                                                          int r_arr, float omega,
+                                                          float inv_diag) {
+  constexpr int TX = 128, RW = 136, NW = TY + 4;
+  __shared__ __align__(16) float P0[3][NW][RW];
+  __shared__ __align__(16) float P1[3][TY + 2][RW];
+  __shared__ __align__(16) float RR[2][TY + 2][RW];
   __shared__ TileTable tt;
   tile_table_build(tt, L, TX, TY, zc);
+  const int lane = threadIdx.x, w = threadIdx.y;
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
   int blk = L.b0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
     if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
     const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
-    const int j = j0 + threadIdx.y;
-    if (j >= ny) continue;  // uniform per warp
     const int py = B.py;
     const long long pz = B.pz;
+    const bool perx = B.bc[0] == BC_PERIODIC, pery = B.bc[2] == BC_PERIODIC,
+               perz = B.bc[4] == BC_PERIODIC;
     const T* P = reinterpret_cast<const T*>(L.base) + B.org[src];
     const T* R = reinterpret_cast<const T*>(L.base) + B.org[r_arr];
     T* Q = reinterpret_cast<T*>(L.base) + B.org[dst];
-    const int i = i0 + lane * VX;
     const int k1 = min(k0 + zc, nz);
-    const long long row = (long long)j * py + i;
-    const long long rowx = (long long)j * py;
-    const bool ld = i <= nx;
-    const bool ldl = lane == 0;
-    const bool ldrgt = lane == 31 && i0 + TX <= nx;
-    const bool out_row = i < nx;
-    const bool full_vec = i + VX <= nx;
-    const bool face_xj = (i == 0) || (i <= nx - 1 && nx - 1 < i + VX) || j == 0 || j == ny - 1;
-    Bundle<T, VX> ring[NR];
-#pragma unroll
-    for (int s = 0; s < NR; ++s) {
-#pragma unroll
-      for (int e = 0; e < VX; ++e) ring[s].p[e] = ring[s].ym[e] = ring[s].yp[e] = ring[s].r[e] = 0.f;
-      ring[s].xl = ring[s].xr = 0.f;
-    }
-    // planes k0 - 1 .. k0 + PF into slots (plane + 1) % NR  (plane k0 - 1 -> slot k0 % NR ...)
-    // slot of plane z is (z - k0 + 1) % NR
-#pragma unroll
-    for (int s = 0; s <= PF + 1; ++s) {
-      const int z = k0 - 1 + s;
-      if (z <= k1) {
-        const long long o = (long long)z * pz + row;
-        load_bundle<T, VX>(ring[s], P, R, o, py, ld, ld && z >= k0 && z < k1, ldl,
-                           (long long)z * pz + rowx + i0 - 1, ldrgt, (long long)z * pz + rowx + i0 + TX);
+    const int x = i0 + lane * 4;
+    // this warp's p0 row and (warps 1..TY+2) r row, mapped into the domain
+    const int yrow = map_coord(j0 - 2 + w, ny, pery);
+    const bool has_r = w >= 1 && w <= TY + 2;
+    // halo columns of lanes 0 and 31, mapped
+    const int xl2 = map_coord(i0 - 2, nx, perx), xl1 = map_coord(i0 - 1, nx, perx);
+    const int xr1 = map_coord(i0 + TX, nx, perx), xr2 = map_coord(i0 + TX + 1, nx, perx);
+
+    // register staging of one plane of p0 (and r) for this thread
+    float sp[4], sr[4];
+    float sh0 = 0.f, sh1 = 0.f, shr = 0.f;
+    auto load_plane = [&](int z, bool want_r, int zr) {
+      const long long ro = (long long)map_coord(z, nz, perz) * pz + (long long)yrow * py;
+      ldv<4>(P + ro + x, sp);
+      if (lane == 0) { sh0 = ldf<T>(P + ro + xl2); sh1 = ldf<T>(P + ro + xl1); }
+      if (lane == 31) { sh0 = ldf<T>(P + ro + xr1); sh1 = ldf<T>(P + ro + xr2); }
+      if (want_r && has_r) {
+        const long long rro = (long long)map_coord(zr, nz, perz) * pz + (long long)yrow * py;
+        ldv<4>(R + rro + x, sr);
+        if (lane == 0) shr = ldf<T>(R + rro + xl1);
+        if (lane == 31) shr = ldf<T>(R + rro + xr1);
       }
+    };
+    auto store_plane = [&](int z, bool want_r, int zr) {
+      float* prow = &P0[((z % 3) + 3) % 3][w][0];
+      *reinterpret_cast<float4*>(prow + 4 + lane * 4) = make_float4(sp[0], sp[1], sp[2], sp[3]);
+      if (lane == 0) { prow[2] = sh0; prow[3] = sh1; }
+      if (lane == 31) { prow[132] = sh0; prow[133] = sh1; }
+      if (want_r && has_r) {
+        float* rrow = &RR[((zr % 2) + 2) % 2][w - 1][0];
+        *reinterpret_cast<float4*>(rrow + 4 + lane * 4) = make_float4(sr[0], sr[1], sr[2], sr[3]);
+        if (lane == 0) rrow[3] = shr;
+        if (lane == 31) rrow[132] = shr;
+      }
+    };
+    // sweep 1 at plane z on rows 1..TY+2 (P1 row w - 1), from P0 planes z-1, z, z+1
+    auto sweep1 = [&](int z) {
+      if (!has_r) return;
+      const float* pc = &P0[((z % 3) + 3) % 3][w][0];
+      const float* pm = &P0[(((z - 1) % 3) + 3) % 3][w][0];
+      const float* pp = &P0[(((z + 1) % 3) + 3) % 3][w][0];
+      const float* rr = &RR[((z % 2) + 2) % 2][w - 1][0];
+      float* out = &P1[((z % 3) + 3) % 3][w - 1][0];
+      const int c0 = 4 + lane * 4;
+      const float4 c4 = *reinterpret_cast<const float4*>(pc + c0);
+      const float4 u4 = *reinterpret_cast<const float4*>(pc + c0 + RW);
+      const float4 d4 = *reinterpret_cast<const float4*>(pc + c0 - RW);
+      const float4 m4 = *reinterpret_cast<const float4*>(pm + c0);
+      const float4 p4 = *reinterpret_cast<const float4*>(pp + c0);
+      const float4 r4 = *reinterpret_cast<const float4*>(rr + c0);
+      const float cc[4] = {c4.x, c4.y, c4.z, c4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w},
+                  dd[4] = {d4.x, d4.y, d4.z, d4.w}, mm[4] = {m4.x, m4.y, m4.z, m4.w},
+                  qq[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+      const float left = pc[c0 - 1], right = pc[c0 + 4];
+      float o[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float xm = e == 0 ? left : cc[e - 1];
+        const float xp = e == 3 ? right : cc[e + 1];
+        const float nb = (xm + xp) * cx + (dd[e] + uu[e]) * cy + (mm[e] + qq[e]) * cz;
+        o[e] = cc[e] + omega * ((nb - rv[e]) * inv_diag - cc[e]);
+      }
+      *reinterpret_cast<float4*>(out + c0) = make_float4(o[0], o[1], o[2], o[3]);
+      if (lane == 0 || lane == 31) {  // ring column x = i0 - 1 (index 3) or i0 + TX (132)
+        const int c = lane == 0 ? 3 : 132;
+        const float nb = (pc[c - 1] + pc[c + 1]) * cx + (pc[c - RW] + pc[c + RW]) * cy +
+                         (pm[c] + pp[c]) * cz;
+        out[c] = pc[c] + omega * ((nb - rr[c]) * inv_diag - pc[c]);
+      }
+    };
+
+    // prologue: sweep 1 at planes k0 - 1 and k0
+    load_plane(k0 - 2, false, 0);
+    store_plane(k0 - 2, false, 0);
+    load_plane(k0 - 1, true, k0 - 1);
+    store_plane(k0 - 1, true, k0 - 1);
+    load_plane(k0, true, k0);
+    store_plane(k0, false, 0);
+    const float srk[4] = {sr[0], sr[1], sr[2], sr[3]};
+    const float shrk = shr;
+    __syncthreads();
+    sweep1(k0 - 1);
+    __syncthreads();
+    // r(k0) into its slot; p0(k0 + 1)
+    for (int e = 0; e < 4; ++e) sr[e] = srk[e];
+    shr = shrk;
+    load_plane(k0 + 1, false, 0);
+    store_plane(k0 + 1, false, 0);
+    if (has_r) {
+      float* rrow = &RR[((k0 % 2) + 2) % 2][w - 1][0];
+      *reinterpret_cast<float4*>(rrow + 4 + lane * 4) = make_float4(sr[0], sr[1], sr[2], sr[3]);
+      if (lane == 0) rrow[3] = shr;
+      if (lane == 31) rrow[132] = shr;
     }
-    for (int kb = k0; kb < k1; kb += NR) {
+    __syncthreads();
+    sweep1(k0);
+    // prefetch p0(k0 + 2), r(k0 + 1) for the first iteration
+    load_plane(k0 + 2, true, k0 + 1);
+
+    const bool out_warp = w >= 2 && w <= TY + 1;
+    const int j = j0 + w - 2;
+    const bool face_xj = (x == 0) || (x + 4 == nx) || j == 0 || j == ny - 1;
+    for (int m = k0; m < k1; ++m) {
+      __syncthreads();  // previous p2 reads and sweep 1 of plane m are done
+      store_plane(m + 2, true, m + 1);
+      if (m + 1 < k1) load_plane(m + 3, true, m + 2);
+      __syncthreads();
+      sweep1(m + 1);
+      __syncthreads();
+      if (out_warp) {
+        const float* qc = &P1[((m % 3) + 3) % 3][w - 1][0];
+        const float* qm = &P1[(((m - 1) % 3) + 3) % 3][w - 1][0];
+        const float* qp = &P1[(((m + 1) % 3) + 3) % 3][w - 1][0];
+        const float* rr = &RR[((m % 2) + 2) % 2][w - 1][0];
+        const int c0 = 4 + lane * 4;
+        const float4 c4 = *reinterpret_cast<const float4*>(qc + c0);
+        const float4 u4 = *reinterpret_cast<const float4*>(qc + c0 + RW);
+        const float4 d4 = *reinterpret_cast<const float4*>(qc + c0 - RW);
+        const float4 m4 = *reinterpret_cast<const float4*>(qm + c0);
+        const float4 p4 = *reinterpret_cast<const float4*>(qp + c0);
+        const float4 r4 = *reinterpret_cast<const float4*>(rr + c0);
+        const float cc[4] = {c4.x, c4.y, c4.z, c4.w}, uu[4] = {u4.x, u4.y, u4.z, u4.w},
+                    dd[4] = {d4.x, d4.y, d4.z, d4.w}, mm[4] = {m4.x, m4.y, m4.z, m4.w},
+                    qq[4] = {p4.x, p4.y, p4.z, p4.w}, rv[4] = {r4.x, r4.y, r4.z, r4.w};
+        const float left = qc[c0 - 1], right = qc[c0 + 4];
+        float o[4];
 #pragma unroll
-      for (int st = 0; st < NR; ++st) {
-        const int k = kb + st;
-        if (k < k1) {
-          // plane k is in slot (k - k0 + 1) % NR = (st + 1 + kb - k0) % NR; kb - k0 is a multiple of NR
-          constexpr int dummy = 0;
-          (void)dummy;
-          Bundle<T, VX>& cb = ring[(st + 1) % NR];
-          const Bundle<T, VX>& mb = ring[st % NR];
-          const Bundle<T, VX>& pb = ring[(st + 2) % NR];
-          float left = __shfl_up_sync(0xffffffffu, cb.p[VX - 1], 1);
-          float right = __shfl_down_sync(0xffffffffu, cb.p[0], 1);
-          if (lane == 0) left = cb.xl;
-          if (lane == 31) right = cb.xr;
-          float out[VX];
+        for (int e = 0; e < 4; ++e) {
+          const float xm = e == 0 ? left : cc[e - 1];
+          const float xp = e == 3 ? right : cc[e + 1];
+          const float nb = (xm + xp) * cx + (dd[e] + uu[e]) * cy + (mm[e] + qq[e]) * cz;
+          o[e] = cc[e] + omega * ((nb - rv[e]) * inv_diag - cc[e]);
+        }
+        T* qo = Q + (long long)m * pz + (long long)j * py + x;
+        stv<T, 4>(qo, o);
+        if (face_xj || m == 0 || m == nz - 1) {
 #pragma unroll
-          for (int e = 0; e < VX; ++e) {
-            const float xm = e == 0 ? left : cb.p[e - 1];
-            const float xp = e == VX - 1 ? right : cb.p[e + 1];
-            const float nb = (xm + xp) * cx + (cb.ym[e] + cb.yp[e]) * cy + (mb.p[e] + pb.p[e]) * cz;
-            out[e] = cb.p[e] + omega * ((nb - cb.r[e]) * inv_diag - cb.p[e]);
-          }
-          if (out_row) {
-            T* qo = Q + (long long)k * pz + row;
-            if (full_vec) {
-              stv<T, VX>(qo, out);
-            } else {
-#pragma unroll
-              for (int e = 0; e < VX; ++e)
-                if (i + e < nx) qo[e] = cvt<T>(out[e]);
-            }
-            if (face_xj || k == 0 || k == nz - 1) {
-#pragma unroll
-              for (int e = 0; e < VX; ++e)
-                if (i + e < nx) p_ghost_images<T>(L, B, dst, i + e, j, k, cvt<T>(out[e]));
-            }
-          }
-          // slot of plane k - 1 (mb) is free: load plane k + PF + 1 into it
-          const int z = k + PF + 1;
-          if (z <= k1) {
-            Bundle<T, VX>& nbnd = ring[st % NR];
-            const long long o = (long long)z * pz + row;
-            load_bundle<T, VX>(nbnd, P, R, o, py, ld, ld && z < k1, ldl,
-                               (long long)z * pz + rowx + i0 - 1, ldrgt,
-                               (long long)z * pz + rowx + i0 + TX);
-          }
+          for (int e = 0; e < 4; ++e) p_ghost_images<T>(L, B, dst, x + e, j, m, cvt<T>(o[e]));
         }
       }
     }
+    __syncthreads();  // the next tile reuses the buffers
   }
 }
 
@@ -1259,27 +1314,22 @@ cudaError_t launch_jacobi(const Launch& L, const JacobiCfg& c, int src, int dst,
   return cudaGetLastError();
 }
 
-template <typename T, int VX, int TY, int PF>
-static void run_jacobi_warp(const Launch& L, int zc, int src, int dst, int r_arr, float omega,
-                            float inv_diag) {
-  const long long tiles = count_tiles(L, 32 * VX, TY, zc);
-  auto kern = k_jacobi_warp<T, VX, TY, PF>;
-  static const int occ = occupancy(kern, 32 * TY);
-  kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, src, dst, r_arr, omega,
-                                                                inv_diag);
+template <typename T, int TY>
+static void run_jacobi2(const Launch& L, int zc, int src, int dst, int r_arr, float omega,
+                        float inv_diag) {
+  const long long tiles = count_tiles(L, 128, TY, zc);
+  auto kern = k_jacobi2<T, TY>;
+  static const int occ = occupancy(kern, 32 * (TY + 4));
+  kern<<<grid_for(L, occ, tiles), dim3(32, TY + 4), 0, L.stream>>>(L, zc, src, dst, r_arr, omega,
+                                                                    inv_diag);
 }
 
-cudaError_t launch_jacobi_warp(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
-                               float omega) {
+cudaError_t launch_jacobi2(const Launch& L, const JacobiCfg& c, int src, int dst, int r_arr,
+                           float omega) {
   const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
   CFD_DISPATCH_T(L.dtype, {
-    if (c.vx == 4 && c.stages == 1) run_jacobi_warp<T, 4, 4, 1>(L, c.zc, src, dst, r_arr, omega, inv_diag);
-    else if (c.vx == 4 && c.stages == 2) run_jacobi_warp<T, 4, 4, 2>(L, c.zc, src, dst, r_arr, omega, inv_diag);
-    else if (c.vx == 2 && c.stages == 2) run_jacobi_warp<T, 2, 4, 2>(L, c.zc, src, dst, r_arr, omega, inv_diag);
-    else if (c.vx == 1 && c.stages == 2) run_jacobi_warp<T, 1, 4, 2>(L, c.zc, src, dst, r_arr, omega, inv_diag);
-    else if (c.vx == 1) run_jacobi_warp<T, 1, 4, 3>(L, c.zc, src, dst, r_arr, omega, inv_diag);
-    else if (c.vx == 2) run_jacobi_warp<T, 2, 4, 3>(L, c.zc, src, dst, r_arr, omega, inv_diag);
-    else run_jacobi_warp<T, 4, 4, 3>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    if (c.ty == 8) run_jacobi2<T, 8>(L, c.zc, src, dst, r_arr, omega, inv_diag);
+    else run_jacobi2<T, 4>(L, c.zc, src, dst, r_arr, omega, inv_diag);
   });
   return cudaGetLastError();
 }

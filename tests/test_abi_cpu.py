@@ -60,3 +60,17 @@ def test_errors_without_gpu_are_status_codes():
 def test_graft_entry_build_runs():
     import __graft_entry__
     __graft_entry__.build()
+
+
+def test_library_has_no_unresolved_internal_symbols():
+    """Every kernel launcher the runtime calls is defined in the library."""
+    import shutil
+    import subprocess
+    from paper_1201_2118_gb300 import build
+    path = build.build()
+    nm = shutil.which("nm")
+    if nm is None:
+        pytest.skip("nm not available")
+    out = subprocess.run([nm, "-D", "-C", path], capture_output=True, text=True).stdout
+    undefined = [l for l in out.splitlines() if " U " in l and "cfd::" in l]
+    assert not undefined, undefined

@@ -23,7 +23,7 @@ JACOBI_CONFIGS = [
     (1, 2, 16, 32, 4), (1, 4, 4, 16, 6), (1, 4, 4, 32, 4), (2, 4, 4, 1, 0), (2, 4, 4, 2, 0),
     (2, 4, 8, 1, 0), (2, 4, 2, 4, 0), (2, 2, 4, 2, 0), (2, 1, 8, 1, 0),
     (3, 4, 4, 32, 5), (3, 4, 8, 16, 6), (3, 4, 2, 32, 6), (3, 4, 4, 64, 6),
-    (4, 4, 4, 16, 1), (4, 4, 4, 32, 2), (4, 4, 4, 7, 3), (4, 1, 4, 8, 2), (4, 2, 4, 13, 3),
+    (5, 4, 4, 16, 0), (5, 4, 8, 32, 0),
 ]
 SIZES = [(45, 37, 21), (150, 77, 40)]
 
@@ -62,8 +62,7 @@ def test_jacobi_variant_matches_oracle(cfg, dims, bc):
 
 
 @pytest.mark.parametrize("cfg", [(1, 4, 8, 32, 4), (1, 2, 8, 16, 4), (0, 1, 8, 16, 4),
-                                 (2, 4, 4, 2, 0), (2, 1, 8, 1, 0), (3, 4, 4, 32, 5),
-                                 (4, 1, 4, 16, 3), (4, 4, 4, 8, 2)])
+                                 (2, 4, 4, 2, 0), (2, 1, 8, 1, 0), (3, 4, 4, 32, 5)])
 def test_jacobi_variant_on_block_set(cfg):
     from oracle import Oracle
     from paper_1201_2118_gb300 import Grid, P, R, WU, WV, WW, mask
@@ -200,7 +199,7 @@ def test_per_block_launch_mode_is_bitwise_identical(g):
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 @pytest.mark.parametrize("cfg", [(3, 8, 4, 32, 5), (3, 8, 8, 16, 6), (3, 8, 2, 64, 6),
-                                 (1, 4, 8, 32, 6), (2, 4, 4, 2, 0), (4, 4, 4, 16, 2)])
+                                 (1, 4, 8, 32, 6), (2, 4, 4, 2, 0)])
 def test_16bit_jacobi_variants_agree_with_register_sweep(dtype, cfg):
     """Every 16-bit sweep variant computes the same FP32 expression and
     rounds once, so it matches the register sweep to one rounding step."""
@@ -243,3 +242,46 @@ def test_stage_variants_match_oracle(stencil, order, g, bc):
     ref = o.stage(0.5, u, 0.5, u1, 0.013)
     for k, a in enumerate((WU, WV, WW)):
         assert rel_err(grid.download(a), o.interior(ref[k])) < 1e-5
+
+
+@pytest.mark.parametrize("cfg", [(5, 4, 4, 16, 0), (5, 4, 8, 7, 0), (5, 4, 4, 64, 0)])
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+@pytest.mark.parametrize("iters", [1, 2, 7, 10])
+@pytest.mark.parametrize("dims", [(128, 40, 21), (256, 16, 3)])
+def test_fused_two_sweep_launches_match_oracle(cfg, bc, iters, dims):
+    """Temporal blocking (two sweeps per launch, boundary-mapped reads) on
+    grids it applies to, odd counts included, against the oracle; ghost
+    faces of the result as the oracle's fill."""
+    from paper_1201_2118_gb300 import P, WU, WV, WW, mask
+    o, g, u, p = make_pair(dims, bc=bc, fields=rand(dims, 11))
+    g.set_kernel_config(jacobi=cfg)
+    w = rounded(rand(dims, 12))
+    for k, a in enumerate((WU, WV, WW)):
+        g.interior(a).copy_(g.torch.from_numpy(w["uvw"[k]]).float().cuda())
+    g.ghost_fill(mask(WU, WV, WW))
+    wo = [o.ghost_fill(o.embed(w["uvw"[k]]), k) for k in range(3)]
+    g.pressure_solve(0.05, iters)
+    r = o.divergence(wo, 0.05)
+    o.jacobi(p, r, iters)
+    assert rel_err(g.download(P), o.interior(p)) < 1e-5
+    gp = g.download(P, ghosts=True)
+    for ax in range(3):
+        for side in (0, -1):
+            sl = [slice(1, -1)] * 3
+            sl[2 - ax] = side
+            assert rel_err(gp[tuple(sl)], p[tuple(sl)]) < 1e-5
+    g.check()
+
+
+def test_fused_sweeps_in_full_steps_match_single_sweeps():
+    from paper_1201_2118_gb300 import U, V, W, P
+    n = (128, 64, 48)
+    h = (1.0 / 128,) * 3
+    res = []
+    for cfg in ((0, 4, 4, 32, 4), (5, 4, 4, 32, 0)):
+        o, g, u, p = make_pair(n, bc="cavity", h=h, nu=1e-3, fields=workloads.ldc_noise(n, seed=1))
+        g.set_kernel_config(jacobi=cfg)
+        g.step(workloads.cfl_dt(h), 3)
+        res.append([g.download(a) for a in (U, V, W, P)])
+    for a, b in zip(*res):
+        assert rel_err(a, b) < 1e-5
