@@ -244,7 +244,9 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
  * sweep (vx 4 for FP32, 8 for 16-bit storage; ty in {4,8} with stages in
  * {5,6}, or ty 2 with 6 stages), kind 5 two fused sweeps per launch (temporal blocking;
  * ty in {4,8}; used on single-block grids with nx % 128 == 0 and
- * ny % ty == 0, other grids and odd sweep counts take single sweeps);
+ * ny % ty == 0, other grids and odd sweep counts take single sweeps),
+ * kind 7 the warp-specialised TMA sweep (a producer warp fills an S-stage
+ * ring, ty consumer warps; vx 4, ty in {4,8,16}, stages in {6,8});
  * zc = z-planes per tile.
  * stencil = {ty in {4,8}, zc, tile_tz in {0,2,4}} for the point kernels: rows
  * per CTA, z chunk, and for the RHS + stage kernel either neighbour reads

@@ -65,6 +65,8 @@ struct Launch {
 //   kind 1: TMA-staged sweep (tensor maps per block, S-stage mbarrier ring)
 //   kind 2: direct sweep (no shared memory; zc = z-planes per CTA, TZ)
 //   kind 3: cp.async-staged sweep (per-thread async copies, S-stage ring)
+//   kind 7: warp-specialised TMA sweep (producer warp, empty/full mbarriers,
+//           no CTA barrier per plane)
 //   kind 5: two fused sweeps per launch (temporal blocking, single block,
 //           nx % 128 == 0, ny % ty == 0); odd counts end with one kind-0 sweep
 struct JacobiCfg { int kind, vx, ty, zc, stages; };

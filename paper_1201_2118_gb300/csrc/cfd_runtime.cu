@@ -205,7 +205,7 @@ cfd_status upload_tables(cfd_grid* g) {
 // Tensor maps of the TMA Jacobi sweep (box sizes depend on the config).
 cfd_status refresh_maps(cfd_grid* g) {
   g->maps_ready = false;
-  if (g->jcfg.kind != 1 || !g->base) return CFD_OK;
+  if ((g->jcfg.kind != 1 && g->jcfg.kind != 7) || !g->base) return CFD_OK;
   std::vector<TmaArray> arrs;
   const int ids[3] = {A_P, A_P2, A_R};
   for (const auto& b : g->hb)
@@ -362,7 +362,7 @@ bool fused_ok(const cfd_grid* g) {
 // variant's single sweeps use the register/shuffle kernel).
 cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst) {
   if (g->jcfg.kind == 5) return launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, src, dst, A_R, (float)g->omega);
-  if (g->jcfg.kind == 1 && g->maps_ready)
+  if ((g->jcfg.kind == 1 || g->jcfg.kind == 7) && g->maps_ready)
     return launch_jacobi_tma(L, g->jcfg, g->base + g->maps_off, src == A_P ? 0 : 1, dst,
                              (float)g->omega);
   if (g->jcfg.kind == 2) return launch_jacobi_direct(L, g->jcfg, src, dst, A_R, (float)g->omega);
@@ -820,7 +820,9 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
                      (((c.ty == 4 || c.ty == 8) && (c.stages == 5 || c.stages == 6)) ||
                       (c.ty == 2 && c.stages == 6));
     const bool ok5 = c.kind == 5 && (c.ty == 4 || c.ty == 8);
-    if (!(ok0 || ok1 || ok2 || ok3 || ok5) || c.zc < 1)
+    const bool ok7 = c.kind == 7 && c.vx == 4 && (c.ty == 4 || c.ty == 8 || c.ty == 16) &&
+                     (c.stages == 6 || c.stages == 8);
+    if (!(ok0 || ok1 || ok2 || ok3 || ok5 || ok7) || c.zc < 1)
       return fail(CFD_EINVAL, "unsupported Jacobi config");
     g->jcfg = c;
     cfd_status s = refresh_maps(g);
@@ -870,6 +872,9 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
     cands.push_back({0, 1, 8, zc, 4});
   }
   cands.push_back({0, 2, 8, 32, 4});
+  for (int zc : {16, 32, 64, 128})
+    for (int ty : {4, 8, 16})
+      for (int st : {6, 8}) cands.push_back({7, 4, ty, zc, st});
   if (g->nblocks == 1)
     for (int zc : {16, 32, 64, 128})
       for (int ty : {4, 8}) cands.push_back({5, 4, ty, zc, 0});
@@ -893,7 +898,7 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   float best_ms = 1e30f;
   for (const auto& c : cands) {
     g->jcfg = c;
-    if (refresh_maps(g) != CFD_OK || (c.kind == 1 && !g->maps_ready)) continue;
+    if (refresh_maps(g) != CFD_OK || ((c.kind == 1 || c.kind == 7) && !g->maps_ready)) continue;
     float ms = 0.f;
     if ((s = time_region(g, 1, &ms, 0)) != CFD_OK) return s;  // warm-up
     if ((s = time_region(g, 5, &ms, 0)) != CFD_OK) return s;
@@ -936,7 +941,7 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
 cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[3]) {
   if (!g) return fail(CFD_EINVAL, "null grid");
   if (jacobi) {
-    jacobi[0] = g->jcfg.kind == 1 && !g->maps_ready ? 0 : g->jcfg.kind;
+    jacobi[0] = (g->jcfg.kind == 1 || g->jcfg.kind == 7) && !g->maps_ready ? 0 : g->jcfg.kind;
     jacobi[1] = g->jcfg.vx;
     jacobi[2] = g->jcfg.ty;
     jacobi[3] = g->jcfg.zc;

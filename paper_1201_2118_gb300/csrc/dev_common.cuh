@@ -1,0 +1,214 @@
+// Device helpers shared by the stencil translation units: storage-type
+// conversion (fields are stored as FP32, BF16 or FP16 and always computed in
+// FP32), VX-wide vector access, and the ghost-on-write images of pressure
+// face cells.
+#pragma once
+#include <cuda_bf16.h>
+#include <cuda_fp16.h>
+
+#include "cfd_internal.h"
+
+namespace cfd {
+namespace {
+
+// ------------------------------------------------------------ storage types
+
+template <typename T> __device__ __forceinline__ float ldf(const T* p);
+template <> __device__ __forceinline__ float ldf<float>(const float* p) { return __ldg(p); }
+template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p) {
+  return __bfloat162float(__ldg(p));
+}
+template <> __device__ __forceinline__ float ldf<__half>(const __half* p) {
+  return __half2float(__ldg(p));
+}
+
+template <typename T> __device__ __forceinline__ T cvt(float x);
+template <> __device__ __forceinline__ float cvt<float>(float x) { return x; }
+template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) {
+  return __float2bfloat16_rn(x);
+}
+template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
+
+// VX consecutive elements as one aligned vector load / store.
+template <typename T, int VX> struct alignas(sizeof(T) * VX) Vec { T v[VX]; };
+
+__device__ __forceinline__ float tof(float x) { return x; }
+__device__ __forceinline__ float tof(__nv_bfloat16 x) { return __bfloat162float(x); }
+__device__ __forceinline__ float tof(__half x) { return __half2float(x); }
+
+template <int VX, typename T>
+__device__ __forceinline__ void ldv(const T* p, float (&out)[VX]) {
+  const Vec<T, VX> x = *reinterpret_cast<const Vec<T, VX>*>(p);
+#pragma unroll
+  for (int e = 0; e < VX; ++e) out[e] = tof(x.v[e]);
+}
+
+template <typename T, int VX>
+__device__ __forceinline__ void stv(T* p, const float (&in)[VX]) {
+  Vec<T, VX> x;
+#pragma unroll
+  for (int e = 0; e < VX; ++e) x.v[e] = cvt<T>(in[e]);
+  *reinterpret_cast<Vec<T, VX>*>(p) = x;
+}
+
+template <typename T>
+struct Fld {
+  const T* p;
+  int py;
+  long long pz;
+  __device__ __forceinline__ float operator()(int i, int j, int k) const {
+    return ldf<T>(p + (long long)k * pz + (long long)j * py + i);
+  }
+};
+
+template <typename T>
+__device__ __forceinline__ Fld<T> fld(const Launch& L, const BlockDev& B, int arr) {
+  return Fld<T>{reinterpret_cast<const T*>(L.base) + B.org[arr], B.py, B.pz};
+}
+
+template <typename T>
+__device__ __forceinline__ T* wptr(const Launch& L, const BlockDev& B, int arr) {
+  return reinterpret_cast<T*>(L.base) + B.org[arr];
+}
+
+// ------------------------------------------------------- ghost-on-write
+//
+// A Jacobi sweep writes each new face value of p also into the first ghost
+// layer where the next sweep reads it: across a periodic or block-to-block
+// face into the neighbour block's ghost cell, at a wall into the own ghost
+// cell (homogeneous Neumann, p_ghost = p_face).  Edges and corners of the
+// ghost layer are never read by the 7-point operator and are not written.
+
+template <typename T>
+__device__ __forceinline__ void p_ghost_images(const Launch& L, const BlockDev& B, int dst,
+                                               int i, int j, int k, T val) {
+  const int q[3] = {i, j, k};
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+#pragma unroll
+    for (int side = 0; side < 2; ++side) {
+      const int face = 2 * d + side;
+      if (q[d] != (side == 0 ? 0 : B.n[d] - 1)) continue;
+      int t[3] = {q[0], q[1], q[2]};
+      const BlockDev* D = &B;
+      if (B.bc[face] == BC_PERIODIC) {
+        D = &L.blocks[B.nbr[face]];
+        t[d] = side == 0 ? D->n[d] : -1;
+      } else {
+        t[d] = side == 0 ? -1 : B.n[d];
+      }
+      wptr<T>(L, *D, dst)[(long long)t[2] * D->pz + (long long)t[1] * D->py + t[0]] = val;
+    }
+  }
+}
+
+// The x- and y-face images of one x-row of a z-column are found once per
+// tile and kept in shared memory: entry f of a row (0: x low, 1: x high,
+// 2: y low, 3: y high) holds the address of the image of cell (x_f, j, 0)
+// and the z pitch of the block it lies in, so the per-plane work is one
+// store per image.  z-face images (first and last plane of a block) use
+// p_ghost_images.
+template <typename T>
+struct RowImage {
+  T* p;
+  long long pz;
+};
+
+template <typename T, int FACE>
+__device__ __forceinline__ void face_image(const Launch& L, const BlockDev& B, int dst, int ti,
+                                           int tj, RowImage<T>& out) {
+  constexpr bool hi = FACE & 1;
+  const BlockDev* D = &B;
+  int t;
+  if (B.bc[FACE] == BC_PERIODIC) {
+    D = &L.blocks[B.nbr[FACE]];
+    t = hi ? -1 : D->n[FACE >> 1];
+  } else {
+    t = hi ? B.n[FACE >> 1] : -1;
+  }
+  if (FACE < 2) ti = t; else tj = t;
+  out.p = wptr<T>(L, *D, dst) + (long long)tj * D->py + ti;
+  out.pz = D->pz;
+}
+
+// Fills the four entries of row j for x-row cells x0 .. x0 + w - 1 (the
+// x-tile of the calling warp) and returns the mask of those that exist.
+template <typename T>
+__device__ __forceinline__ unsigned row_images(const Launch& L, const BlockDev& B, int dst,
+                                               int x0, int w, int j, RowImage<T>* e) {
+  const int nx = B.n[0], ny = B.n[1];
+  unsigned m = 0;
+  if (j >= ny || x0 >= nx) return 0;
+  if (x0 == 0) { face_image<T, 0>(L, B, dst, 0, j, e[0]); m |= 1u; }
+  if (x0 + w > nx - 1) { face_image<T, 1>(L, B, dst, nx - 1, j, e[1]); m |= 2u; }
+  if (j == 0) { face_image<T, 2>(L, B, dst, x0, j, e[2]); m |= 4u; }
+  if (j == ny - 1) { face_image<T, 3>(L, B, dst, x0, j, e[3]); m |= 8u; }
+  return m;
+}
+
+// z-face images of cell (i, j, k) for k == 0 or k == n_z - 1.
+template <typename T>
+__device__ __forceinline__ void p_ghost_z(const Launch& L, const BlockDev& B, int dst, int i,
+                                          int j, int k, T val) {
+#pragma unroll
+  for (int side = 0; side < 2; ++side) {
+    const int face = 4 + side;
+    if (k != (side == 0 ? 0 : B.n[2] - 1)) continue;
+    const BlockDev* D = &B;
+    int t;
+    if (B.bc[face] == BC_PERIODIC) {
+      D = &L.blocks[B.nbr[face]];
+      t = side == 0 ? D->n[2] : -1;
+    } else {
+      t = side == 0 ? -1 : B.n[2];
+    }
+    wptr<T>(L, *D, dst)[(long long)t * D->pz + (long long)j * D->py + i] = val;
+  }
+}
+
+// Per-thread share of a row's images: bit f of the result says that the
+// thread writes image f (the x images belong to the lanes holding x = 0 and
+// x = n_x - 1, the y images to every lane with cells in the row).  i is the
+// thread's first cell, VX cells per thread.
+template <int VX>
+__device__ __forceinline__ unsigned thread_images(unsigned row_mask, int lane, int i, int nx) {
+  if (i >= nx) return 0;
+  unsigned m = row_mask & 12u;
+  if ((row_mask & 1u) && lane == 0) m |= 1u;
+  if ((row_mask & 2u) && nx - 1 < i + VX) m |= 2u;
+  return m;
+}
+
+// Writes the images the thread owns for plane k; xl = i - x0 is the
+// thread's offset in the row tile, nv its number of cells inside the block.
+template <typename T, int VX>
+__device__ __forceinline__ void put_row_images(const RowImage<T>* e, unsigned tm, int k, int xl,
+                                               int nv, const float (&out)[VX]) {
+  if (tm & 1u) e[0].p[k * e[0].pz] = cvt<T>(out[0]);
+  if (tm & 2u) {
+    // out[nv - 1] as a chain of selects (a C++ select chain is turned into
+    // an indexed load from a local-memory copy of out)
+    float v = out[0];
+#pragma unroll
+    for (int q = 1; q < VX; ++q)
+      asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, %0, p;\n\t}"
+          : "+f"(v)
+          : "f"(out[q]), "r"(nv - 1), "r"(q));
+    e[1].p[k * e[1].pz] = cvt<T>(v);
+  }
+#pragma unroll
+  for (int f = 2; f < 4; ++f)
+    if (tm & (1u << f)) {
+      T* p = e[f].p + k * e[f].pz + xl;
+      if (nv >= VX) {
+        stv<T, VX>(p, out);
+      } else {
+#pragma unroll
+        for (int q = 0; q < VX; ++q)
+          if (q < nv) p[q] = cvt<T>(out[q]);
+      }
+    }
+}
+
+}  // namespace
+}  // namespace cfd

@@ -23,39 +23,11 @@
 #include <cstring>
 
 #include "cfd_internal.h"
+#include "dev_common.cuh"
 #include "tiles.cuh"
 
 namespace cfd {
 namespace {
-
-__device__ __forceinline__ float tof(float x) { return x; }
-__device__ __forceinline__ float tof(__nv_bfloat16 x) { return __bfloat162float(x); }
-__device__ __forceinline__ float tof(__half x) { return __half2float(x); }
-
-template <typename T> __device__ __forceinline__ T cvt(float x);
-template <> __device__ __forceinline__ float cvt<float>(float x) { return x; }
-template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) {
-  return __float2bfloat16_rn(x);
-}
-template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
-
-template <typename T, int VX> struct alignas(sizeof(T) * VX) Vec { T v[VX]; };
-
-template <int VX, typename T>
-__device__ __forceinline__ void ldv(const T* p, float (&out)[VX]) {
-  const Vec<T, VX> x = *reinterpret_cast<const Vec<T, VX>*>(p);
-#pragma unroll
-  for (int e = 0; e < VX; ++e) out[e] = tof(x.v[e]);
-}
-
-template <typename T, int VX>
-__device__ __forceinline__ void stv(T* p, const float (&in)[VX]) {
-  Vec<T, VX> x;
-#pragma unroll
-  for (int e = 0; e < VX; ++e) x.v[e] = cvt<T>(in[e]);
-  *reinterpret_cast<Vec<T, VX>*>(p) = x;
-}
-
 
 // ------------------------------------------------------------- PTX helpers
 
@@ -106,30 +78,6 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
-template <typename T>
-__device__ __forceinline__ void p_ghost_images(const Launch& L, const BlockDev& B, int dst, int i,
-                                               int j, int k, T val) {
-  const int q[3] = {i, j, k};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int face = 2 * d + side;
-      if (q[d] != (side == 0 ? 0 : B.n[d] - 1)) continue;
-      int t[3] = {q[0], q[1], q[2]};
-      const BlockDev* D = &B;
-      if (B.bc[face] == BC_PERIODIC) {
-        D = &L.blocks[B.nbr[face]];
-        t[d] = side == 0 ? D->n[d] : -1;
-      } else {
-        t[d] = side == 0 ? -1 : B.n[d];
-      }
-      T* out = reinterpret_cast<T*>(L.base) + D->org[dst];
-      out[(long long)t[2] * D->pz + (long long)t[1] * D->py + t[0]] = val;
-    }
-  }
-}
-
 template <typename T, int VX, int TY>
 struct TmaGeom {
   static constexpr int TX = 32 * VX;
@@ -152,6 +100,7 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
   extern __shared__ __align__(128) unsigned char smem[];
   // S stages of (p box, r box), then the S mbarriers
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S * Gm::STAGE);
+  __shared__ RowImage<T> rimg[TY][4];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const int tid = ty * 32 + lane;
   if (smem_u32(smem) & 127u) {  // TMA destinations need 128-byte alignment
@@ -223,9 +172,13 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
     T* Q = reinterpret_cast<T*>(L.base) + B.org[dst];
     const int x0 = i0 + xl;
     const bool full_vec = x0 + VX <= nx;
-    const bool x_face = (x0 == 0) || (x0 <= nx - 1 && nx - 1 < x0 + VX);
     const bool row_ok = j < ny && x0 < nx;
-    const bool face_xj = x_face || j == 0 || j == ny - 1;
+    __syncwarp();
+    unsigned rm = 0;
+    if (lane == 0) rm = row_images<T>(L, B, dst, i0, TX, j, rimg[ty]);
+    const unsigned tm = thread_images<VX>(__shfl_sync(0xffffffffu, rm, 0), lane, x0, nx);
+    const int nv = min(VX, nx - x0);
+    __syncwarp();
     T* qrow = Q + (long long)(k0 - 1) * pzl + (long long)j * pyl + x0;
     for (int k = k0; k < k1; ++k) {
       const int q = k - k0 + 1;
@@ -259,10 +212,11 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
           for (int e = 0; e < VX; ++e)
             if (x0 + e < nx) qrow[e] = cvt<T>(out[e]);
         }
-        if (face_xj || k == 0 || k == nz - 1) {
+        if (tm) put_row_images<T, VX>(rimg[ty], tm, k, xl, nv, out);
+        if (k == 0 || k == nz - 1) {
 #pragma unroll
           for (int e = 0; e < VX; ++e)
-            if (x0 + e < nx) p_ghost_images<T>(L, B, dst, x0 + e, j, k, cvt<T>(out[e]));
+            if (x0 + e < nx) p_ghost_z<T>(L, B, dst, x0 + e, j, k, cvt<T>(out[e]));
         }
       }
 #pragma unroll
@@ -291,6 +245,195 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
     }
     sbase = (sbase + np) % S;
   }
+}
+
+// Warp-specialised TMA sweep: warp TY of the CTA is the producer (one lane
+// issues the TMA loads of each plane into an S-stage ring, waiting on the
+// stage's "empty" mbarrier), warps 0..TY-1 are consumers, one row of 32 VX
+// cells each.  A consumer waits only on the "full" mbarrier of the plane it
+// needs next and, once it no longer reads a plane, arrives on that stage's
+// empty barrier (count TY), so consumer warps never wait for each other and
+// there is no CTA-wide barrier per plane.  Plane f of the CTA's sequence
+// (over all its tiles) lives in stage f % S; its full barrier completes
+// phase f / S, its empty barrier is waited with the opposite parity so the
+// first pass through the ring does not wait.
+
+__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
+  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
+}
+
+template <typename T, int VX, int TY, int S>
+__global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUtensorMap* maps,
+                                                             int zc, int src_slot, int dst,
+                                                             float omega, float inv_diag) {
+  using Gm = TmaGeom<T, VX, TY>;
+  constexpr int TX = Gm::TX, HX = Gm::HX, PW = Gm::PW;
+  extern __shared__ __align__(128) unsigned char smem[];
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S * Gm::STAGE);
+  unsigned long long* empty = full + S;
+  __shared__ RowImage<T> rimg[TY][4];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  if (smem_u32(smem) & 127u) {
+    if (w == 0 && lane == 0) atomicOr(L.err_flag, 4);
+    return;
+  }
+  if (w == 0 && lane == 0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), TY);
+    }
+    mbar_fence_init();
+  }
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, zc);  // also orders the barrier init before use
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  const int g = L.ghost;
+  constexpr int xo = kAlignBytes / (int)sizeof(T);
+  unsigned seq = 0;     // planes of this CTA so far
+  unsigned issued = 0;  // planes the producer has issued
+  bool bad = false;
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int k1 = min(k0 + zc, nz);
+    const int np = k1 - k0 + 2;  // planes k0 - 1 .. k1
+    if (w == TY) {
+      // ---------------- producer
+      if (lane == 0) {
+        const CUtensorMap* mp = maps + 3 * blk + src_slot;
+        const CUtensorMap* mr = maps + 3 * blk + 2;
+        const int px = xo + i0 - HX, pyc = g + j0 - 1, rx = xo + i0, ry = g + j0;
+        for (int q = 0; q < np && !bad; ++q) {
+          const unsigned f = seq + q;
+          const int s = f % S;
+          bad |= !mbar_wait(smem_u32(&empty[s]), ((f / S) & 1u) ^ 1u);
+          if (bad) break;
+          ++issued;
+          const int z = g + k0 - 1 + q;
+          const bool need_r = (q >= 1 && q <= np - 2);
+          const uint32_t bar = smem_u32(&full[s]);
+          mbar_expect_tx(bar, Gm::PBYTES + (need_r ? Gm::RBYTES : 0));
+          tma_load_3d(smem_u32(smem + s * Gm::STAGE), mp, px, pyc, z, bar);
+          if (need_r) tma_load_3d(smem_u32(smem + s * Gm::STAGE + Gm::PSTRIDE), mr, rx, ry, z, bar);
+        }
+      }
+      seq += np;
+      if (bad) break;
+      continue;
+    }
+    // ---------------- consumers (warp w = row j0 + w)
+    auto stage = [&](unsigned f) { return reinterpret_cast<const T*>(smem + (f % S) * Gm::STAGE); };
+    auto wait_full = [&](unsigned f) {
+      bad |= !mbar_wait(smem_u32(&full[f % S]), (f / S) & 1u);
+    };
+    auto release = [&](unsigned f) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[f % S]));
+    };
+    const int j = j0 + w;
+    const int xl = lane * VX;
+    const int row = (w + 1) * PW + HX + xl;
+    const long long pzl = B.pz;
+    const int pyl = B.py;
+    const int x0 = i0 + xl;
+    const bool row_ok = j < ny && x0 < nx;
+    const bool full_vec = x0 + VX <= nx;
+    __syncwarp();
+    unsigned rm = 0;
+    if (lane == 0) rm = row_images<T>(L, B, dst, i0, TX, j, rimg[w]);
+    const unsigned tm = thread_images<VX>(__shfl_sync(0xffffffffu, rm, 0), lane, x0, nx);
+    const int nv = min(VX, nx - x0);
+    __syncwarp();
+    T* qrow = reinterpret_cast<T*>(L.base) + B.org[dst] + (long long)(k0 - 1) * pzl +
+              (long long)j * pyl + x0;
+    float m[VX], c[VX];
+    wait_full(seq);
+    wait_full(seq + 1);
+    ldv<VX>(stage(seq) + row, m);
+    ldv<VX>(stage(seq + 1) + row, c);
+    release(seq);
+    for (int q = 1; q <= np - 2; ++q) {
+      const unsigned f = seq + q;
+      wait_full(f + 1);
+      if (bad) break;
+      const T* Pq = stage(f);
+      const T* Pn = stage(f + 1);
+      const T* Rq = Pq + Gm::PSTRIDE / (int)sizeof(T);
+      float zp[VX], up[VX], dn[VX], rr[VX];
+      ldv<VX>(Pn + row, zp);
+      ldv<VX>(Pq + row + PW, up);
+      ldv<VX>(Pq + row - PW, dn);
+      ldv<VX>(Rq + w * TX + xl, rr);
+      float left = __shfl_up_sync(0xffffffffu, c[VX - 1], 1);
+      float right = __shfl_down_sync(0xffffffffu, c[0], 1);
+      if (lane == 0) left = tof(Pq[row - 1]);
+      if (lane == 31) right = tof(Pq[row + VX]);
+      release(f);
+      float out[VX];
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        const float xm = e == 0 ? left : c[e - 1];
+        const float xp = e == VX - 1 ? right : c[e + 1];
+        const float nb = (xm + xp) * cx + (dn[e] + up[e]) * cy + (m[e] + zp[e]) * cz;
+        out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+      }
+      const int k = k0 + q - 1;
+      qrow += pzl;
+      if (row_ok) {
+        if (full_vec) {
+          stv<T, VX>(qrow, out);
+        } else {
+#pragma unroll
+          for (int e = 0; e < VX; ++e)
+            if (x0 + e < nx) qrow[e] = cvt<T>(out[e]);
+        }
+        if (tm) put_row_images<T, VX>(rimg[w], tm, k, xl, nv, out);
+        if (k == 0 || k == nz - 1) {
+#pragma unroll
+          for (int e = 0; e < VX; ++e)
+            if (x0 + e < nx) p_ghost_z<T>(L, B, dst, x0 + e, j, k, cvt<T>(out[e]));
+        }
+      }
+#pragma unroll
+      for (int e = 0; e < VX; ++e) {
+        m[e] = c[e];
+        c[e] = zp[e];
+      }
+    }
+    release(seq + np - 1);
+    seq += np;
+    if (bad) break;
+  }
+  if (bad && lane == 0) atomicOr(L.err_flag, 2);
+  if (w == TY && lane == 0)  // never leave with our own copies in flight
+    for (unsigned f = issued > (unsigned)S ? issued - S : 0; f < issued; ++f)
+      mbar_wait(smem_u32(&full[f % S]), (f / S) & 1u);
+}
+
+template <typename T, int VX, int TY, int S>
+cudaError_t run_ws(const Launch& L, const JacobiCfg& c, const void* maps, int src_slot, int dst,
+                   float omega, float inv_diag) {
+  using Gm = TmaGeom<T, VX, TY>;
+  auto kern = k_jacobi_ws<T, VX, TY, S>;
+  const int smem = S * Gm::STAGE + 16 * S;
+  static int occ = -1;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (TY + 1), smem) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+  }
+  const long long tiles = count_tiles(L, Gm::TX, TY, c.zc);
+  long long grid = (long long)L.sms * occ;
+  if (tiles < grid) grid = tiles;
+  kern<<<(unsigned)(grid > 0 ? grid : 1), dim3(32, TY + 1), smem, L.stream>>>(
+      L, static_cast<const CUtensorMap*>(maps), c.zc, src_slot, dst, omega, inv_diag);
+  return cudaGetLastError();
 }
 
 template <typename T, int VX, int TY, int S>
@@ -371,6 +514,17 @@ cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* m
                               int src_slot, int dst, float omega) {
   const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
   cudaError_t e = cudaErrorInvalidValue;
+  if (c.kind == 7) {
+    CFD_DISPATCH_T(L.dtype, {
+      if (c.ty == 4 && c.stages == 8) e = run_ws<T, 4, 4, 8>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+      else if (c.ty == 4) e = run_ws<T, 4, 4, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+      else if (c.ty == 8 && c.stages == 8) e = run_ws<T, 4, 8, 8>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+      else if (c.ty == 8) e = run_ws<T, 4, 8, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+      else if (c.stages == 8) e = run_ws<T, 4, 16, 8>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+      else e = run_ws<T, 4, 16, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    });
+    return e;
+  }
   CFD_DISPATCH_T(L.dtype, {
     if (c.vx == 4 && c.ty == 4 && c.stages == 4) e = run<T, 4, 4, 4>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
     else if (c.vx == 4 && c.ty == 4) e = run<T, 4, 4, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);

@@ -10,70 +10,11 @@
 #include <cuda_fp16.h>
 
 #include "cfd_internal.h"
+#include "dev_common.cuh"
 #include "tiles.cuh"
 
 namespace cfd {
 namespace {
-
-// ------------------------------------------------------------ storage types
-
-template <typename T> __device__ __forceinline__ float ldf(const T* p);
-template <> __device__ __forceinline__ float ldf<float>(const float* p) { return __ldg(p); }
-template <> __device__ __forceinline__ float ldf<__nv_bfloat16>(const __nv_bfloat16* p) {
-  return __bfloat162float(__ldg(p));
-}
-template <> __device__ __forceinline__ float ldf<__half>(const __half* p) {
-  return __half2float(__ldg(p));
-}
-
-template <typename T> __device__ __forceinline__ T cvt(float x);
-template <> __device__ __forceinline__ float cvt<float>(float x) { return x; }
-template <> __device__ __forceinline__ __nv_bfloat16 cvt<__nv_bfloat16>(float x) {
-  return __float2bfloat16_rn(x);
-}
-template <> __device__ __forceinline__ __half cvt<__half>(float x) { return __float2half_rn(x); }
-
-// VX consecutive elements as one aligned vector load / store.
-template <typename T, int VX> struct alignas(sizeof(T) * VX) Vec { T v[VX]; };
-
-__device__ __forceinline__ float tof(float x) { return x; }
-__device__ __forceinline__ float tof(__nv_bfloat16 x) { return __bfloat162float(x); }
-__device__ __forceinline__ float tof(__half x) { return __half2float(x); }
-
-template <int VX, typename T>
-__device__ __forceinline__ void ldv(const T* p, float (&out)[VX]) {
-  const Vec<T, VX> x = *reinterpret_cast<const Vec<T, VX>*>(p);
-#pragma unroll
-  for (int e = 0; e < VX; ++e) out[e] = tof(x.v[e]);
-}
-
-template <typename T, int VX>
-__device__ __forceinline__ void stv(T* p, const float (&in)[VX]) {
-  Vec<T, VX> x;
-#pragma unroll
-  for (int e = 0; e < VX; ++e) x.v[e] = cvt<T>(in[e]);
-  *reinterpret_cast<Vec<T, VX>*>(p) = x;
-}
-
-template <typename T>
-struct Fld {
-  const T* p;
-  int py;
-  long long pz;
-  __device__ __forceinline__ float operator()(int i, int j, int k) const {
-    return ldf<T>(p + (long long)k * pz + (long long)j * py + i);
-  }
-};
-
-template <typename T>
-__device__ __forceinline__ Fld<T> fld(const Launch& L, const BlockDev& B, int arr) {
-  return Fld<T>{reinterpret_cast<const T*>(L.base) + B.org[arr], B.py, B.pz};
-}
-
-template <typename T>
-__device__ __forceinline__ T* wptr(const Launch& L, const BlockDev& B, int arr) {
-  return reinterpret_cast<T*>(L.base) + B.org[arr];
-}
 
 // ------------------------------------------------------------------ ghosts
 //
@@ -438,34 +379,12 @@ __global__ void __launch_bounds__(32 * TY) k_copy(Launch L, int zc, int src, int
 // the mirror ghost for a zero-gradient wall).  Each such ghost cell has one
 // owner, so there is no separate halo launch per sweep.
 
-template <typename T>
-__device__ __forceinline__ void p_ghost_images(const Launch& L, const BlockDev& B, int dst,
-                                               int i, int j, int k, T val) {
-  const int q[3] = {i, j, k};
-#pragma unroll
-  for (int d = 0; d < 3; ++d) {
-#pragma unroll
-    for (int side = 0; side < 2; ++side) {
-      const int face = 2 * d + side;
-      if (q[d] != (side == 0 ? 0 : B.n[d] - 1)) continue;
-      int t[3] = {q[0], q[1], q[2]};
-      const BlockDev* D = &B;
-      if (B.bc[face] == BC_PERIODIC) {
-        D = &L.blocks[B.nbr[face]];
-        t[d] = side == 0 ? D->n[d] : -1;
-      } else {
-        t[d] = side == 0 ? -1 : B.n[d];
-      }
-      wptr<T>(L, *D, dst)[(long long)t[2] * D->pz + (long long)t[1] * D->py + t[0]] = val;
-    }
-  }
-}
-
 template <typename T, int VX, int TY>
 __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, int dst,
                                                     int r_arr, float omega, float inv_diag) {
   constexpr int TX = 32 * VX;
   __shared__ __align__(16) float sm[TY + 2][TX];
+  __shared__ RowImage<T> rimg[TY][4];
   const int lane = threadIdx.x, ty = threadIdx.y;
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
   __shared__ TileTable tt;
@@ -483,6 +402,12 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, i
     T* Q = wptr<T>(L, B, dst);
     const int i = i0 + lane * VX;
     const int j = j0 + ty;
+    __syncwarp();
+    unsigned rm = 0;
+    if (lane == 0) rm = row_images<T>(L, B, dst, i0, TX, j, rimg[ty]);
+    const unsigned tm = thread_images<VX>(__shfl_sync(0xffffffffu, rm, 0), lane, i, nx);
+    const int nv = min(VX, nx - i);
+    __syncwarp();
     const int k1 = min(k0 + zc, nz);
     // loads stay inside allocated rows: columns up to nx (first ghost) and
     // rows up to ny (first ghost) are what the interior outputs need
@@ -586,13 +511,11 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, i
           for (int e = 0; e < VX; ++e)
             if (i + e < nx) qrow[e] = cvt<T>(out[e]);
         }
-        const bool face_k = (k == 0) || (k == nz - 1);
-        const bool face_j = (j == 0) || (j == ny - 1);
+        if (tm) put_row_images<T, VX>(rimg[ty], tm, k, lane * VX, nv, out);
+        if (k == 0 || k == nz - 1) {
 #pragma unroll
-        for (int e = 0; e < VX; ++e) {
-          const int x = i + e;
-          if (x < nx && (face_k || face_j || x == 0 || x == nx - 1))
-            p_ghost_images<T>(L, B, dst, x, j, k, cvt<T>(out[e]));
+          for (int e = 0; e < VX; ++e)
+            if (i + e < nx) p_ghost_z<T>(L, B, dst, i + e, j, k, cvt<T>(out[e]));
         }
       }
       __syncthreads();

@@ -24,8 +24,13 @@ JACOBI_CONFIGS = [
     (2, 4, 8, 1, 0), (2, 4, 2, 4, 0), (2, 2, 4, 2, 0), (2, 1, 8, 1, 0),
     (3, 4, 4, 32, 5), (3, 4, 8, 16, 6), (3, 4, 2, 32, 6), (3, 4, 4, 64, 6),
     (5, 4, 4, 16, 0), (5, 4, 8, 32, 0),
+    (7, 4, 4, 16, 6), (7, 4, 8, 32, 8), (7, 4, 16, 128, 6), (7, 4, 4, 7, 8),
 ]
 SIZES = [(45, 37, 21), (150, 77, 40)]
+
+
+def cfg_id(c):
+    return "k" + "_".join(map(str, c))
 
 
 def rand(dims, seed):
@@ -33,7 +38,7 @@ def rand(dims, seed):
     return {c: rng.uniform(-1, 1, dims[::-1]) for c in "uvwp"}
 
 
-@pytest.mark.parametrize("cfg", JACOBI_CONFIGS)
+@pytest.mark.parametrize("cfg", JACOBI_CONFIGS, ids=cfg_id)
 @pytest.mark.parametrize("dims", SIZES)
 @pytest.mark.parametrize("bc", ["periodic", "cavity"])
 def test_jacobi_variant_matches_oracle(cfg, dims, bc):
@@ -62,7 +67,8 @@ def test_jacobi_variant_matches_oracle(cfg, dims, bc):
 
 
 @pytest.mark.parametrize("cfg", [(1, 4, 8, 32, 4), (1, 2, 8, 16, 4), (0, 1, 8, 16, 4),
-                                 (2, 4, 4, 2, 0), (2, 1, 8, 1, 0), (3, 4, 4, 32, 5)])
+                                 (2, 4, 4, 2, 0), (2, 1, 8, 1, 0), (3, 4, 4, 32, 5),
+                                 (7, 4, 8, 32, 6)], ids=cfg_id)
 def test_jacobi_variant_on_block_set(cfg):
     from oracle import Oracle
     from paper_1201_2118_gb300 import Grid, P, R, WU, WV, WW, mask
@@ -199,7 +205,8 @@ def test_per_block_launch_mode_is_bitwise_identical(g):
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 @pytest.mark.parametrize("cfg", [(3, 8, 4, 32, 5), (3, 8, 8, 16, 6), (3, 8, 2, 64, 6),
-                                 (1, 4, 8, 32, 6), (2, 4, 4, 2, 0)])
+                                 (1, 4, 8, 32, 6), (2, 4, 4, 2, 0), (7, 4, 8, 32, 8)],
+                         ids=cfg_id)
 def test_16bit_jacobi_variants_agree_with_register_sweep(dtype, cfg):
     """Every 16-bit sweep variant computes the same FP32 expression and
     rounds once, so it matches the register sweep to one rounding step."""
