@@ -36,7 +36,8 @@ import workloads  # noqa: E402
 METRIC = "GLUP/s and HBM GB/s vs peak per sweep; batched/bf16 vs plain; adjoint/fwd ratio"
 UNIT = "GLUP/s"
 JACOBI_BYTES_PER_CELL = {"f32": 12, "bf16": 6, "f16": 6}
-KERNEL_SRC = os.path.join(ROOT, "paper_1201_2118_gb300", "csrc", "stencil_kernels.cu")
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1201_2118_gb300", "csrc", f)
+               for f in ("stencil_kernels.cu", "jacobi_tma.cu", "dev_common.cuh", "tiles.cuh")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jacobi_dram_traffic.json")
 
 
@@ -150,9 +151,13 @@ def traffic_for(kernel_hash: str, cells: int, config):
     return t["dram_bytes_per_cell"] * cells
 
 
-def file_hash(path):
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+def file_hash(paths):
+    """sha256 over the Jacobi kernels' sources, in order."""
+    h = hashlib.sha256()
+    for path in paths:
+        with open(path, "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
 
 
 # --------------------------------------------------------------- oracle leg
@@ -433,10 +438,13 @@ def run_gpu(a):
     bytes_per_launch = JACOBI_BYTES_PER_CELL[a.dtype] * cells
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = traffic_for(file_hash(KERNEL_SRC), cells, jcfg[0])
-    kname = ("k_jacobi2 (two fused weighted Jacobi sweeps per launch" if fused else
-             "Jacobi sweep kernel (one weighted Jacobi sweep per launch") + \
-        ", config %s, %d^3, %s)" % (list(jcfg[0]), n, a.dtype)
+    traffic = traffic_for(file_hash(KERNEL_SRCS), cells, jcfg[0])
+    kernel_names = {0: "k_jacobi", 1: "k_jacobi_tma", 2: "k_jacobi_direct", 3: "k_jacobi_async",
+                    5: "k_jacobi2", 7: "k_jacobi_ws"}
+    kname = "%s (%s, config %s, %d^3, %s)" % (
+        kernel_names.get(jcfg[0][0], "?"),
+        "two fused weighted Jacobi sweeps per launch" if fused else "one weighted Jacobi sweep per launch",
+        list(jcfg[0]), n, a.dtype)
     roofline = {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                 "frac": achieved / peak, "traffic": traffic, "kernel": kname,
                 "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,

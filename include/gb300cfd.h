@@ -248,10 +248,11 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
  * kind 7 the warp-specialised TMA sweep (a producer warp fills an S-stage
  * ring, ty consumer warps; vx 4, ty in {4,8,16}, stages in {6,8});
  * zc = z-planes per tile.
- * stencil = {ty in {4,8}, zc, tile_tz in {0,2,4}} for the point kernels: rows
- * per CTA, z chunk, and for the RHS + stage kernel either neighbour reads
- * through L1 (tile_tz 0) or a shared-memory box of 32 x 8 x tile_tz cells
- * plus halo.  NULL leaves a part unchanged.  Results do not depend on the
+ * stencil = {ty in {4,8}, zc, tile_tz in {0,1,2,4}} for the point kernels:
+ * rows per CTA, z chunk, and for the RHS + stage kernel either neighbour
+ * reads through L1 (tile_tz 0), a z-streaming ring of shared-memory planes
+ * of 32 x ty cells plus halo (tile_tz 1), or a shared-memory box of
+ * 32 x 8 x tile_tz cells plus halo (2, 4).  NULL leaves a part unchanged.  Results do not depend on the
  * variant. */
 cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[3]);
 cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[3]);

@@ -82,7 +82,7 @@ struct cfd_grid {
   bool sticky = false;
 
   JacobiCfg jcfg{0, 4, 8, 32, 4};
-  StencilCfg scfg{8, 16, 0};
+  StencilCfg scfg{8, 32, 1};
   bool per_block = false;  // baseline mode: one launch per block per stencil kernel
 
   cudaGraphExec_t gexec = nullptr;
@@ -833,7 +833,7 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
   }
   if (stencil) {
     if ((stencil[0] != 4 && stencil[0] != 8) || stencil[1] < 1 ||
-        (stencil[2] != 0 && stencil[2] != 2 && stencil[2] != 4))
+        (stencil[2] != 0 && stencil[2] != 1 && stencil[2] != 2 && stencil[2] != 4))
       return fail(CFD_EINVAL, "unsupported stencil config");
     g->scfg = StencilCfg{stencil[0], stencil[1], stencil[2]};
   }
@@ -912,9 +912,10 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   CK(g, launch_copy(L, g->scfg, A_U1, A_P));
   StencilCfg sbest = g->scfg;
   float sbest_ms = 1e30f;
-  for (int tz : {0, 2, 4})
+  for (int tz : {0, 1, 2, 4})
   for (int ty : {4, 8})
-    for (int zc : {8, 16, 32}) {
+    for (int zc : {8, 16, 32, 64}) {
+      if (tz == 1 && zc < 16) continue;
       g->scfg = StencilCfg{ty, zc, tz};
       float ms = 0.f;
       if ((s = time_region(g, 1, &ms, 1)) != CFD_OK) return s;

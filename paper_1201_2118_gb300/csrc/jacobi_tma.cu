@@ -62,10 +62,23 @@ __device__ __forceinline__ unsigned long long gtimer() {
 }
 constexpr unsigned long long kWaitLimitNs = 2000000000ull;
 
+// try_wait with a suspend-time hint: the waiting thread sleeps until the
+// phase completes or about 100 us have passed, instead of polling
+__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "selp.b32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity), "r"(100000)
+      : "memory");
+  return ok != 0;
+}
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   if (mbar_try_wait(bar, parity)) return true;
   const unsigned long long t0 = gtimer();
-  while (!mbar_try_wait(bar, parity))
+  while (!mbar_try_wait_sleep(bar, parity))
     if (gtimer() - t0 > kWaitLimitNs) return false;
   return true;
 }
@@ -253,14 +266,31 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
 // cells each.  A consumer waits only on the "full" mbarrier of the plane it
 // needs next and, once it no longer reads a plane, arrives on that stage's
 // empty barrier (count TY), so consumer warps never wait for each other and
-// there is no CTA-wide barrier per plane.  Plane f of the CTA's sequence
-// (over all its tiles) lives in stage f % S; its full barrier completes
-// phase f / S, its empty barrier is waited with the opposite parity so the
-// first pass through the ring does not wait.
+// there is no CTA-wide barrier per plane.  Consumers read all seven stencil
+// points of a cell and r straight from the staged planes (z-1, z, z+1 are
+// three stages), so nothing is carried in registers from plane to plane.
+// The planes of a CTA are numbered across its tiles; plane f lives in stage
+// f % S, its full barrier completes phase f / S, and its empty barrier is
+// waited with the opposite parity so the first pass through the ring does
+// not wait.
 
 __device__ __forceinline__ void mbar_arrive(uint32_t bar) {
   asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
 }
+
+// Position in the ring: stage index and phase parity of plane f.
+template <int S>
+struct Ring {
+  int s;
+  uint32_t ph;
+  __device__ __forceinline__ explicit Ring(unsigned f) : s((int)(f % S)), ph((f / S) & 1u) {}
+  __device__ __forceinline__ void next() {
+    if (++s == S) {
+      s = 0;
+      ph ^= 1u;
+    }
+  }
+};
 
 template <typename T, int VX, int TY, int S>
 __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUtensorMap* maps,
@@ -268,6 +298,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
                                                              float omega, float inv_diag) {
   using Gm = TmaGeom<T, VX, TY>;
   constexpr int TX = Gm::TX, HX = Gm::HX, PW = Gm::PW;
+  constexpr int STAGE_T = Gm::STAGE / (int)sizeof(T), RS_T = Gm::PSTRIDE / (int)sizeof(T);
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S * Gm::STAGE);
   unsigned long long* empty = full + S;
@@ -290,6 +321,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
   const int g = L.ghost;
   constexpr int xo = kAlignBytes / (int)sizeof(T);
+  const T* ring = reinterpret_cast<const T*>(smem);
   unsigned seq = 0;     // planes of this CTA so far
   unsigned issued = 0;  // planes the producer has issued
   bool bad = false;
@@ -307,18 +339,18 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
         const CUtensorMap* mp = maps + 3 * blk + src_slot;
         const CUtensorMap* mr = maps + 3 * blk + 2;
         const int px = xo + i0 - HX, pyc = g + j0 - 1, rx = xo + i0, ry = g + j0;
-        for (int q = 0; q < np && !bad; ++q) {
-          const unsigned f = seq + q;
-          const int s = f % S;
-          bad |= !mbar_wait(smem_u32(&empty[s]), ((f / S) & 1u) ^ 1u);
+        Ring<S> at(seq);
+        for (int q = 0; q < np; ++q, at.next()) {
+          bad |= !mbar_wait(smem_u32(&empty[at.s]), at.ph ^ 1u);
           if (bad) break;
           ++issued;
           const int z = g + k0 - 1 + q;
           const bool need_r = (q >= 1 && q <= np - 2);
-          const uint32_t bar = smem_u32(&full[s]);
+          const uint32_t bar = smem_u32(&full[at.s]);
+          unsigned char* st = smem + at.s * Gm::STAGE;
           mbar_expect_tx(bar, Gm::PBYTES + (need_r ? Gm::RBYTES : 0));
-          tma_load_3d(smem_u32(smem + s * Gm::STAGE), mp, px, pyc, z, bar);
-          if (need_r) tma_load_3d(smem_u32(smem + s * Gm::STAGE + Gm::PSTRIDE), mr, rx, ry, z, bar);
+          tma_load_3d(smem_u32(st), mp, px, pyc, z, bar);
+          if (need_r) tma_load_3d(smem_u32(st + Gm::PSTRIDE), mr, rx, ry, z, bar);
         }
       }
       seq += np;
@@ -326,17 +358,10 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
       continue;
     }
     // ---------------- consumers (warp w = row j0 + w)
-    auto stage = [&](unsigned f) { return reinterpret_cast<const T*>(smem + (f % S) * Gm::STAGE); };
-    auto wait_full = [&](unsigned f) {
-      bad |= !mbar_wait(smem_u32(&full[f % S]), (f / S) & 1u);
-    };
-    auto release = [&](unsigned f) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&empty[f % S]));
-    };
     const int j = j0 + w;
     const int xl = lane * VX;
-    const int row = (w + 1) * PW + HX + xl;
+    const int row = (w + 1) * PW + HX + xl;  // this thread's centre in a p box
+    const int rrow = RS_T + w * TX + xl;     // and in the r box of the stage
     const long long pzl = B.pz;
     const int pyl = B.py;
     const int x0 = i0 + xl;
@@ -350,29 +375,33 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
     __syncwarp();
     T* qrow = reinterpret_cast<T*>(L.base) + B.org[dst] + (long long)(k0 - 1) * pzl +
               (long long)j * pyl + x0;
-    float m[VX], c[VX];
-    wait_full(seq);
-    wait_full(seq + 1);
-    ldv<VX>(stage(seq) + row, m);
-    ldv<VX>(stage(seq + 1) + row, c);
-    release(seq);
-    for (int q = 1; q <= np - 2; ++q) {
-      const unsigned f = seq + q;
-      wait_full(f + 1);
+    auto release = [&](int s) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[s]));
+    };
+    // stages of planes q - 1, q and q + 1
+    Ring<S> lo(seq), mid(seq), hi(seq);
+    mid.next();
+    hi.next();
+    bad |= !mbar_wait(smem_u32(&full[lo.s]), lo.ph);
+    bad |= !mbar_wait(smem_u32(&full[mid.s]), mid.ph);
+    hi.next();
+    for (int q = 1; q <= np - 2 && !bad; ++q) {
+      bad |= !mbar_wait(smem_u32(&full[hi.s]), hi.ph);
       if (bad) break;
-      const T* Pq = stage(f);
-      const T* Pn = stage(f + 1);
-      const T* Rq = Pq + Gm::PSTRIDE / (int)sizeof(T);
-      float zp[VX], up[VX], dn[VX], rr[VX];
-      ldv<VX>(Pn + row, zp);
-      ldv<VX>(Pq + row + PW, up);
-      ldv<VX>(Pq + row - PW, dn);
-      ldv<VX>(Rq + w * TX + xl, rr);
-      float left = __shfl_up_sync(0xffffffffu, c[VX - 1], 1);
-      float right = __shfl_down_sync(0xffffffffu, c[0], 1);
-      if (lane == 0) left = tof(Pq[row - 1]);
-      if (lane == 31) right = tof(Pq[row + VX]);
-      release(f);
+      const T* Pm = ring + lo.s * STAGE_T;
+      const T* Pc = ring + mid.s * STAGE_T;
+      const T* Pp = ring + hi.s * STAGE_T;
+      float m[VX], c[VX], zp[VX], up[VX], dn[VX], rr[VX];
+      ldv<VX>(Pm + row, m);
+      ldv<VX>(Pc + row, c);
+      ldv<VX>(Pp + row, zp);
+      ldv<VX>(Pc + row + PW, up);
+      ldv<VX>(Pc + row - PW, dn);
+      ldv<VX>(Pc + rrow, rr);
+      const float left = tof(Pc[row - 1]);
+      const float right = tof(Pc[row + VX]);
+      release(lo.s);
       float out[VX];
 #pragma unroll
       for (int e = 0; e < VX; ++e) {
@@ -398,15 +427,14 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
             if (x0 + e < nx) p_ghost_z<T>(L, B, dst, x0 + e, j, k, cvt<T>(out[e]));
         }
       }
-#pragma unroll
-      for (int e = 0; e < VX; ++e) {
-        m[e] = c[e];
-        c[e] = zp[e];
-      }
+      lo = mid;
+      mid = hi;
+      hi.next();
     }
-    release(seq + np - 1);
-    seq += np;
     if (bad) break;
+    release(lo.s);
+    release(mid.s);
+    seq += np;
   }
   if (bad && lane == 0) atomicOr(L.err_flag, 2);
   if (w == TY && lane == 0)  // never leave with our own copies in flight

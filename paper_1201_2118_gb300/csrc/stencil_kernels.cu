@@ -276,13 +276,134 @@ __global__ void __launch_bounds__(256) k_stage_tile(Launch L, float a, Set3 xs, 
   }
 }
 
+// z-streaming RHS + stage: a CTA owns a 32 x TY column of one block and
+// walks it along z with a ring of R shared-memory planes of u, v, w (each
+// 32 + 2H by TY + 2H cells, H = 1 for order 2, 2 for order 4): planes
+// k - H .. k + H are resident while plane k is computed, and the loads of
+// plane k + H + 1 are issued into registers before that and stored into the
+// free slot after it, so every field value comes from DRAM about once and
+// there is one barrier per plane.  Plane kk lives in slot kk & (R - 1).
+
+template <int SX, int PL, int R>
+struct RingFld {
+  const float* t;  // ring + component * PL
+  int i0, j0;      // grid index of plane element (0, 0)
+  __device__ __forceinline__ float operator()(int i, int j, int k) const {
+    return t[(k & (R - 1)) * (3 * PL) + (j - j0) * SX + (i - i0)];
+  }
+};
+
+template <typename T, int ORDER, int TY>
+__global__ void __launch_bounds__(32 * TY) k_stage_ring(Launch L, int zc, float a, Set3 xs,
+                                                        float b, Set3 ys, float cdt, Set3 os,
+                                                        float nu) {
+  constexpr int H = ORDER == 2 ? 1 : 2;
+  constexpr int SX = 32 + 2 * H, SY = TY + 2 * H, PL = SX * SY;
+  constexpr int R = ORDER == 2 ? 4 : 8;  // >= 2H + 2, a power of two
+  constexpr int NT = 32 * TY;
+  constexpr int NL = (3 * PL + NT - 1) / NT;  // plane elements loaded per thread
+  __shared__ float ring[R * 3 * PL];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, TY, zc);
+  const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
+  const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const T* base = reinterpret_cast<const T*>(L.base);
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int g = L.ghost;
+    const int py = B.py;
+    const long long pz = B.pz;
+    const int k1 = min(k0 + zc, nz);
+    // this thread's share of a plane: ring offset and field offset (plane
+    // 0) of each element; elements outside the allocated extent (partial
+    // tiles) are not loaded, and only cells outside the block read them
+    int soff[NL];
+    long long goff[NL];
+    bool lok[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int idx = tid + q * NT;
+      const int c = idx / PL, rem = idx % PL;
+      const int xx = rem % SX, yy = rem / SX;
+      const int i = i0 - H + xx, j = j0 - H + yy;
+      lok[q] = idx < 3 * PL && i <= nx + g - 1 && j <= ny + g - 1;
+      soff[q] = c * PL + rem;
+      goff[q] = lok[q] ? B.org[ys.a[c]] + (long long)j * py + i : 0;
+    }
+    const int kmax = nz + g - 1;
+    auto fetch = [&](int kk, float (&v)[NL]) {
+#pragma unroll
+      for (int q = 0; q < NL; ++q)
+        v[q] = (lok[q] && kk <= kmax) ? ldf<T>(base + goff[q] + (long long)kk * pz) : 0.f;
+    };
+    auto put = [&](int kk, const float (&v)[NL]) {
+      float* slot = ring + (kk & (R - 1)) * (3 * PL);
+#pragma unroll
+      for (int q = 0; q < NL; ++q)
+        if (tid + q * NT < 3 * PL) slot[soff[q]] = v[q];
+    };
+    for (int kk = k0 - H; kk <= k0 + H; ++kk) {
+      float v[NL];
+      fetch(kk, v);
+      put(kk, v);
+    }
+    __syncthreads();
+    const int i = i0 + tx, j = j0 + ty;
+    const bool mine = i < nx && j < ny;
+    const bool wall[3] = {B.bc[1] == BC_WALL && i == nx - 1, B.bc[3] == BC_WALL && j == ny - 1,
+                          B.bc[5] == BC_WALL};
+    const long long o0 = (long long)j * py + i;
+    const T* X[3] = {base + B.org[xs.a[0]] + o0, base + B.org[xs.a[1]] + o0,
+                     base + B.org[xs.a[2]] + o0};
+    T* O[3] = {reinterpret_cast<T*>(L.base) + B.org[os.a[0]] + o0,
+               reinterpret_cast<T*>(L.base) + B.org[os.a[1]] + o0,
+               reinterpret_cast<T*>(L.base) + B.org[os.a[2]] + o0};
+    const RingFld<SX, PL, R> f[3] = {{ring, i0 - H, j0 - H}, {ring + PL, i0 - H, j0 - H},
+                                     {ring + 2 * PL, i0 - H, j0 - H}};
+    for (int k = k0; k < k1; ++k) {
+      const int kn = k + H + 1;
+      const bool more = kn <= k1 - 1 + H;
+      float nxt[NL];
+      if (more) fetch(kn, nxt);
+      if (mine) {
+        float F[3];
+        F[0] = rhs_comp<RingFld<SX, PL, R>, ORDER, 0>(f, i, j, k, ih, ih2, nu);
+        F[1] = rhs_comp<RingFld<SX, PL, R>, ORDER, 1>(f, i, j, k, ih, ih2, nu);
+        F[2] = rhs_comp<RingFld<SX, PL, R>, ORDER, 2>(f, i, j, k, ih, ih2, nu);
+        const long long o = (long long)k * pz;
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const bool wf = wall[c] && (c != 2 || k == nz - 1);
+          float v = b * f[c](i, j, k) + cdt * F[c];
+          if (a != 0.f) v += a * ldf<T>(X[c] + o);
+          O[c][o] = cvt<T>(wf ? 0.f : v);
+        }
+      }
+      if (more) put(kn, nxt);
+      __syncthreads();
+    }
+  }
+}
+
 // --------------------------------------------------------------- divergence
+//
+// Both walk 32 x TY columns along z with one cell per thread; the block's
+// pointers are taken into registers once per tile (the output stores could
+// alias the block table as far as the compiler knows) and the z-neighbour
+// read by one plane is kept for the next.
 
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, float inv_cdt,
                                                  int r_arr) {
   __shared__ TileTable tt;
   tile_table_build(tt, L, 32, TY, zc);
+  const float ihx = L.ih[0], ihy = L.ih[1], ihz = L.ih[2];
+  const T* base = reinterpret_cast<const T*>(L.base);
   int blk = L.b0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
@@ -290,14 +411,23 @@ __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, floa
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
-    const Fld<T> u = fld<T>(L, B, ws.a[0]), v = fld<T>(L, B, ws.a[1]), w = fld<T>(L, B, ws.a[2]);
-    T* r = wptr<T>(L, B, r_arr);
-    const int k1 = min(k0 + zc, B.n[2]);
-    for (int k = k0; k < k1; ++k) {
-      const float d = (u(i, j, k) - u(i - 1, j, k)) * L.ih[0] +
-                      (v(i, j, k) - v(i, j - 1, k)) * L.ih[1] +
-                      (w(i, j, k) - w(i, j, k - 1)) * L.ih[2];
-      r[(long long)k * B.pz + (long long)j * B.py + i] = cvt<T>(d * inv_cdt);
+    const int py = B.py;
+    const long long pz = B.pz;
+    const int kn = min(k0 + zc, B.n[2]) - k0;
+    const long long o0 = (long long)k0 * pz + (long long)j * py + i;
+    const T* u = base + B.org[ws.a[0]] + o0;
+    const T* v = base + B.org[ws.a[1]] + o0;
+    const T* w = base + B.org[ws.a[2]] + o0;
+    T* r = reinterpret_cast<T*>(L.base) + B.org[r_arr] + o0;
+    float wm = ldf<T>(w - pz);
+#pragma unroll 1
+    for (int q = 0; q < kn; ++q) {
+      const long long o = (long long)q * pz;
+      const float wc = ldf<T>(w + o);
+      const float d = (ldf<T>(u + o) - ldf<T>(u + o - 1)) * ihx +
+                      (ldf<T>(v + o) - ldf<T>(v + o - py)) * ihy + (wc - wm) * ihz;
+      r[o] = cvt<T>(d * inv_cdt);
+      wm = wc;
     }
   }
 }
@@ -309,28 +439,43 @@ __global__ void __launch_bounds__(32 * TY) k_project(Launch L, int zc, Set3 ws, 
                                                      float cdt, Set3 os) {
   __shared__ TileTable tt;
   tile_table_build(tt, L, 32, TY, zc);
+  const float ihx = L.ih[0], ihy = L.ih[1], ihz = L.ih[2];
+  const T* base = reinterpret_cast<const T*>(L.base);
   int blk = L.b0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
     if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
-    if (i >= B.n[0] || j >= B.n[1]) continue;
-    const Fld<T> p = fld<T>(L, B, p_arr);
-    const int k1 = min(k0 + zc, B.n[2]);
-    const bool wx = B.bc[1] == BC_WALL && i == B.n[0] - 1;
-    const bool wy = B.bc[3] == BC_WALL && j == B.n[1] - 1;
-    for (int k = k0; k < k1; ++k) {
-      const long long o = (long long)k * B.pz + (long long)j * B.py + i;
-      const float pc = p(i, j, k);
-      const float g[3] = {(p(i + 1, j, k) - pc) * L.ih[0], (p(i, j + 1, k) - pc) * L.ih[1],
-                          (p(i, j, k + 1) - pc) * L.ih[2]};
-      const bool wf[3] = {wx, wy, B.bc[5] == BC_WALL && k == B.n[2] - 1};
+    if (i >= nx || j >= ny) continue;
+    const int py = B.py;
+    const long long pz = B.pz;
+    const int kn = min(k0 + zc, nz) - k0;
+    const long long o0 = (long long)k0 * pz + (long long)j * py + i;
+    const T* P = base + B.org[p_arr] + o0;
+    const T* W[3] = {base + B.org[ws.a[0]] + o0, base + B.org[ws.a[1]] + o0,
+                     base + B.org[ws.a[2]] + o0};
+    T* U[3] = {reinterpret_cast<T*>(L.base) + B.org[os.a[0]] + o0,
+               reinterpret_cast<T*>(L.base) + B.org[os.a[1]] + o0,
+               reinterpret_cast<T*>(L.base) + B.org[os.a[2]] + o0};
+    const bool wx = B.bc[1] == BC_WALL && i == nx - 1;
+    const bool wy = B.bc[3] == BC_WALL && j == ny - 1;
+    const int kwall = B.bc[5] == BC_WALL ? nz - 1 - k0 : -1;
+    float pc = ldf<T>(P);
+#pragma unroll 1
+    for (int q = 0; q < kn; ++q) {
+      const long long o = (long long)q * pz;
+      const float pzn = ldf<T>(P + o + pz);
+      const float g[3] = {(ldf<T>(P + o + 1) - pc) * ihx, (ldf<T>(P + o + py) - pc) * ihy,
+                          (pzn - pc) * ihz};
+      const bool wf[3] = {wx, wy, q == kwall};
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
-        const float v = fld<T>(L, B, ws.a[c])(i, j, k) - cdt * g[c];
-        wptr<T>(L, B, os.a[c])[o] = cvt<T>(wf[c] ? 0.f : v);
+        const float v = ldf<T>(W[c] + o) - cdt * g[c];
+        U[c][o] = cvt<T>(wf[c] ? 0.f : v);
       }
+      pc = pzn;
     }
   }
 }
@@ -1148,10 +1293,31 @@ static void run_stage(const Launch& L, int zc, float a, Set3 xs, float b, Set3 y
   kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
 }
 
+template <typename T, int ORDER, int TY>
+static void run_stage_ring(const Launch& L, int zc, float a, Set3 xs, float b, Set3 ys, float cdt,
+                           Set3 os, float nu) {
+  const long long tiles = count_tiles(L, 32, TY, zc);
+  auto kern = k_stage_ring<T, ORDER, TY>;
+  static const int occ = occupancy(kern, 32 * TY);
+  kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
+}
+
 cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float a,
                          const int* xset, float b, const int* yset, float cdt, const int* oset,
                          float nu) {
   const Set3 xs = xset ? mk3(xset) : Set3{{0, 0, 0}};
+  if (c.tile_tz == 1) {
+    CFD_DISPATCH_T(L.dtype, {
+      if (order == 4) {
+        if (c.ty == 4) run_stage_ring<T, 4, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+        else run_stage_ring<T, 4, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+      } else {
+        if (c.ty == 4) run_stage_ring<T, 2, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+        else run_stage_ring<T, 2, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+      }
+    });
+    return cudaGetLastError();
+  }
   if (c.tile_tz == 2 || c.tile_tz == 4) {
     CFD_DISPATCH_T(L.dtype, {
       if (order == 4) {
