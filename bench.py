@@ -38,7 +38,7 @@ UNIT = "GLUP/s"
 JACOBI_BYTES_PER_CELL = {"f32": 12, "bf16": 6, "f16": 6}
 KERNEL_SRCS = [os.path.join(ROOT, "paper_1201_2118_gb300", "csrc", f)
                for f in ("stencil_kernels.cu", "jacobi_tma.cu", "dev_common.cuh", "tiles.cuh")]
-TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jacobi_dram_traffic.json")
+TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jacobi_dram_traffic.txt")
 
 
 def parse():

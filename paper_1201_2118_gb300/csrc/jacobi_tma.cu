@@ -524,7 +524,7 @@ bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int
     cuuint32_t estr[3] = {1, 1, 1};
     memset(&maps[a], 0, sizeof(CUtensorMap));
     CUresult r = enc(&maps[a], dt, 3, A.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
-                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+                     CU_TENSOR_MAP_SWIZZLE_NONE, CU_TENSOR_MAP_L2_PROMOTION_NONE,
                      CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE);
     if (r != CUDA_SUCCESS) return false;
   }

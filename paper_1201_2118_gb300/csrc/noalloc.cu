@@ -16,6 +16,7 @@
 #include <string>
 
 #include "gb300cfd.h"
+#include "ffloat.cuh"
 
 namespace {
 
@@ -46,7 +47,8 @@ __device__ __forceinline__ double wmax(double v) {
 }
 
 // Sum |u|^2, max |u_d|, max |D u| and the non-finite count of one z-plane per
-// CTA (same per-cell arithmetic as the grid reduction), written to
+// CTA (the grid reduction's float-float per-cell arithmetic, each cell's
+// |u|^2 added to an FP64 sum), written to
 // partials[4 z .. 4 z + 3].  Every slot 0..nz-1 is written by every call, so
 // the static array needs no clearing between calls.
 template <typename T>
@@ -58,22 +60,28 @@ __global__ void __launch_bounds__(256) k_plane_partials(const T* u, const T* v, 
   const int k = blockIdx.x;
   double a[4] = {0.0, 0.0, 0.0, 0.0};
   const float ih[3] = {ihx, ihy, ihz};
+  float umax = 0.f;
+  cfd::FF dmax = {0.f, 0.f};
+  int bad = 0;
   for (int c = threadIdx.x; c < nx * ny; c += 256) {
     const int i = c % nx, j = c / nx;
     const long long o = (long long)k * pz + (long long)j * py + i;
     const float x[3] = {ld(u + o), ld(v + o), ld(w + o)};
     const float xm[3] = {ld(u + o - 1), ld(v + o - py), ld(w + o - pz)};
-    double div = 0.0;
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
-      const double xd = x[d];
-      a[0] += xd * xd;
-      a[1] = fmax(a[1], fabs(xd));
-      div += (xd - (double)xm[d]) * (double)ih[d];
-      if (!isfinite(x[d])) a[3] += 1.0;
+      umax = fmaxf(umax, fabsf(x[d]));
+      bad += !isfinite(x[d]);
     }
-    a[2] = fmax(a[2], fabs(div));
+    cfd::FF sq = {0.f, 0.f}, div;
+    cfd::ff_cell(x, xm, ih, sq, div);
+    a[0] += cfd::ff_to_double(sq);
+    div = cfd::ff_abs(div);
+    if (cfd::ff_gt(div, dmax)) dmax = div;
   }
+  a[1] = umax;
+  a[2] = cfd::ff_to_double(dmax);
+  a[3] = bad;
   const int wid = threadIdx.x >> 5, ln = threadIdx.x & 31;
   a[0] = wsum(a[0]);
   a[1] = wmax(a[1]);

@@ -11,6 +11,7 @@
 
 #include "cfd_internal.h"
 #include "dev_common.cuh"
+#include "ffloat.cuh"
 #include "tiles.cuh"
 
 namespace cfd {
@@ -1138,8 +1139,10 @@ __device__ __forceinline__ void block_reduce4(double (&v)[4], double (*sh)[4]) {
   }
 }
 
-__device__ __forceinline__ bool finite_f(float x) { return isfinite(x); }
-
+// mode 0: sum |u|^2, max |u_d|, max |D u| and the non-finite count of a
+// velocity set; the per-cell work is float-float, each thread's column sum
+// (at most zc cells) is added to an FP64 accumulator.  mode 1: sum of
+// (L p - r)^2 in FP64.
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, Set3 set,
                                                     int p_arr, int r_arr, double* partials) {
@@ -1147,6 +1150,11 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
   double acc[4] = {0.0, 0.0, 0.0, 0.0};
   __shared__ TileTable tt;
   tile_table_build(tt, L, 32, TY, zc);
+  const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
+  const T* base = reinterpret_cast<const T*>(L.base);
+  float umax = 0.f;
+  FF dmax = {0.f, 0.f};
+  int bad = 0;
   int blk = L.b0;
   for (long long t = blockIdx.x;; t += gridDim.x) {
     int i0, j0, k0;
@@ -1154,36 +1162,51 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
     const BlockDev& B = L.blocks[blk];
     const int i = i0 + threadIdx.x, j = j0 + threadIdx.y;
     if (i >= B.n[0] || j >= B.n[1]) continue;
-    const int k1 = min(k0 + zc, B.n[2]);
+    const int py = B.py;
+    const long long pz = B.pz;
+    const int kn = min(k0 + zc, B.n[2]) - k0;
+    const long long o0 = (long long)k0 * pz + (long long)j * py + i;
     if (mode == 0) {
-      const Fld<T> f[3] = {fld<T>(L, B, set.a[0]), fld<T>(L, B, set.a[1]), fld<T>(L, B, set.a[2])};
-      for (int k = k0; k < k1; ++k) {
-        const float x[3] = {f[0](i, j, k), f[1](i, j, k), f[2](i, j, k)};
-        const float xm[3] = {f[0](i - 1, j, k), f[1](i, j - 1, k), f[2](i, j, k - 1)};
-        double div = 0.0;
+      const T* X[3] = {base + B.org[set.a[0]] + o0, base + B.org[set.a[1]] + o0,
+                       base + B.org[set.a[2]] + o0};
+      const long long back[3] = {1, py, pz};
+      FF col = {0.f, 0.f};
+      for (int q = 0; q < kn; ++q) {
+        const long long o = (long long)q * pz;
+        float x[3], xm[3];
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
-          const double xd = x[c];
-          acc[0] += xd * xd;
-          acc[1] = fmax(acc[1], fabs(xd));
-          div += (xd - (double)xm[c]) * (double)L.ih[c];
-          if (!finite_f(x[c])) acc[3] += 1.0;
+          x[c] = ldf<T>(X[c] + o);
+          xm[c] = ldf<T>(X[c] + o - back[c]);
+          umax = fmaxf(umax, fabsf(x[c]));
+          bad += !isfinite(x[c]);
         }
-        acc[2] = fmax(acc[2], fabs(div));
+        FF div;
+        ff_cell(x, xm, ih, col, div);
+        div = ff_abs(div);
+        if (ff_gt(div, dmax)) dmax = div;
       }
+      acc[0] += ff_to_double(col);
     } else {
-      const Fld<T> p = fld<T>(L, B, p_arr), r = fld<T>(L, B, r_arr);
-      for (int k = k0; k < k1; ++k) {
-        const double pc = p(i, j, k);
-        const double lp = ((double)p(i + 1, j, k) - 2.0 * pc + (double)p(i - 1, j, k)) * (double)L.ih2[0] +
-                          ((double)p(i, j + 1, k) - 2.0 * pc + (double)p(i, j - 1, k)) * (double)L.ih2[1] +
-                          ((double)p(i, j, k + 1) - 2.0 * pc + (double)p(i, j, k - 1)) * (double)L.ih2[2];
-        const float rv = r(i, j, k);
-        const double e = lp - (double)rv;
+      const T* P = base + B.org[p_arr] + o0;
+      const T* Rr = base + B.org[r_arr] + o0;
+      for (int q = 0; q < kn; ++q) {
+        const long long o = (long long)q * pz;
+        const double pc = ldf<T>(P + o);
+        const double lp =
+            ((double)ldf<T>(P + o + 1) - 2.0 * pc + (double)ldf<T>(P + o - 1)) * (double)L.ih2[0] +
+            ((double)ldf<T>(P + o + py) - 2.0 * pc + (double)ldf<T>(P + o - py)) * (double)L.ih2[1] +
+            ((double)ldf<T>(P + o + pz) - 2.0 * pc + (double)ldf<T>(P + o - pz)) * (double)L.ih2[2];
+        const double e = lp - (double)ldf<T>(Rr + o);
         acc[0] += e * e;
         if (!isfinite(e)) acc[3] += 1.0;
       }
     }
+  }
+  if (mode == 0) {
+    acc[1] = umax;
+    acc[2] = ff_to_double(dmax);
+    acc[3] = bad;
   }
   block_reduce4<32 * TY>(acc, sh);
   if (threadIdx.x == 0 && threadIdx.y == 0) {

@@ -1,0 +1,65 @@
+"""A small, fixed workload for profiler captures and timings of the Jacobi
+sweep variants.
+
+    python -m paper_1201_2118_gb300.profile_case --n 384 --jacobi 1,4,16,16,4 --sweeps 8
+    python -m paper_1201_2118_gb300.profile_case --n 512 --time --sweeps 40 \\
+        --jacobi 1,4,16,16,4 7,4,16,64,8 0,4,4,32,4
+
+builds an n^3 lid-driven cavity grid (seeded cavity noise), and for each
+given Jacobi variant (kind,vx,ty,zc,stages) runs the requested number of
+sweeps on the grid's stream, then checks the device error flag.  With
+--time, each variant first runs 4 warm-up sweeps and the timed sweeps are
+bracketed by CUDA events on the grid's stream; the line printed per variant
+gives microseconds per sweep and the algorithmic bytes (read p and r, write
+p) per second.  The launch to capture under ncu is selected with -k/-s/-c.
+"""
+import argparse
+import os
+import sys
+
+
+def main(argv=None):
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--n", type=int, default=384)
+    ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
+    ap.add_argument("--jacobi", nargs="*", default=[], help="kind,vx,ty,zc,stages ...")
+    ap.add_argument("--sweeps", type=int, default=12)
+    ap.add_argument("--time", action="store_true")
+    a = ap.parse_args(argv)
+    root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+    if root not in sys.path:
+        sys.path.insert(0, root)
+    import torch
+    import workloads
+    from paper_1201_2118_gb300 import Grid
+    n = a.n
+    s = torch.cuda.Stream()
+    g = Grid((n, n, n), ghost=1, h=(1.0 / n,) * 3, dtype=a.dtype, stream=s)
+    g.set_cavity(1.0)
+    g.upload(workloads.ldc_noise(n, seed=1))
+    g.pressure_solve(1e-3, 0)
+    es = 4 if a.dtype == "f32" else 2
+    for c in a.jacobi or [None]:
+        if c is not None:
+            g.set_kernel_config(jacobi=tuple(int(x) for x in c.split(",")))
+        cfg = g.kernel_config()[0]
+        if not a.time:
+            g.jacobi(a.sweeps)
+            torch.cuda.synchronize()
+            print("ok", n, a.dtype, cfg, a.sweeps, flush=True)
+            continue
+        g.jacobi(4)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.jacobi(a.sweeps)
+        e1.record(s)
+        torch.cuda.synchronize()
+        us = e0.elapsed_time(e1) * 1e3 / a.sweeps
+        gbs = 3 * es * n ** 3 / (us * 1e-6) / 1e9
+        print("%d^3 %s %s %.1f us/sweep %.0f GB/s" % (n, a.dtype, cfg, us, gbs), flush=True)
+    g.check()
+
+
+if __name__ == "__main__":
+    main()
