@@ -36,8 +36,14 @@ import workloads  # noqa: E402
 METRIC = "GLUP/s and HBM GB/s vs peak per sweep; batched/bf16 vs plain; adjoint/fwd ratio"
 UNIT = "GLUP/s"
 JACOBI_BYTES_PER_CELL = {"f32": 12, "bf16": 6, "f16": 6}
-KERNEL_SRCS = [os.path.join(ROOT, "paper_1201_2118_gb300", "csrc", f)
-               for f in ("stencil_kernels.cu", "jacobi_tma.cu", "dev_common.cuh", "tiles.cuh")]
+CSRC = os.path.join(ROOT, "paper_1201_2118_gb300", "csrc")
+
+
+def kernel_sources(kind: int):
+    """Source files of the Jacobi variant `kind` (the TMA variants live in
+    jacobi_tma.cu, the others in stencil_kernels.cu)."""
+    main = "jacobi_tma.cu" if kind in (1, 7) else "stencil_kernels.cu"
+    return [os.path.join(CSRC, f) for f in (main, "dev_common.cuh", "tiles.cuh", "cfd_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jacobi_dram_traffic.txt")
 
 
@@ -438,7 +444,7 @@ def run_gpu(a):
     bytes_per_launch = JACOBI_BYTES_PER_CELL[a.dtype] * cells
     achieved = bytes_per_launch / (launch_ms * 1e-3) / 1e9
     peak, peak_kind = peaks()
-    traffic = traffic_for(file_hash(KERNEL_SRCS), cells, jcfg[0])
+    traffic = traffic_for(file_hash(kernel_sources(jcfg[0][0])), cells, jcfg[0])
     kernel_names = {0: "k_jacobi", 1: "k_jacobi_tma", 2: "k_jacobi_direct", 3: "k_jacobi_async",
                     5: "k_jacobi2", 7: "k_jacobi_ws"}
     kname = "%s (%s, config %s, %d^3, %s)" % (
