@@ -42,7 +42,7 @@ CSRC = os.path.join(ROOT, "paper_1201_2118_gb300", "csrc")
 def kernel_sources(kind: int):
     """Source files of the Jacobi variant `kind` (the TMA variants live in
     jacobi_tma.cu, the others in stencil_kernels.cu)."""
-    main = "jacobi_tma.cu" if kind in (1, 7) else "stencil_kernels.cu"
+    main = "jacobi_tma.cu" if kind in (1, 7, 9) else "stencil_kernels.cu"
     return [os.path.join(CSRC, f) for f in (main, "dev_common.cuh", "tiles.cuh", "cfd_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jacobi_dram_traffic.txt")
 
@@ -428,10 +428,10 @@ def run_gpu(a):
     ke, umax, divmax = g.reduce(0)
 
     # ---- dominant kernel: the Jacobi sweep, timed alone on the grid's stream
-    # (a fused launch of kind 5 does two sweeps; its compulsory traffic is
+    # (a fused launch of kind 5 or 9 does two sweeps; its compulsory traffic is
     # still one read of p and r and one write of p per launch)
     sweeps = 100
-    fused = jcfg[0][0] == 5
+    fused = jcfg[0][0] in (5, 9)
     per_launch = 2 if fused else 1
     j0, j1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     g.jacobi(4)
@@ -446,7 +446,7 @@ def run_gpu(a):
     peak, peak_kind = peaks()
     traffic = traffic_for(file_hash(kernel_sources(jcfg[0][0])), cells, jcfg[0])
     kernel_names = {0: "k_jacobi", 1: "k_jacobi_tma", 2: "k_jacobi_direct", 3: "k_jacobi_async",
-                    5: "k_jacobi2", 7: "k_jacobi_ws"}
+                    5: "k_jacobi2", 7: "k_jacobi_ws", 9: "k_jacobi2_ws"}
     kname = "%s (%s, config %s, %d^3, %s)" % (
         kernel_names.get(jcfg[0][0], "?"),
         "two fused weighted Jacobi sweeps per launch" if fused else "one weighted Jacobi sweep per launch",

@@ -69,6 +69,8 @@ struct Launch {
 //           no CTA barrier per plane)
 //   kind 5: two fused sweeps per launch (temporal blocking, single block,
 //           nx % 128 == 0, ny % ty == 0); odd counts end with one kind-0 sweep
+//   kind 9: two sweeps per launch, warp-specialised TMA (single block with
+//           walls on all six faces); odd counts end with one kind-0 sweep
 struct JacobiCfg { int kind, vx, ty, zc, stages; };
 // Point kernels: rows per CTA (32 x ty threads) and z chunk; the RHS + stage
 // kernel either reads neighbours through L1 (tile_tz = 0) or from a
@@ -86,6 +88,9 @@ constexpr int kTmaMapBytes = 128;
 bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int dtype,
                         const JacobiCfg& c);
 cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* maps_dev,
+                              int src_slot, int dst, float omega);
+// Two sweeps per launch (kind 9), src -> dst; single block, walls on all faces.
+cudaError_t launch_jacobi2_ws(const Launch& L, const JacobiCfg& c, const void* maps_dev,
                               int src_slot, int dst, float omega);
 
 long long count_tiles(const Launch& L, int tx, int ty, int tz);

@@ -205,7 +205,7 @@ cfd_status upload_tables(cfd_grid* g) {
 // Tensor maps of the TMA Jacobi sweep (box sizes depend on the config).
 cfd_status refresh_maps(cfd_grid* g) {
   g->maps_ready = false;
-  if ((g->jcfg.kind != 1 && g->jcfg.kind != 7) || !g->base) return CFD_OK;
+  if ((g->jcfg.kind != 1 && g->jcfg.kind != 7 && g->jcfg.kind != 9) || !g->base) return CFD_OK;
   std::vector<TmaArray> arrs;
   const int ids[3] = {A_P, A_P2, A_R};
   for (const auto& b : g->hb)
@@ -354,6 +354,12 @@ cfd_status enq_stage(cfd_grid* g, double a, int xs, double b, int ys, double c, 
 
 // Fused two-sweep launches apply (single block, tiles dividing x and y).
 bool fused_ok(const cfd_grid* g) {
+  if (g->jcfg.kind == 9) {
+    if (g->nblocks != 1 || !g->maps_ready) return false;
+    for (int f = 0; f < 6; ++f)
+      if (g->bdev[0].bc[f] != BC_WALL) return false;
+    return true;
+  }
   return g->jcfg.kind == 5 && g->nblocks == 1 && g->hb[0].n[0] % 128 == 0 &&
          g->hb[0].n[1] % g->jcfg.ty == 0 && g->hb[0].n[1] >= 2 && g->hb[0].n[2] >= 2;
 }
@@ -361,7 +367,8 @@ bool fused_ok(const cfd_grid* g) {
 // One Jacobi sweep src -> dst with the configured variant (the fused
 // variant's single sweeps use the register/shuffle kernel).
 cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst) {
-  if (g->jcfg.kind == 5) return launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, src, dst, A_R, (float)g->omega);
+  if (g->jcfg.kind == 5 || g->jcfg.kind == 9)
+    return launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, src, dst, A_R, (float)g->omega);
   if ((g->jcfg.kind == 1 || g->jcfg.kind == 7) && g->maps_ready)
     return launch_jacobi_tma(L, g->jcfg, g->base + g->maps_off, src == A_P ? 0 : 1, dst,
                              (float)g->omega);
@@ -377,7 +384,11 @@ cfd_status enq_sweeps(cfd_grid* g, int iters) {
   if (fused_ok(g)) {
     const Launch L = make_launch(g);
     for (int it = 0; it + 1 < iters; it += 2) {
-      CK(g, launch_jacobi2(L, g->jcfg, cur, oth, A_R, (float)g->omega));
+      if (g->jcfg.kind == 9)
+        CK(g, launch_jacobi2_ws(L, g->jcfg, g->base + g->maps_off, cur == A_P ? 0 : 1, oth,
+                                (float)g->omega));
+      else
+        CK(g, launch_jacobi2(L, g->jcfg, cur, oth, A_R, (float)g->omega));
       g->launches += 1;
       std::swap(cur, oth);
     }
@@ -535,7 +546,8 @@ cfd_status time_region(cfd_grid* g, int reps, float* ms, int what) {
   CK(g, cudaEventRecord(a, g->own));
   cfd_status s = CFD_OK;
   for (int r = 0; r < reps && s == CFD_OK; ++r)
-    s = what == 0 ? enq_sweeps(g, 2) : enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, 1e-3, CFD_SET_W);
+    // four sweeps end in P for every variant, so no copy is timed
+    s = what == 0 ? enq_sweeps(g, 4) : enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, 1e-3, CFD_SET_W);
   CK(g, cudaEventRecord(b, g->own));
   CK(g, cudaEventSynchronize(b));
   CK(g, cudaEventElapsedTime(ms, a, b));
@@ -822,7 +834,10 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
     const bool ok5 = c.kind == 5 && (c.ty == 4 || c.ty == 8);
     const bool ok7 = c.kind == 7 && c.vx == 4 && (c.ty == 4 || c.ty == 8 || c.ty == 16) &&
                      (c.stages == 6 || c.stages == 8);
-    if (!(ok0 || ok1 || ok2 || ok3 || ok5 || ok7) || c.zc < 1)
+    const bool ok9 = c.kind == 9 && c.vx == 4 &&
+                     ((c.ty == 16 && (c.stages == 6 || c.stages == 7)) ||
+                      (c.ty == 8 && (c.stages == 5 || c.stages == 6)));
+    if (!(ok0 || ok1 || ok2 || ok3 || ok5 || ok7 || ok9) || c.zc < 1)
       return fail(CFD_EINVAL, "unsupported Jacobi config");
     g->jcfg = c;
     cfd_status s = refresh_maps(g);
@@ -878,6 +893,10 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   if (g->nblocks == 1)
     for (int zc : {16, 32, 64, 128})
       for (int ty : {4, 8}) cands.push_back({5, 4, ty, zc, 0});
+  for (int zc : {32, 64})
+    for (const JacobiCfg& d : {JacobiCfg{9, 4, 16, zc, 7}, JacobiCfg{9, 4, 16, zc, 6},
+                               JacobiCfg{9, 4, 8, zc, 5}, JacobiCfg{9, 4, 8, zc, 6}})
+      cands.push_back(d);
   const int avx = g->dtype == CFD_F32 ? 4 : 8;
   for (int zc : {16, 32, 64})
     for (const JacobiCfg& d : {JacobiCfg{3, avx, 4, zc, 5}, JacobiCfg{3, avx, 4, zc, 6},
@@ -898,7 +917,8 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   float best_ms = 1e30f;
   for (const auto& c : cands) {
     g->jcfg = c;
-    if (refresh_maps(g) != CFD_OK || ((c.kind == 1 || c.kind == 7) && !g->maps_ready)) continue;
+    if (refresh_maps(g) != CFD_OK || ((c.kind == 1 || c.kind == 7 || c.kind == 9) && !g->maps_ready))
+      continue;
     float ms = 0.f;
     if ((s = time_region(g, 1, &ms, 0)) != CFD_OK) return s;  // warm-up
     if ((s = time_region(g, 5, &ms, 0)) != CFD_OK) return s;
@@ -927,7 +947,7 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
     }
   g->scfg = sbest;
   invalidate_graph(g);
-  const double us = best_ms * 1000.0 / 10.0;
+  const double us = best_ms * 1000.0 / 20.0;  // 5 repetitions x 4 sweeps
   if (sweep_us) *sweep_us = us;
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "a")) {
@@ -942,7 +962,9 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
 cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[3]) {
   if (!g) return fail(CFD_EINVAL, "null grid");
   if (jacobi) {
-    jacobi[0] = (g->jcfg.kind == 1 || g->jcfg.kind == 7) && !g->maps_ready ? 0 : g->jcfg.kind;
+    jacobi[0] = (g->jcfg.kind == 1 || g->jcfg.kind == 7 || g->jcfg.kind == 9) && !g->maps_ready
+                    ? 0
+                    : g->jcfg.kind;
     jacobi[1] = g->jcfg.vx;
     jacobi[2] = g->jcfg.ty;
     jacobi[3] = g->jcfg.zc;

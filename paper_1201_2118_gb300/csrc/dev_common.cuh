@@ -179,23 +179,27 @@ __device__ __forceinline__ unsigned thread_images(unsigned row_mask, int lane, i
   return m;
 }
 
+// v[idx] for a register array, as a chain of predicated selects (a C++
+// select chain over a runtime index becomes an indexed load from a
+// local-memory copy of the array)
+template <int VX>
+__device__ __forceinline__ float pick(const float (&v)[VX], int idx) {
+  float r = v[0];
+#pragma unroll
+  for (int q = 1; q < VX; ++q)
+    asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, %0, p;\n\t}"
+        : "+f"(r)
+        : "f"(v[q]), "r"(idx), "r"(q));
+  return r;
+}
+
 // Writes the images the thread owns for plane k; xl = i - x0 is the
 // thread's offset in the row tile, nv its number of cells inside the block.
 template <typename T, int VX>
 __device__ __forceinline__ void put_row_images(const RowImage<T>* e, unsigned tm, int k, int xl,
                                                int nv, const float (&out)[VX]) {
   if (tm & 1u) e[0].p[k * e[0].pz] = cvt<T>(out[0]);
-  if (tm & 2u) {
-    // out[nv - 1] as a chain of selects (a C++ select chain is turned into
-    // an indexed load from a local-memory copy of out)
-    float v = out[0];
-#pragma unroll
-    for (int q = 1; q < VX; ++q)
-      asm("{\n\t.reg .pred p;\n\tsetp.eq.s32 p, %2, %3;\n\tselp.f32 %0, %1, %0, p;\n\t}"
-          : "+f"(v)
-          : "f"(out[q]), "r"(nv - 1), "r"(q));
-    e[1].p[k * e[1].pz] = cvt<T>(v);
-  }
+  if (tm & 2u) e[1].p[k * e[1].pz] = cvt<T>(pick<VX>(out, nv - 1));
 #pragma unroll
   for (int f = 2; f < 4; ++f)
     if (tm & (1u << f)) {

@@ -442,6 +442,325 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
       mbar_wait(smem_u32(&full[f % S]), (f / S) & 1u);
 }
 
+// Two weighted Jacobi sweeps per launch, warp-specialised (temporal
+// blocking for grids whose six faces are walls).  p' = J(p), p'' = J(p')
+// with the same r; p' never leaves the SM.
+//
+// Tile: 128 x TY output cells of one block, walked along z in chunks of zc
+// planes.  Warps: TY + 2 row warps, one extras warp, one producer warp.
+// The producer loads, per plane, the p box (x from i0 - HX, rows j0 - 2 ..
+// j0 + TY + 1) and the r box (rows j0 - 1 .. j0 + TY) into an S-stage ring.
+// In iteration t, row warp w (row y = j0 - 1 + w, 4 cells per lane) takes
+// the first sweep on plane m = k0 - 1 + t over x = i0 .. i0 + 127 and the
+// extras warp the two cells x = i0 - 1 and x = i0 + 128 of every row; both
+// store, rounded to the storage type, into slot t of a shared-memory ring
+// of NS1 first-sweep planes (row width 136: x = i0 - 4 at index 0).  Then
+// row warps 1 .. TY take the second sweep on plane m - 2 from slots t - 3 ..
+// t - 1 and r from the stage of plane m - 2, and write it to global memory
+// with its ghost-on-write images.  An mbarrier per slot (count TY + 3) says
+// that every row of a first-sweep plane is written; each iteration waits
+// for the plane of iteration t - 2, which is all the second sweep needs from
+// other warps and bounds the skew: a warp writing slot t may coexist with
+// one reading slot t - 6, so NS1 = 7.  First-sweep values outside the block
+// (walls: p'_ghost = p'_face) come from the face cell: the x images are
+// written into the ring by the face cell's lane, the y and z images are
+// selected in the second sweep of face rows and planes.
+
+template <typename T, int TY>
+struct Ws2Geom {
+  static constexpr int TX = 128;
+  static constexpr int HX = 16 / (int)sizeof(T);
+  static constexpr int PW = TX + 2 * HX;  // p and r box width
+  static constexpr int PBYTES = PW * (TY + 4) * (int)sizeof(T);
+  static constexpr int RBYTES = PW * (TY + 2) * (int)sizeof(T);
+  static constexpr int PSTRIDE = (PBYTES + 127) / 128 * 128;
+  static constexpr int STAGE = PSTRIDE + (RBYTES + 127) / 128 * 128;
+  static constexpr int SW = 136;            // first-sweep row width (floats)
+  static constexpr int SPLANE = SW * (TY + 2);
+  static constexpr int NS1 = 7;             // first-sweep ring slots
+};
+
+__device__ __forceinline__ float jac_point(float c, float xm, float xp, float ym, float yp, float zm,
+                                           float zp, float r, float cx, float cy, float cz,
+                                           float omega, float inv_diag) {
+  const float nb = (xm + xp) * cx + (ym + yp) * cy + (zm + zp) * cz;
+  return c + omega * ((nb - r) * inv_diag - c);
+}
+
+// x mod n for 0 <= x < 2n
+template <int N>
+__device__ __forceinline__ int wrapn(int x) { return x >= N ? x - N : x; }
+
+template <typename T, int TY, int S>
+__global__ void __launch_bounds__(32 * (TY + 4)) k_jacobi2_ws(Launch L, const CUtensorMap* maps,
+                                                              int zc, int src_slot, int dst,
+                                                              float omega, float inv_diag) {
+  using G = Ws2Geom<T, TY>;
+  constexpr int TX = G::TX, HX = G::HX, PW = G::PW, SW = G::SW, NS1 = G::NS1;
+  constexpr int NW = TY + 2;              // row warps
+  constexpr int PWARP = NW + 1;           // warp NW: extras, warp NW + 1: producer
+  constexpr int STAGE_T = G::STAGE / (int)sizeof(T), RS_T = G::PSTRIDE / (int)sizeof(T);
+  extern __shared__ __align__(128) unsigned char smem[];
+  float* s1 = reinterpret_cast<float*>(smem + S * G::STAGE);
+  unsigned long long* full = reinterpret_cast<unsigned long long*>(s1 + NS1 * G::SPLANE);
+  unsigned long long* empty = full + S;
+  unsigned long long* s1bar = empty + S;
+  __shared__ RowImage<T> rimg[NW][4];
+  const int lane = threadIdx.x, w = threadIdx.y;
+  if (smem_u32(smem) & 127u) {
+    if (w == 0 && lane == 0) atomicOr(L.err_flag, 4);
+    return;
+  }
+  if (w == 0 && lane == 0) {
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+      mbar_init(smem_u32(&full[s]), 1);
+      mbar_init(smem_u32(&empty[s]), NW + 1);
+    }
+#pragma unroll
+    for (int s = 0; s < NS1; ++s) mbar_init(smem_u32(&s1bar[s]), NW + 1);
+    mbar_fence_init();
+  }
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, zc);  // also orders the barrier init before use
+  const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  const int g = L.ghost;
+  constexpr int xo = kAlignBytes / (int)sizeof(T);
+  const T* ring = reinterpret_cast<const T*>(smem);
+  unsigned seq = 0;     // p/r planes of this CTA so far
+  unsigned it1 = 0;     // first-sweep iterations of this CTA so far
+  unsigned issued = 0;  // planes the producer has issued
+  bool bad = false;
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int k1 = min(k0 + zc, nz);
+    const int nzc = k1 - k0;
+    const int np = nzc + 4;  // p planes k0 - 2 .. k1 + 1
+    if (w == PWARP) {
+      // ---------------- producer
+      if (lane == 0) {
+        const CUtensorMap* mp = maps + 3 * blk + src_slot;
+        const CUtensorMap* mr = maps + 3 * blk + 2;
+        const int bx = xo + i0 - HX, py0 = g + j0 - 2, ry0 = g + j0 - 1;
+        Ring<S> at(seq);
+        for (int q = 0; q < np; ++q, at.next()) {
+          bad |= !mbar_wait(smem_u32(&empty[at.s]), at.ph ^ 1u);
+          if (bad) break;
+          ++issued;
+          const int z = g + k0 - 2 + q;
+          const bool need_r = (q >= 1 && q <= np - 2);
+          const uint32_t bar = smem_u32(&full[at.s]);
+          unsigned char* st = smem + at.s * G::STAGE;
+          mbar_expect_tx(bar, G::PBYTES + (need_r ? G::RBYTES : 0));
+          tma_load_3d(smem_u32(st), mp, bx, py0, z, bar);
+          if (need_r) tma_load_3d(smem_u32(st + G::PSTRIDE), mr, bx, ry0, z, bar);
+        }
+      }
+      seq += np;
+      it1 += nzc + 2;
+      if (bad) break;
+      continue;
+    }
+    // ---------------- row warps and the extras warp
+    const bool rowwarp = w < NW;
+    const int y = j0 - 1 + w;  // row of a row warp
+    const bool yreal = rowwarp && y >= 0 && y < ny;
+    const bool out_row = w >= 1 && w <= TY && yreal;  // second-sweep rows of this tile
+    const int xl = lane * 4;
+    const int x0 = i0 + xl;
+    const int nv = min(4, nx - x0);          // cells of this lane inside the block
+    const int prow = (w + 1) * PW + HX + xl; // p box: this lane's first cell
+    const int rrow = RS_T + w * PW + HX + xl;
+    const int srow = w * SW + 4 + xl;        // first-sweep ring
+    const bool xhi_in = nv >= 1 && x0 + nv == nx;  // this lane holds x = nx - 1
+    // extras warp: cell c < 2 NW is row c / 2, x = i0 - 1 (even c) or i0 + 128;
+    // lane l takes cells l and l + 32
+    constexpr int NE = (2 * NW + 31) / 32;
+    unsigned tm = 0;
+    if (rowwarp) {
+      __syncwarp();
+      unsigned rm = 0;
+      if (lane == 0 && out_row) rm = row_images<T>(L, B, dst, i0, TX, y, rimg[w]);
+      tm = thread_images<4>(__shfl_sync(0xffffffffu, rm, 0), lane, x0, nx);
+      __syncwarp();
+    }
+    const long long pzl = B.pz;
+    T* qrow = reinterpret_cast<T*>(L.base) + B.org[dst] + (long long)y * B.py + x0 +
+              (long long)k0 * pzl;  // plane k0 of the output row
+    auto release = [&](int st) {
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
+    };
+    // ring positions: stage of plane m - 1 (q = t) with its phase, slot of
+    // iteration t with the phase of its barrier
+    int sq = (int)(seq % S);
+    uint32_t phq = (seq / S) & 1u;
+    int sl = (int)(it1 % NS1);
+    uint32_t phl = (it1 / NS1) & 1u;
+    {
+      // planes k0 - 2 and k0 - 1 must be there before the first iteration
+      const int s1_ = wrapn<S>(sq + 1);
+      bad |= !mbar_wait(smem_u32(&full[sq]), phq);
+      bad |= !mbar_wait(smem_u32(&full[s1_]), phq ^ (uint32_t)(sq + 1 >= S));
+    }
+    for (int t2 = 0; t2 <= nzc + 2 && !bad; ++t2) {
+      const int m = k0 - 1 + t2;  // first-sweep plane of this iteration
+      const int sc = wrapn<S>(sq + 1), sp = wrapn<S>(sq + 2);
+      if (t2 <= nzc + 1) {
+        // ---- first sweep on plane m: stages sq (m - 1), sc (m), sp (m + 1)
+        bad |= !mbar_wait(smem_u32(&full[sp]), phq ^ (uint32_t)(sq + 2 >= S));
+        if (bad) break;
+        const T* Pm = ring + sq * STAGE_T;
+        const T* Pc = ring + sc * STAGE_T;
+        const T* Pp = ring + sp * STAGE_T;
+        float* S1 = s1 + sl * G::SPLANE;
+        const bool mreal = m >= 0 && m < nz;
+        if (yreal && mreal && nv > 0) {
+          float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
+          ldv<4>(Pc + prow, c);
+          ldv<4>(Pm + prow, zm);
+          ldv<4>(Pp + prow, zp);
+          ldv<4>(Pc + prow + PW, yp);
+          ldv<4>(Pc + prow - PW, ym);
+          ldv<4>(Pc + rrow, rr);
+          const float left = tof(Pc[prow - 1]);
+          const float right = tof(Pc[prow + 4]);
+          float o[4];
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            const float xm = e == 0 ? left : c[e - 1];
+            const float xp = e == 3 ? right : c[e + 1];
+            o[e] = tof(cvt<T>(jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy,
+                                        cz, omega, inv_diag)));
+          }
+          *reinterpret_cast<float4*>(S1 + srow) = make_float4(o[0], o[1], o[2], o[3]);
+          if (lane == 0 && i0 == 0) S1[srow - 1] = o[0];   // x = -1 <- x = 0
+          if (xhi_in) S1[srow + nv] = pick<4>(o, nv - 1);  // x = nx <- x = nx - 1
+        }
+        if (!rowwarp && mreal) {
+#pragma unroll
+          for (int q = 0; q < NE; ++q) {
+            const int ce = lane + 32 * q;
+            const int er = ce >> 1, ex = (ce & 1) ? i0 + TX : i0 - 1, ey = j0 - 1 + er;
+            if (ce < 2 * NW && ex >= 0 && ex < nx && ey >= 0 && ey < ny) {
+              const int epi = (er + 1) * PW + HX + (ex - i0);
+              const int eri = RS_T + er * PW + HX + (ex - i0);
+              S1[er * SW + 4 + (ex - i0)] = tof(cvt<T>(
+                  jac_point(tof(Pc[epi]), tof(Pc[epi - 1]), tof(Pc[epi + 1]), tof(Pc[epi - PW]),
+                            tof(Pc[epi + PW]), tof(Pm[epi]), tof(Pp[epi]), tof(Pc[eri]), cx, cy, cz,
+                            omega, inv_diag)));
+            }
+          }
+        }
+        __syncwarp();
+        if (lane == 0) mbar_arrive(smem_u32(&s1bar[sl]));
+      }
+      // every iteration (also across tiles) waits until every row of the
+      // first-sweep plane of two iterations before is written
+      const int sl2 = sl >= 2 ? sl - 2 : sl + NS1 - 2;
+      if (it1 + t2 >= 2) {
+        bad |= !mbar_wait(smem_u32(&s1bar[sl2]), phl ^ (uint32_t)(sl < 2));
+        if (bad) break;
+      }
+      if (t2 >= 3 && out_row && nv > 0) {
+        // ---- second sweep on plane P = m - 2: slots sl - 3, sl - 2, sl - 1;
+        // r from the stage of plane P (q = t - 1)
+        const int P = m - 2;
+        const float* A = s1 + (sl >= 3 ? sl - 3 : sl + NS1 - 3) * G::SPLANE + srow;
+        const float* Bc = s1 + sl2 * G::SPLANE + srow;
+        const float* C = s1 + (sl >= 1 ? sl - 1 : NS1 - 1) * G::SPLANE + srow;
+        const T* Rp = ring + (sq >= 1 ? sq - 1 : S - 1) * STAGE_T;
+        float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
+        ldv<4>(Bc, c);
+        ldv<4>(A, zm);
+        ldv<4>(C, zp);
+        ldv<4>(Bc + SW, yp);
+        ldv<4>(Bc - SW, ym);
+        ldv<4>(Rp + rrow, rr);
+        const float left = Bc[-1];
+        const float right = Bc[4];
+        if ((y == 0) | (y == ny - 1) | (P == 0) | (P == nz - 1)) {
+          // face rows and planes: the first sweep's ghost is the face value
+#pragma unroll
+          for (int e = 0; e < 4; ++e) {
+            if (y == 0) ym[e] = c[e];
+            if (y == ny - 1) yp[e] = c[e];
+            if (P == 0) zm[e] = c[e];
+            if (P == nz - 1) zp[e] = c[e];
+          }
+        }
+        float out[4];
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          const float xm = e == 0 ? left : c[e - 1];
+          const float xp = e == 3 ? right : c[e + 1];
+          out[e] = jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy, cz, omega,
+                             inv_diag);
+        }
+        T* qk = qrow + (long long)(P - k0) * pzl;
+        if (nv >= 4) {
+          stv<T, 4>(qk, out);
+        } else {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (e < nv) qk[e] = cvt<T>(out[e]);
+        }
+        if (tm) put_row_images<T, 4>(rimg[w], tm, P, xl, nv, out);
+        if ((P == 0) | (P == nz - 1)) {
+#pragma unroll
+          for (int e = 0; e < 4; ++e)
+            if (e < nv) p_ghost_z<T>(L, B, dst, x0 + e, y, P, cvt<T>(out[e]));
+        }
+      }
+      if (t2 >= 1) release(sq >= 1 ? sq - 1 : S - 1);  // plane m - 2 (q = t - 1) is done
+      if (++sq == S) {
+        sq = 0;
+        phq ^= 1u;
+      }
+      if (t2 <= nzc + 1 && ++sl == NS1) {
+        sl = 0;
+        phl ^= 1u;
+      }
+    }
+    if (bad) break;
+    // stages of planes k1, k1 + 1 (q = nzc + 2, nzc + 3): sq now points at q = nzc + 3
+    release(sq >= 1 ? sq - 1 : S - 1);
+    release(sq);
+    seq += np;
+    it1 += nzc + 2;
+  }
+  if (bad && lane == 0) atomicOr(L.err_flag, 2);
+  if (w == PWARP && lane == 0)  // never leave with our own copies in flight
+    for (unsigned f = issued > (unsigned)S ? issued - S : 0; f < issued; ++f)
+      mbar_wait(smem_u32(&full[f % S]), (f / S) & 1u);
+}
+
+template <typename T, int TY, int S>
+cudaError_t run_ws2(const Launch& L, const JacobiCfg& c, const void* maps, int src_slot, int dst,
+                    float omega, float inv_diag) {
+  using G = Ws2Geom<T, TY>;
+  auto kern = k_jacobi2_ws<T, TY, S>;
+  const int smem = S * G::STAGE + G::NS1 * G::SPLANE * 4 + 8 * (2 * S + G::NS1);
+  static int occ = -1;
+  if (occ < 0) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);
+    if (e != cudaSuccess) return e;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, kern, 32 * (TY + 4), smem) != cudaSuccess ||
+        occ < 1)
+      occ = 1;
+  }
+  const long long tiles = count_tiles(L, G::TX, TY, c.zc);
+  long long grid = (long long)L.sms * occ;
+  if (tiles < grid) grid = tiles;
+  kern<<<(unsigned)(grid > 0 ? grid : 1), dim3(32, TY + 4), smem, L.stream>>>(
+      L, static_cast<const CUtensorMap*>(maps), c.zc, src_slot, dst, omega, inv_diag);
+  return cudaGetLastError();
+}
+
 template <typename T, int VX, int TY, int S>
 cudaError_t run_ws(const Launch& L, const JacobiCfg& c, const void* maps, int src_slot, int dst,
                    float omega, float inv_diag) {
@@ -519,8 +838,11 @@ bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int
     const bool is_r = (a % 3) == 2;
     cuuint64_t dims[3] = {(cuuint64_t)A.row_elems, (cuuint64_t)A.rows, (cuuint64_t)A.planes};
     cuuint64_t strides[2] = {(cuuint64_t)A.row_elems * es, (cuuint64_t)A.row_elems * A.rows * es};
-    cuuint32_t box[3] = {(cuuint32_t)tma_box_x(dtype, c.vx, !is_r),
-                         (cuuint32_t)(c.ty + (is_r ? 0 : 2)), 1};
+    // kind 9 (two sweeps): p box rows j0 - 2 .. j0 + ty + 1, r box with the
+    // same x halo and rows j0 - 1 .. j0 + ty
+    const bool two = c.kind == 9;
+    cuuint32_t box[3] = {(cuuint32_t)tma_box_x(dtype, c.vx, two || !is_r),
+                         (cuuint32_t)(c.ty + (two ? (is_r ? 2 : 4) : (is_r ? 0 : 2))), 1};
     cuuint32_t estr[3] = {1, 1, 1};
     memset(&maps[a], 0, sizeof(CUtensorMap));
     CUresult r = enc(&maps[a], dt, 3, A.ptr, dims, strides, box, estr, CU_TENSOR_MAP_INTERLEAVE_NONE,
@@ -537,6 +859,19 @@ bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int
     case 1: { using T = __nv_bfloat16; __VA_ARGS__; } break; \
     default: { using T = __half; __VA_ARGS__; } break;       \
   }
+
+cudaError_t launch_jacobi2_ws(const Launch& L, const JacobiCfg& c, const void* maps_dev,
+                              int src_slot, int dst, float omega) {
+  const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+  cudaError_t e = cudaErrorInvalidValue;
+  CFD_DISPATCH_T(L.dtype, {
+    if (c.ty == 16 && c.stages == 7) e = run_ws2<T, 16, 7>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.ty == 16) e = run_ws2<T, 16, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.stages == 6) e = run_ws2<T, 8, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else e = run_ws2<T, 8, 5>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+  });
+  return e;
+}
 
 cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* maps_dev,
                               int src_slot, int dst, float omega) {

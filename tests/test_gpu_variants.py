@@ -205,7 +205,8 @@ def test_per_block_launch_mode_is_bitwise_identical(g):
 
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 @pytest.mark.parametrize("cfg", [(3, 8, 4, 32, 5), (3, 8, 8, 16, 6), (3, 8, 2, 64, 6),
-                                 (1, 4, 8, 32, 6), (2, 4, 4, 2, 0), (7, 4, 8, 32, 8)],
+                                 (1, 4, 8, 32, 6), (2, 4, 4, 2, 0), (7, 4, 8, 32, 8),
+                                 (9, 4, 16, 16, 6), (9, 4, 8, 32, 5)],
                          ids=cfg_id)
 def test_16bit_jacobi_variants_agree_with_register_sweep(dtype, cfg):
     """Every 16-bit sweep variant computes the same FP32 expression and
@@ -280,15 +281,65 @@ def test_fused_two_sweep_launches_match_oracle(cfg, bc, iters, dims):
     g.check()
 
 
+@pytest.mark.parametrize("cfg", [(9, 4, 16, 16, 7), (9, 4, 8, 7, 5), (9, 4, 8, 64, 6), (9, 4, 16, 3, 6)],
+                         ids=cfg_id)
+@pytest.mark.parametrize("iters", [1, 2, 5, 10])
+@pytest.mark.parametrize("dims", [(128, 40, 21), (150, 37, 21), (300, 16, 2), (70, 5, 33)])
+def test_two_sweep_ws_launches_match_oracle(cfg, iters, dims):
+    """Warp-specialised two-sweep launches (walls on all faces) on full and
+    ragged tiles, chunk edges at the walls and inside, odd counts, against
+    the oracle; the result's first ghost layer as the oracle's fill."""
+    from paper_1201_2118_gb300 import P, WU, WV, WW, mask
+    o, g, u, p = make_pair(dims, bc="cavity", fields=rand(dims, 13))
+    g.set_kernel_config(jacobi=cfg)
+    assert g.kernel_config()[0] == cfg
+    w = rounded(rand(dims, 14))
+    for k, a in enumerate((WU, WV, WW)):
+        g.interior(a).copy_(g.torch.from_numpy(w["uvw"[k]]).float().cuda())
+    g.ghost_fill(mask(WU, WV, WW))
+    wo = [o.ghost_fill(o.embed(w["uvw"[k]]), k) for k in range(3)]
+    g.pressure_solve(0.05, iters)
+    r = o.divergence(wo, 0.05)
+    o.jacobi(p, r, iters)
+    assert rel_err(g.download(P), o.interior(p)) < 1e-5
+    gp = g.download(P, ghosts=True)
+    for ax in range(3):
+        for side in (0, -1):
+            sl = [slice(1, -1)] * 3
+            sl[2 - ax] = side
+            assert rel_err(gp[tuple(sl)], p[tuple(sl)]) < 1e-5
+    g.check()
+
+
+def test_two_sweep_ws_on_periodic_grid_takes_single_sweeps():
+    """On a grid with periodic faces the two-sweep variant does not apply;
+    the solve still matches the oracle (single sweeps)."""
+    from paper_1201_2118_gb300 import P, WU, WV, WW, mask
+    dims = (128, 40, 21)
+    o, g, u, p = make_pair(dims, bc="periodic", fields=rand(dims, 15))
+    g.set_kernel_config(jacobi=(9, 4, 16, 16, 6))
+    w = rounded(rand(dims, 16))
+    for k, a in enumerate((WU, WV, WW)):
+        g.interior(a).copy_(g.torch.from_numpy(w["uvw"[k]]).float().cuda())
+    g.ghost_fill(mask(WU, WV, WW))
+    wo = [o.ghost_fill(o.embed(w["uvw"[k]]), k) for k in range(3)]
+    g.pressure_solve(0.05, 6)
+    r = o.divergence(wo, 0.05)
+    o.jacobi(p, r, 6)
+    assert rel_err(g.download(P), o.interior(p)) < 1e-5
+    g.check()
+
+
 def test_fused_sweeps_in_full_steps_match_single_sweeps():
     from paper_1201_2118_gb300 import U, V, W, P
     n = (128, 64, 48)
     h = (1.0 / 128,) * 3
     res = []
-    for cfg in ((0, 4, 4, 32, 4), (5, 4, 4, 32, 0)):
+    for cfg in ((0, 4, 4, 32, 4), (5, 4, 4, 32, 0), (9, 4, 16, 16, 6)):
         o, g, u, p = make_pair(n, bc="cavity", h=h, nu=1e-3, fields=workloads.ldc_noise(n, seed=1))
         g.set_kernel_config(jacobi=cfg)
         g.step(workloads.cfl_dt(h), 3)
         res.append([g.download(a) for a in (U, V, W, P)])
-    for a, b in zip(*res):
-        assert rel_err(a, b) < 1e-5
+    for other in res[1:]:
+        for a, b in zip(res[0], other):
+            assert rel_err(a, b) < 1e-5
