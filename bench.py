@@ -145,14 +145,15 @@ class ClockSampler:
 
 def traffic_for(kernel_hash: str, cells: int, config):
     """DRAM bytes per Jacobi launch from the committed ncu summary, scaled to
-    this launch's cells; None when the kernel source or the variant differs
-    from the captured one."""
+    this launch's cells; None when the kernel source or the variant's tile
+    (kind, vx, ty, zc) differs from the captured one."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except Exception:
         return None
-    if t.get("kernel_sha256") != kernel_hash or list(t.get("config", [])) != list(config):
+    # the ring depth (last config entry) does not change which bytes move
+    if t.get("kernel_sha256") != kernel_hash or list(t.get("config", []))[:4] != list(config)[:4]:
         return None
     return t["dram_bytes_per_cell"] * cells
 

@@ -492,7 +492,7 @@ template <int N>
 __device__ __forceinline__ int wrapn(int x) { return x >= N ? x - N : x; }
 
 template <typename T, int TY, int S>
-__global__ void __launch_bounds__(32 * (TY + 4)) k_jacobi2_ws(Launch L, const CUtensorMap* maps,
+__global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const CUtensorMap* maps,
                                                               int zc, int src_slot, int dst,
                                                               float omega, float inv_diag) {
   using G = Ws2Geom<T, TY>;

@@ -481,31 +481,24 @@ __global__ void __launch_bounds__(32 * TY) k_project(Launch L, int zc, Set3 ws, 
   }
 }
 
-template <typename T, int TY>
-__global__ void __launch_bounds__(32 * TY) k_copy(Launch L, int zc, int src, int dst) {
-  __shared__ TileTable tt;
-  tile_table_build(tt, L, 32, TY, zc);
-  int blk = L.b0;
+// Whole-array copy (every plane, row and padding element of each block's
+// array; an array is one contiguous 128-byte-aligned span of planes x pz
+// elements starting g planes, g rows and 128 bytes before the interior
+// origin), in 16-byte vectors.
+template <typename T>
+__global__ void __launch_bounds__(256) k_copy(Launch L, int src, int dst) {
+  constexpr int V = 16 / (int)sizeof(T);
+  constexpr int xo = kAlignBytes / (int)sizeof(T);
   const int g = L.ghost;
-  for (long long t = blockIdx.x;; t += gridDim.x) {
-    int i0, j0, k0;
-    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
-    const BlockDev& B = L.blocks[blk];
-    // copies the full ghosted extent: tiles cover the interior, edge tiles
-    // also take the ghost layers next to them
-    const T* s = reinterpret_cast<const T*>(L.base) + B.org[src];
-    T* d = wptr<T>(L, B, dst);
-    const int k1 = min(k0 + zc, B.n[2]);
-    const int ilo = (i0 == 0) ? -g : i0, jlo = (j0 == 0) ? -g : j0;
-    const int ihi = min(i0 + 32, B.n[0]) + (i0 + 32 >= B.n[0] ? g : 0);
-    const int jhi = min(j0 + TY, B.n[1]) + (j0 + TY >= B.n[1] ? g : 0);
-    const int klo = (k0 == 0) ? -g : k0, khi = k1 + (k1 == B.n[2] ? g : 0);
-    for (int k = klo; k < khi; ++k)
-      for (int jj = jlo + threadIdx.y; jj < jhi; jj += TY)
-        for (int ii = ilo + threadIdx.x; ii < ihi; ii += 32) {
-          const long long o = (long long)k * B.pz + (long long)jj * B.py + ii;
-          d[o] = s[o];
-        }
+  for (int b = L.b0; b < L.b0 + L.nblocks; ++b) {
+    const BlockDev& B = L.blocks[b];
+    const long long lead = (long long)g * B.pz + (long long)g * B.py + xo;
+    const long long n = (long long)(B.n[2] + 2 * g) * B.pz / V;
+    const uint4* s4 =
+        reinterpret_cast<const uint4*>(reinterpret_cast<const T*>(L.base) + B.org[src] - lead);
+    uint4* d4 = reinterpret_cast<uint4*>(reinterpret_cast<T*>(L.base) + B.org[dst] - lead);
+    for (long long i = (long long)blockIdx.x * 256 + threadIdx.x; i < n; i += (long long)gridDim.x * 256)
+      d4[i] = s4[i];
   }
 }
 
@@ -1387,12 +1380,11 @@ cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset
   return cudaGetLastError();
 }
 
-cudaError_t launch_copy(const Launch& L, const StencilCfg& c, int src, int dst) {
-  const long long tiles = count_tiles(L, 32, 8, c.zc);
+cudaError_t launch_copy(const Launch& L, const StencilCfg&, int src, int dst) {
   CFD_DISPATCH_T(L.dtype, {
-    auto kern = k_copy<T, 8>;
+    auto kern = k_copy<T>;
     static const int occ = occupancy(kern, 256);
-    kern<<<grid_for(L, occ, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, src, dst);
+    kern<<<(unsigned)(L.sms * occ), 256, 0, L.stream>>>(L, src, dst);
   });
   return cudaGetLastError();
 }
