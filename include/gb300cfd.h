@@ -231,7 +231,11 @@ cfd_status cfd_set_state(cfd_grid* g, double t, long long step);
 
 /* Copy the interior of one array of one block between host memory
  * (compact (nz, ny, nx), storage dtype; pinned for asynchronous copies)
- * and the device.  to_device != 0: host -> device.  Asynchronous. */
+ * and the device.  to_device != 0: host -> device.  Asynchronous: the host
+ * buffer must stay valid and untouched until the grid's stream has reached
+ * this point.  Page-locked buffers are read or written directly by a
+ * kernel over the host link; others go through a contiguous staging copy
+ * in the grid's memory (one interior of the largest block). */
 cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int to_device);
 
 /* Kernel variants.  jacobi = {kind, vx, ty, zc, stages}: kind 0 is the

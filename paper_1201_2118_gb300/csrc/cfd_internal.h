@@ -89,6 +89,11 @@ bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int
                         const JacobiCfg& c);
 cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* maps_dev,
                               int src_slot, int dst, float omega);
+// Interior of one array of the launch's (single) block <-> a compact
+// (nz, ny, nx) buffer in device memory: to_compact 0 scatters the buffer
+// into the array, 1 gathers the array into the buffer.
+cudaError_t launch_pack(const Launch& L, int arr, void* compact, int to_compact);
+
 // Two sweeps per launch (kind 9), src -> dst; single block, walls on all faces.
 cudaError_t launch_jacobi2_ws(const Launch& L, const JacobiCfg& c, const void* maps_dev,
                               int src_slot, int dst, float omega);

@@ -1089,6 +1089,43 @@ __global__ void __launch_bounds__(32 * TY * TZ) k_jacobi_direct(Launch L, int sr
   }
 }
 
+// ---------------------------------------------------- compact <-> padded
+
+// One warp per interior row: the compact buffer holds rows of nx elements
+// back to back, the array rows start 128-byte aligned at x = 0.  Rows whose
+// compact start is 16-byte aligned move as 16-byte vectors.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack(Launch L, int arr, T* compact, int to_compact) {
+  constexpr int V = 16 / (int)sizeof(T);
+  const BlockDev& B = L.blocks[L.b0];
+  const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+  const int py = B.py;
+  const long long pz = B.pz;
+  T* a = reinterpret_cast<T*>(L.base) + B.org[arr];
+  const long long rows = (long long)ny * nz;
+  const int lane = threadIdx.x & 31;
+  const bool vec = (nx % V) == 0;
+  for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows;
+       r += ((long long)gridDim.x * blockDim.x) >> 5) {
+    const int j = (int)(r % ny), k = (int)(r / ny);
+    T* ar = a + (long long)k * pz + (long long)j * py;
+    T* cr = compact + r * nx;
+    if (vec) {
+      uint4* av = reinterpret_cast<uint4*>(ar);
+      uint4* cv = reinterpret_cast<uint4*>(cr);
+      for (int i = lane; i < nx / V; i += 32) {
+        if (to_compact) cv[i] = av[i];
+        else av[i] = cv[i];
+      }
+    } else {
+      for (int i = lane; i < nx; i += 32) {
+        if (to_compact) cr[i] = ar[i];
+        else ar[i] = cr[i];
+      }
+    }
+  }
+}
+
 // --------------------------------------------------------------- reductions
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1376,6 +1413,16 @@ cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset
     auto kern = k_project<T, 8>;
     static const int occ = occupancy(kern, 256);
     kern<<<grid_for(L, occ, tiles), dim3(32, 8), 0, L.stream>>>(L, c.zc, mk3(wset), p_arr, cdt, mk3(oset));
+  });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack(const Launch& L, int arr, void* compact, int to_compact) {
+  CFD_DISPATCH_T(L.dtype, {
+    auto kern = k_pack<T>;
+    static const int occ = occupancy(kern, 256);
+    kern<<<(unsigned)(L.sms * occ), 256, 0, L.stream>>>(L, arr, static_cast<T*>(compact),
+                                                       to_compact);
   });
   return cudaGetLastError();
 }

@@ -8,6 +8,8 @@ sweep variants.
 builds an n^3 lid-driven cavity grid (seeded cavity noise), and for each
 given Jacobi variant (kind,vx,ty,zc,stages) runs the requested number of
 sweeps on the grid's stream, then checks the device error flag.  With
+--stages N it runs N RHS + stage-2 combines per stencil variant
+(ty,zc,tile_tz) instead (--order 2 or 4).  With
 --time, each variant first runs 4 warm-up sweeps and the timed sweeps are
 bracketed by CUDA events on the grid's stream; the line printed per variant
 gives microseconds per sweep and the algorithmic bytes (read p and r, write
@@ -25,6 +27,10 @@ def main(argv=None):
     ap.add_argument("--jacobi", nargs="*", default=[], help="kind,vx,ty,zc,stages ...")
     ap.add_argument("--sweeps", type=int, default=12)
     ap.add_argument("--time", action="store_true")
+    ap.add_argument("--stages", type=int, default=0,
+                    help="instead of sweeps: this many RHS + stage-2 combines per stencil variant")
+    ap.add_argument("--stencil", nargs="*", default=[], help="ty,zc,tile_tz ...")
+    ap.add_argument("--order", type=int, default=2, choices=[2, 4])
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -34,11 +40,38 @@ def main(argv=None):
     from paper_1201_2118_gb300 import Grid
     n = a.n
     s = torch.cuda.Stream()
-    g = Grid((n, n, n), ghost=1, h=(1.0 / n,) * 3, dtype=a.dtype, stream=s)
+    g = Grid((n, n, n), ghost=1 if a.order == 2 else 2, h=(1.0 / n,) * 3, dtype=a.dtype, stream=s)
     g.set_cavity(1.0)
+    g.set_params(1e-3, 50, 1.0, a.order)
     g.upload(workloads.ldc_noise(n, seed=1))
     g.pressure_solve(1e-3, 0)
     es = 4 if a.dtype == "f32" else 2
+    if a.stages:
+        from paper_1201_2118_gb300 import SET_U, SET_U1, SET_W
+        for c in a.stencil or [None]:
+            if c is not None:
+                g.set_kernel_config(stencil=tuple(int(x) for x in c.split(",")))
+            cfg = g.kernel_config()[1]
+            # stage-2 form: w = 1/2 u + 1/2 u1 + 1/2 dt F(u1), 36 B/cell
+            run = lambda k: [g.stage(0.5, SET_U, 0.5, SET_U1, 1e-4, SET_W) for _ in range(k)]
+            if not a.time:
+                run(a.stages)
+                torch.cuda.synchronize()
+                print("ok", n, a.dtype, "stencil", cfg, a.stages, flush=True)
+                continue
+            run(2)
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            run(a.stages)
+            e1.record(s)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / a.stages
+            gbs = 9 * es * n ** 3 / (us * 1e-6) / 1e9
+            print("%d^3 %s order %d stencil %s %.1f us/stage %.0f GB/s" % (n, a.dtype, a.order, cfg, us, gbs),
+                  flush=True)
+        g.check()
+        return
     for c in a.jacobi or [None]:
         if c is not None:
             g.set_kernel_config(jacobi=tuple(int(x) for x in c.split(",")))
