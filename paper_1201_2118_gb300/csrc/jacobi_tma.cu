@@ -82,6 +82,18 @@ __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
     if (gtimer() - t0 > kWaitLimitNs) return false;
   return true;
 }
+__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity) {
+  const unsigned long long t0 = gtimer();
+  while (!mbar_try_wait_sleep(bar, parity))
+    if (gtimer() - t0 > kWaitLimitNs) return false;
+  return true;
+}
+// The same bounded wait with the polling loop out of line (less code in
+// kernels that wait several times per plane; the call raises the register
+// count of kernels that run two CTAs per SM, which use mbar_wait).
+__device__ __forceinline__ bool mbar_wait_split(uint32_t bar, uint32_t parity) {
+  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
+}
 __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
                                             int z, uint32_t bar) {
   asm volatile(
@@ -461,7 +473,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
 // that every row of a first-sweep plane is written; each iteration waits
 // for the plane of iteration t - 2, which is all the second sweep needs from
 // other warps and bounds the skew: a warp writing slot t may coexist with
-// one reading slot t - 6, so NS1 = 7.  First-sweep values outside the block
+// one reading slot t - 6, so NS1 >= 7; it is 8.  First-sweep values outside the block
 // (walls: p'_ghost = p'_face) come from the face cell: the x images are
 // written into the ring by the face cell's lane, the y and z images are
 // selected in the second sweep of face rows and planes.
@@ -477,7 +489,7 @@ struct Ws2Geom {
   static constexpr int STAGE = PSTRIDE + (RBYTES + 127) / 128 * 128;
   static constexpr int SW = 136;            // first-sweep row width (floats)
   static constexpr int SPLANE = SW * (TY + 2);
-  static constexpr int NS1 = 7;             // first-sweep ring slots
+  static constexpr int NS1 = 8;             // first-sweep ring slots (a power of two)
 };
 
 __device__ __forceinline__ float jac_point(float c, float xm, float xp, float ym, float yp, float zm,
@@ -595,135 +607,164 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       __syncwarp();
       if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
     };
-    // ring positions: stage of plane m - 1 (q = t) with its phase, slot of
-    // iteration t with the phase of its barrier
+    // ring positions: stage of plane m - 1 (q = t) with its phase; first-
+    // sweep iterations are numbered across tiles (u = it1 + t), slot u % 8
     int sq = (int)(seq % S);
     uint32_t phq = (seq / S) & 1u;
-    int sl = (int)(it1 % NS1);
-    uint32_t phl = (it1 / NS1) & 1u;
-    {
-      // planes k0 - 2 and k0 - 1 must be there before the first iteration
-      const int s1_ = wrapn<S>(sq + 1);
-      bad |= !mbar_wait(smem_u32(&full[sq]), phq);
-      bad |= !mbar_wait(smem_u32(&full[s1_]), phq ^ (uint32_t)(sq + 1 >= S));
-    }
-    for (int t2 = 0; t2 <= nzc + 2 && !bad; ++t2) {
-      const int m = k0 - 1 + t2;  // first-sweep plane of this iteration
+    const bool act1 = yreal && nv > 0;                 // this lane has first-sweep cells
+    const bool act2 = out_row && nv > 0;               // ... and second-sweep outputs
+    const bool yface = (y == 0) | (y == ny - 1);
+    auto wait_full = [&](int st, uint32_t ph) {
+      if (!mbar_wait_split(smem_u32(&full[st]), ph)) bad = true;
+    };
+    auto wait_s1 = [&](unsigned u) {
+      if (!mbar_wait_split(smem_u32(&s1bar[u & (NS1 - 1)]), (u / NS1) & 1u)) bad = true;
+    };
+    // first sweep on plane m = k0 - 1 + t into slot u = it1 + t
+    auto sweep1 = [&](int t) {
+      const int m = k0 - 1 + t;
       const int sc = wrapn<S>(sq + 1), sp = wrapn<S>(sq + 2);
-      if (t2 <= nzc + 1) {
-        // ---- first sweep on plane m: stages sq (m - 1), sc (m), sp (m + 1)
-        bad |= !mbar_wait(smem_u32(&full[sp]), phq ^ (uint32_t)(sq + 2 >= S));
-        if (bad) break;
-        const T* Pm = ring + sq * STAGE_T;
-        const T* Pc = ring + sc * STAGE_T;
-        const T* Pp = ring + sp * STAGE_T;
-        float* S1 = s1 + sl * G::SPLANE;
-        const bool mreal = m >= 0 && m < nz;
-        if (yreal && mreal && nv > 0) {
-          float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
-          ldv<4>(Pc + prow, c);
-          ldv<4>(Pm + prow, zm);
-          ldv<4>(Pp + prow, zp);
-          ldv<4>(Pc + prow + PW, yp);
-          ldv<4>(Pc + prow - PW, ym);
-          ldv<4>(Pc + rrow, rr);
-          const float left = tof(Pc[prow - 1]);
-          const float right = tof(Pc[prow + 4]);
-          float o[4];
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            const float xm = e == 0 ? left : c[e - 1];
-            const float xp = e == 3 ? right : c[e + 1];
-            o[e] = tof(cvt<T>(jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy,
-                                        cz, omega, inv_diag)));
-          }
-          *reinterpret_cast<float4*>(S1 + srow) = make_float4(o[0], o[1], o[2], o[3]);
-          if (lane == 0 && i0 == 0) S1[srow - 1] = o[0];   // x = -1 <- x = 0
-          if (xhi_in) S1[srow + nv] = pick<4>(o, nv - 1);  // x = nx <- x = nx - 1
-        }
-        if (!rowwarp && mreal) {
-#pragma unroll
-          for (int q = 0; q < NE; ++q) {
-            const int ce = lane + 32 * q;
-            const int er = ce >> 1, ex = (ce & 1) ? i0 + TX : i0 - 1, ey = j0 - 1 + er;
-            if (ce < 2 * NW && ex >= 0 && ex < nx && ey >= 0 && ey < ny) {
-              const int epi = (er + 1) * PW + HX + (ex - i0);
-              const int eri = RS_T + er * PW + HX + (ex - i0);
-              S1[er * SW + 4 + (ex - i0)] = tof(cvt<T>(
-                  jac_point(tof(Pc[epi]), tof(Pc[epi - 1]), tof(Pc[epi + 1]), tof(Pc[epi - PW]),
-                            tof(Pc[epi + PW]), tof(Pm[epi]), tof(Pp[epi]), tof(Pc[eri]), cx, cy, cz,
-                            omega, inv_diag)));
-            }
-          }
-        }
-        __syncwarp();
-        if (lane == 0) mbar_arrive(smem_u32(&s1bar[sl]));
-      }
-      // every iteration (also across tiles) waits until every row of the
-      // first-sweep plane of two iterations before is written
-      const int sl2 = sl >= 2 ? sl - 2 : sl + NS1 - 2;
-      if (it1 + t2 >= 2) {
-        bad |= !mbar_wait(smem_u32(&s1bar[sl2]), phl ^ (uint32_t)(sl < 2));
-        if (bad) break;
-      }
-      if (t2 >= 3 && out_row && nv > 0) {
-        // ---- second sweep on plane P = m - 2: slots sl - 3, sl - 2, sl - 1;
-        // r from the stage of plane P (q = t - 1)
-        const int P = m - 2;
-        const float* A = s1 + (sl >= 3 ? sl - 3 : sl + NS1 - 3) * G::SPLANE + srow;
-        const float* Bc = s1 + sl2 * G::SPLANE + srow;
-        const float* C = s1 + (sl >= 1 ? sl - 1 : NS1 - 1) * G::SPLANE + srow;
-        const T* Rp = ring + (sq >= 1 ? sq - 1 : S - 1) * STAGE_T;
+      wait_full(sp, phq ^ (uint32_t)(sq + 2 >= S));
+      if (bad) return;
+      const T* Pm = ring + sq * STAGE_T;
+      const T* Pc = ring + sc * STAGE_T;
+      const T* Pp = ring + sp * STAGE_T;
+      float* S1 = s1 + (int)((it1 + t) & (NS1 - 1)) * G::SPLANE;
+      const bool mreal = (m >= 0) & (m < nz);
+      if (act1 && mreal) {
         float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
-        ldv<4>(Bc, c);
-        ldv<4>(A, zm);
-        ldv<4>(C, zp);
-        ldv<4>(Bc + SW, yp);
-        ldv<4>(Bc - SW, ym);
-        ldv<4>(Rp + rrow, rr);
-        const float left = Bc[-1];
-        const float right = Bc[4];
-        if ((y == 0) | (y == ny - 1) | (P == 0) | (P == nz - 1)) {
-          // face rows and planes: the first sweep's ghost is the face value
-#pragma unroll
-          for (int e = 0; e < 4; ++e) {
-            if (y == 0) ym[e] = c[e];
-            if (y == ny - 1) yp[e] = c[e];
-            if (P == 0) zm[e] = c[e];
-            if (P == nz - 1) zp[e] = c[e];
-          }
-        }
-        float out[4];
+        ldv<4>(Pc + prow, c);
+        ldv<4>(Pm + prow, zm);
+        ldv<4>(Pp + prow, zp);
+        ldv<4>(Pc + prow + PW, yp);
+        ldv<4>(Pc + prow - PW, ym);
+        ldv<4>(Pc + rrow, rr);
+        const float left = tof(Pc[prow - 1]);
+        const float right = tof(Pc[prow + 4]);
+        float o[4];
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
           const float xm = e == 0 ? left : c[e - 1];
           const float xp = e == 3 ? right : c[e + 1];
-          out[e] = jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy, cz, omega,
-                             inv_diag);
+          o[e] = tof(cvt<T>(jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy, cz,
+                                      omega, inv_diag)));
         }
-        T* qk = qrow + (long long)(P - k0) * pzl;
-        if (nv >= 4) {
-          stv<T, 4>(qk, out);
-        } else {
+        *reinterpret_cast<float4*>(S1 + srow) = make_float4(o[0], o[1], o[2], o[3]);
+        if (lane == 0 && i0 == 0) S1[srow - 1] = o[0];   // x = -1 <- x = 0
+        if (xhi_in) S1[srow + nv] = pick<4>(o, nv - 1);  // x = nx <- x = nx - 1
+      }
+      if (!rowwarp && mreal) {
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (e < nv) qk[e] = cvt<T>(out[e]);
-        }
-        if (tm) put_row_images<T, 4>(rimg[w], tm, P, xl, nv, out);
-        if ((P == 0) | (P == nz - 1)) {
-#pragma unroll
-          for (int e = 0; e < 4; ++e)
-            if (e < nv) p_ghost_z<T>(L, B, dst, x0 + e, y, P, cvt<T>(out[e]));
+        for (int q = 0; q < NE; ++q) {
+          const int ce = lane + 32 * q;
+          const int er = ce >> 1, ex = (ce & 1) ? i0 + TX : i0 - 1, ey = j0 - 1 + er;
+          if (ce < 2 * NW && ex >= 0 && ex < nx && ey >= 0 && ey < ny) {
+            const int epi = (er + 1) * PW + HX + (ex - i0);
+            const int eri = RS_T + er * PW + HX + (ex - i0);
+            S1[er * SW + 4 + (ex - i0)] = tof(cvt<T>(
+                jac_point(tof(Pc[epi]), tof(Pc[epi - 1]), tof(Pc[epi + 1]), tof(Pc[epi - PW]),
+                          tof(Pc[epi + PW]), tof(Pm[epi]), tof(Pp[epi]), tof(Pc[eri]), cx, cy, cz,
+                          omega, inv_diag)));
+          }
         }
       }
-      if (t2 >= 1) release(sq >= 1 ? sq - 1 : S - 1);  // plane m - 2 (q = t - 1) is done
+      __syncwarp();
+      if (lane == 0) mbar_arrive(smem_u32(&s1bar[(it1 + t) & (NS1 - 1)]));
+    };
+    // second sweep on plane P = k0 - 3 + t from slots u - 3, u - 2, u - 1
+    // (u = it1 + t) and r from the stage of plane P (q = t - 1)
+    auto sweep2 = [&](int t) {
+      const unsigned u = it1 + t;
+      const int P = k0 - 3 + t;
+      const float* A = s1 + (int)((u - 3) & (NS1 - 1)) * G::SPLANE + srow;
+      const float* Bc = s1 + (int)((u - 2) & (NS1 - 1)) * G::SPLANE + srow;
+      const float* C = s1 + (int)((u - 1) & (NS1 - 1)) * G::SPLANE + srow;
+      const T* Rp = ring + (sq >= 1 ? sq - 1 : S - 1) * STAGE_T;
+      float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
+      ldv<4>(Bc, c);
+      ldv<4>(A, zm);
+      ldv<4>(C, zp);
+      ldv<4>(Bc + SW, yp);
+      ldv<4>(Bc - SW, ym);
+      ldv<4>(Rp + rrow, rr);
+      const float left = Bc[-1];
+      const float right = Bc[4];
+      const bool zlo = P == 0, zhi = P == nz - 1;
+      if (yface | zlo | zhi) {
+        // face rows and planes: the first sweep's ghost is the face value
+#pragma unroll
+        for (int e = 0; e < 4; ++e) {
+          if (y == 0) ym[e] = c[e];
+          if (y == ny - 1) yp[e] = c[e];
+          if (zlo) zm[e] = c[e];
+          if (zhi) zp[e] = c[e];
+        }
+      }
+      float out[4];
+#pragma unroll
+      for (int e = 0; e < 4; ++e) {
+        const float xm = e == 0 ? left : c[e - 1];
+        const float xp = e == 3 ? right : c[e + 1];
+        out[e] = jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy, cz, omega,
+                           inv_diag);
+      }
+      T* qk = qrow + (long long)(P - k0) * pzl;
+      if (nv >= 4) {
+        stv<T, 4>(qk, out);
+      } else {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (e < nv) qk[e] = cvt<T>(out[e]);
+      }
+      if (tm) put_row_images<T, 4>(rimg[w], tm, P, xl, nv, out);
+      if (zlo | zhi) {
+#pragma unroll
+        for (int e = 0; e < 4; ++e)
+          if (e < nv) p_ghost_z<T>(L, B, dst, x0 + e, y, P, cvt<T>(out[e]));
+      }
+    };
+    auto advance = [&]() {  // end of an iteration: the stage of plane m - 2 is done
+      release(sq >= 1 ? sq - 1 : S - 1);
       if (++sq == S) {
         sq = 0;
         phq ^= 1u;
       }
-      if (t2 <= nzc + 1 && ++sl == NS1) {
-        sl = 0;
-        phl ^= 1u;
+    };
+    // planes k0 - 2 and k0 - 1 must be there before the first iteration
+    wait_full(sq, phq);
+    wait_full(wrapn<S>(sq + 1), phq ^ (uint32_t)(sq + 1 >= S));
+    // iterations 0 .. 2: first sweep only (the first output plane needs the
+    // first sweep on k0 - 1 .. k0 + 1); every iteration waits for the plane
+    // of two iterations before (also across tiles) to bound the skew
+    for (int t2 = 0; t2 < 3 && !bad; ++t2) {
+      sweep1(t2);
+      if (bad) break;
+      if (it1 + t2 >= 2) wait_s1(it1 + t2 - 2);
+      if (bad) break;
+      if (t2 == 0) {
+        if (++sq == S) {  // no stage is done yet after iteration 0
+          sq = 0;
+          phq ^= 1u;
+        }
+      } else {
+        advance();
+      }
+    }
+    // iterations 3 .. nzc + 1: both sweeps
+    for (int t2 = 3; t2 <= nzc + 1 && !bad; ++t2) {
+      sweep1(t2);
+      if (bad) break;
+      wait_s1(it1 + t2 - 2);
+      if (bad) break;
+      if (act2) sweep2(t2);
+      advance();
+    }
+    // iteration nzc + 2: second sweep on the last plane only
+    if (!bad) {
+      wait_s1(it1 + nzc);
+      if (!bad) {
+        if (act2) sweep2(nzc + 2);
+        advance();
       }
     }
     if (bad) break;
