@@ -462,21 +462,22 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
 // planes.  Warps: TY + 2 row warps, one extras warp, one producer warp.
 // The producer loads, per plane, the p box (x from i0 - HX, rows j0 - 2 ..
 // j0 + TY + 1) and the r box (rows j0 - 1 .. j0 + TY) into an S-stage ring.
-// In iteration t, row warp w (row y = j0 - 1 + w, 4 cells per lane) takes
-// the first sweep on plane m = k0 - 1 + t over x = i0 .. i0 + 127 and the
-// extras warp the two cells x = i0 - 1 and x = i0 + 128 of every row; both
-// store, rounded to the storage type, into slot t of a shared-memory ring
-// of NS1 first-sweep planes (row width 136: x = i0 - 4 at index 0).  Then
-// row warps 1 .. TY take the second sweep on plane m - 2 from slots t - 3 ..
-// t - 1 and r from the stage of plane m - 2, and write it to global memory
-// with its ghost-on-write images.  An mbarrier per slot (count TY + 3) says
-// that every row of a first-sweep plane is written; each iteration waits
-// for the plane of iteration t - 2, which is all the second sweep needs from
-// other warps and bounds the skew: a warp writing slot t may coexist with
-// one reading slot t - 6, so NS1 >= 7; it is 8.  First-sweep values outside the block
-// (walls: p'_ghost = p'_face) come from the face cell: the x images are
-// written into the ring by the face cell's lane, the y and z images are
-// selected in the second sweep of face rows and planes.
+// In iteration t, row warps 1 .. TY first take the second sweep on plane
+// m - 2 (m = k0 - 1 + t) from slots t - 3 .. t - 1 of a shared-memory ring
+// of NS1 first-sweep planes and r from the stage of plane m - 2, and write
+// it to global memory with its ghost-on-write images; then row warp w
+// (row y = j0 - 1 + w, 4 cells per lane) takes the first sweep on plane m
+// over x = i0 .. i0 + 127 and the extras warp the cells x = i0 - 1 and
+// x = i0 + 128 of every row; both store it, rounded to the storage type,
+// into slot t (row width 136: x = i0 - 4 at index 0).  An mbarrier per
+// slot (count TY + 3) says that every row of a first-sweep plane is
+// written; each iteration starts by waiting for the plane of iteration
+// t - 2, which is all the second sweep needs from other warps and bounds
+// the skew: a warp writing slot t may coexist with one reading slot t - 4,
+// so NS1 >= 5; it is 8.  First-sweep values outside the block (walls:
+// p'_ghost = p'_face) come from the face cell: the x images are written
+// into the ring by the face cell's lane, the y and z images are selected
+// in the second sweep of face rows and planes.
 
 template <typename T, int TY>
 struct Ws2Geom {
@@ -668,8 +669,6 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
           }
         }
       }
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&s1bar[(it1 + t) & (NS1 - 1)]));
     };
     // second sweep on plane P = k0 - 3 + t from slots u - 3, u - 2, u - 1
     // (u = it1 + t) and r from the stage of plane P (q = t - 1)
@@ -708,7 +707,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
         out[e] = jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy, cz, omega,
                            inv_diag);
       }
-      T* qk = qrow + (long long)(P - k0) * pzl;
+      T* qk = qrow + (long long)(P - k0) * pzl;  // (P - k0 < zc: 32-bit product)
       if (nv >= 4) {
         stv<T, 4>(qk, out);
       } else {
@@ -723,8 +722,14 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
           if (e < nv) p_ghost_z<T>(L, B, dst, x0 + e, y, P, cvt<T>(out[e]));
       }
     };
-    auto advance = [&]() {  // end of an iteration: the stage of plane m - 2 is done
-      release(sq >= 1 ? sq - 1 : S - 1);
+    // end of iteration t: the first-sweep plane of slot u is written and
+    // (t >= 1) the stage of plane m - 2 is no longer read
+    auto finish = [&](int t, bool first_plane_done, bool stage_done) {
+      __syncwarp();
+      if (lane == 0) {
+        if (first_plane_done) mbar_arrive(smem_u32(&s1bar[(it1 + t) & (NS1 - 1)]));
+        if (stage_done) mbar_arrive(smem_u32(&empty[sq >= 1 ? sq - 1 : S - 1]));
+      }
       if (++sq == S) {
         sq = 0;
         phq ^= 1u;
@@ -733,38 +738,33 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     // planes k0 - 2 and k0 - 1 must be there before the first iteration
     wait_full(sq, phq);
     wait_full(wrapn<S>(sq + 1), phq ^ (uint32_t)(sq + 1 >= S));
-    // iterations 0 .. 2: first sweep only (the first output plane needs the
-    // first sweep on k0 - 1 .. k0 + 1); every iteration waits for the plane
-    // of two iterations before (also across tiles) to bound the skew
+    // Each iteration first waits for the first-sweep plane of two iterations
+    // before (also across tiles: this bounds the skew between warps), takes
+    // the second sweep (iterations 3 ..), then the first (.. nzc + 1).
+    // Iterations 0 .. 2: first sweep only (the first output plane needs the
+    // first sweep on k0 - 1 .. k0 + 1).
     for (int t2 = 0; t2 < 3 && !bad; ++t2) {
-      sweep1(t2);
-      if (bad) break;
       if (it1 + t2 >= 2) wait_s1(it1 + t2 - 2);
       if (bad) break;
-      if (t2 == 0) {
-        if (++sq == S) {  // no stage is done yet after iteration 0
-          sq = 0;
-          phq ^= 1u;
-        }
-      } else {
-        advance();
-      }
+      sweep1(t2);
+      if (bad) break;
+      finish(t2, true, t2 >= 1);
     }
     // iterations 3 .. nzc + 1: both sweeps
     for (int t2 = 3; t2 <= nzc + 1 && !bad; ++t2) {
-      sweep1(t2);
-      if (bad) break;
       wait_s1(it1 + t2 - 2);
       if (bad) break;
       if (act2) sweep2(t2);
-      advance();
+      sweep1(t2);
+      if (bad) break;
+      finish(t2, true, true);
     }
     // iteration nzc + 2: second sweep on the last plane only
     if (!bad) {
       wait_s1(it1 + nzc);
       if (!bad) {
         if (act2) sweep2(nzc + 2);
-        advance();
+        finish(nzc + 2, false, true);
       }
     }
     if (bad) break;
