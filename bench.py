@@ -143,19 +143,26 @@ class ClockSampler:
                 "power_w_max": max((num(r[3]) or 0.0) for r in rows)}
 
 
-def traffic_for(kernel_hash: str, cells: int, config):
-    """DRAM bytes per Jacobi launch from the committed ncu summary, scaled to
-    this launch's cells; None when the kernel source or the variant's tile
-    (kind, vx, ty, zc) differs from the captured one."""
+def profile_record(kernel_hash: str, config):
+    """The committed ncu record of the Jacobi launch (DRAM bytes and warp
+    instructions per cell), or None when the kernel source or the variant's
+    tile (kind, vx, ty, zc) differs from the captured one (the ring depth,
+    the last config entry, does not change which bytes move)."""
     try:
         with open(TRAFFIC_FILE) as f:
             t = json.load(f)
     except Exception:
         return None
-    # the ring depth (last config entry) does not change which bytes move
     if t.get("kernel_sha256") != kernel_hash or list(t.get("config", []))[:4] != list(config)[:4]:
         return None
-    return t["dram_bytes_per_cell"] * cells
+    return t
+
+
+def traffic_for(kernel_hash: str, cells: int, config):
+    """DRAM bytes per Jacobi launch from the committed ncu record, scaled to
+    this launch's cells; None when the record does not apply."""
+    t = profile_record(kernel_hash, config)
+    return None if t is None else t["dram_bytes_per_cell"] * cells
 
 
 def file_hash(paths):
@@ -458,6 +465,22 @@ def run_gpu(a):
                 "sweeps_per_launch": per_launch,
                 "peak_source": "%s hbm_gbs (burst copy)" % peak_kind,
                 "sweep_glups": per_launch * cells / (launch_ms * 1e-3) / 1e9}
+    # the instruction-issue side of the same launch: warp instructions per
+    # cell from the ncu record, against 4 issues per SM cycle at the SM
+    # clock sampled during the timed steps
+    rec = profile_record(file_hash(kernel_sources(jcfg[0][0])), jcfg[0])
+    issue = None
+    clk_summary = clk.summary()
+    if rec is not None and rec.get("warp_instructions_per_cell") and clk_summary.get("sm_mhz"):
+        sms = torch.cuda.get_device_properties(local).multi_processor_count
+        inst = rec["warp_instructions_per_cell"] * cells
+        ach = inst / (launch_ms * 1e-3)
+        pk = 4.0 * sms * clk_summary["sm_mhz"] * 1e6
+        issue = {"achieved": ach, "peak": pk, "unit": "warp instructions/s", "frac": ach / pk,
+                 "instructions_per_launch": inst,
+                 "peak_source": "4 issue slots per SM per cycle x %d SMs x median SM clock %.0f MHz"
+                                % (sms, clk_summary["sm_mhz"])}
+    roofline["issue"] = issue
 
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
@@ -519,7 +542,7 @@ def run_gpu(a):
             "cpu_baseline": cpu,
             "e2e": e2e,
             "gpu_launches": launches,
-            "clocks": clk.summary(),
+            "clocks": clk_summary,
             "check": {"kinetic_energy": ke, "max_abs_u": umax, "max_abs_div": divmax},
             "jacobi_config": jcfg,
             "secondary": secondary,
