@@ -711,6 +711,134 @@ __device__ __forceinline__ void cp_async_n(void* smem, const void* gmem) {
   else cp_async4(smem, gmem);
 }
 
+__device__ __forceinline__ void cp_commit_group() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_wait_group() {
+  asm volatile("cp.async.wait_group %0;" ::"n"(N) : "memory");
+}
+// 4-byte cp.async to a shared-memory byte address.  No memory clobber: the
+// caller orders the copies against its own shared-memory accesses with
+// cp.async.wait_group and barriers (which clobber memory), and a clobber
+// here would pin the caller's per-thread index arrays to local memory.
+__device__ __forceinline__ void cp_async4_s(uint32_t saddr, const void* gmem) {
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(gmem));
+}
+
+// Copies of plane kk of u, v, w (this thread's share) into its ring slot,
+// then one commit group (empty past the last plane, so that "all but the
+// newest D groups" always means the same planes).
+template <int NL, int R, int PL>
+__device__ __forceinline__ void stage_issue(uint32_t ring_s, const int (&soff)[NL],
+                                            const long long (&goff)[NL], const bool (&lok)[NL],
+                                            const float* base, int kk, long long pz, bool live) {
+  if (live) {
+    const uint32_t slot = ring_s + (uint32_t)((kk & (R - 1)) * (3 * PL) * 4);
+#pragma unroll
+    for (int q = 0; q < NL; ++q)
+      if (lok[q]) cp_async4_s(slot + 4u * soff[q], base + goff[q] + (long long)kk * pz);
+  }
+  cp_commit_group();
+}
+
+// FP32 variant of the z-streaming RHS + stage ring: planes of u, v, w are
+// copied into the ring with cp.async two planes ahead of the last one the
+// stencil needs (no registers hold them, no second pass through registers),
+// eight slots so that a slot is rewritten only after every thread has left
+// the planes that read it; the stage-2 input is loaded before the plane's
+// barrier so its latency overlaps the wait.  Same arithmetic (rhs_comp) and
+// results as k_stage_ring.
+template <int ORDER, int TY>
+__global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float a, Set3 xs,
+                                                         float b, Set3 ys, float cdt, Set3 os,
+                                                         float nu) {
+  constexpr int H = ORDER == 2 ? 1 : 2;
+  constexpr int D = 2;  // planes in flight beyond k + H
+  constexpr int SX = 32 + 2 * H, SY = TY + 2 * H, PL = SX * SY;
+  constexpr int R = 8;  // >= 2H + 1 + D and a power of two
+  static_assert(2 * H + 1 + D <= R, "ring too small");
+  constexpr int NT = 32 * TY;
+  constexpr int NL = (3 * PL + NT - 1) / NT;
+  __shared__ float ring[R * 3 * PL];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, 32, TY, zc);
+  const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
+  const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const float* base = reinterpret_cast<const float*>(L.base);
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, 32, TY, zc, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int g = L.ghost;
+    const int py = B.py;
+    const long long pz = B.pz;
+    const int k1 = min(k0 + zc, nz);
+    int soff[NL];
+    long long goff[NL];
+    bool lok[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int idx = tid + q * NT;
+      const int c = idx / PL, rem = idx % PL;
+      const int xx = rem % SX, yy = rem / SX;
+      const int i = i0 - H + xx, j = j0 - H + yy;
+      lok[q] = idx < 3 * PL && i <= nx + g - 1 && j <= ny + g - 1;
+      soff[q] = c * PL + rem;
+      goff[q] = lok[q] ? B.org[ys.a[c]] + (long long)j * py + i : 0;
+    }
+    const int kmax = nz + g - 1;
+    const int klast = k1 - 1 + H;  // last plane the tile reads
+    // one commit group per plane, empty groups past the last plane, so that
+    // "all but the newest D groups" always means "up to plane k + H"
+    const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
+    for (int kk = k0 - H; kk <= k0 + H + D - 1; ++kk)
+      stage_issue<NL, R, PL>(ring_s, soff, goff, lok, base, kk, pz, kk <= klast && kk <= kmax);
+    const int i = i0 + tx, j = j0 + ty;
+    const bool mine = i < nx && j < ny;
+    const bool wall[3] = {B.bc[1] == BC_WALL && i == nx - 1, B.bc[3] == BC_WALL && j == ny - 1,
+                          B.bc[5] == BC_WALL};
+    const long long o0 = (long long)j * py + i;
+    const float* X[3] = {base + B.org[xs.a[0]] + o0, base + B.org[xs.a[1]] + o0,
+                         base + B.org[xs.a[2]] + o0};
+    float* O[3] = {reinterpret_cast<float*>(L.base) + B.org[os.a[0]] + o0,
+                   reinterpret_cast<float*>(L.base) + B.org[os.a[1]] + o0,
+                   reinterpret_cast<float*>(L.base) + B.org[os.a[2]] + o0};
+    const RingFld<SX, PL, R> f[3] = {{ring, i0 - H, j0 - H}, {ring + PL, i0 - H, j0 - H},
+                                     {ring + 2 * PL, i0 - H, j0 - H}};
+    for (int k = k0; k < k1; ++k) {
+      {  // plane k + H + D; its slot was last read D + 1 planes ago or more
+        const int kk = k + H + D;
+        stage_issue<NL, R, PL>(ring_s, soff, goff, lok, base, kk, pz, kk <= klast && kk <= kmax);
+      }
+      const long long o = (long long)k * pz;
+      float xv[3] = {0.f, 0.f, 0.f};
+      if (a != 0.f && mine) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) xv[c] = __ldg(X[c] + o);
+      }
+      cp_wait_group<D>();  // this thread's copies of planes .. k + H have landed
+      __syncthreads();
+      if (mine) {
+        float F[3];
+        F[0] = rhs_comp<RingFld<SX, PL, R>, ORDER, 0>(f, i, j, k, ih, ih2, nu);
+        F[1] = rhs_comp<RingFld<SX, PL, R>, ORDER, 1>(f, i, j, k, ih, ih2, nu);
+        F[2] = rhs_comp<RingFld<SX, PL, R>, ORDER, 2>(f, i, j, k, ih, ih2, nu);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const bool wf = wall[c] && (c != 2 || k == nz - 1);
+          float v = b * f[c](i, j, k) + cdt * F[c];
+          if (a != 0.f) v += a * xv[c];
+          O[c][o] = wf ? 0.f : v;
+        }
+      }
+    }
+    cp_wait_group<0>();  // (only empty groups can be pending) before the next tile's copies
+    __syncthreads();
+  }
+}
+
 template <typename T, int VX, int TY, int S>
 struct AsyncGeom {
   static constexpr int TX = 32 * VX;
@@ -1350,9 +1478,15 @@ template <typename T, int ORDER, int TY>
 static void run_stage_ring(const Launch& L, int zc, float a, Set3 xs, float b, Set3 ys, float cdt,
                            Set3 os, float nu) {
   const long long tiles = count_tiles(L, 32, TY, zc);
-  auto kern = k_stage_ring<T, ORDER, TY>;
-  static const int occ = occupancy(kern, 32 * TY);
-  kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
+  if constexpr (sizeof(T) == 4) {
+    auto kern = k_stage_async<ORDER, TY>;
+    static const int occ = occupancy(kern, 32 * TY);
+    kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
+  } else {
+    auto kern = k_stage_ring<T, ORDER, TY>;
+    static const int occ = occupancy(kern, 32 * TY);
+    kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
+  }
 }
 
 cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float a,
