@@ -518,7 +518,6 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
   unsigned long long* full = reinterpret_cast<unsigned long long*>(s1 + NS1 * G::SPLANE);
   unsigned long long* empty = full + S;
   unsigned long long* s1bar = empty + S;
-  __shared__ RowImage<T> rimg[NW][4];
   const int lane = threadIdx.x, w = threadIdx.y;
   if (smem_u32(smem) & 127u) {
     if (w == 0 && lane == 0) atomicOr(L.err_flag, 4);
@@ -593,14 +592,6 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     // extras warp: cell c < 2 NW is row c / 2, x = i0 - 1 (even c) or i0 + 128;
     // lane l takes cells l and l + 32
     constexpr int NE = (2 * NW + 31) / 32;
-    unsigned tm = 0;
-    if (rowwarp) {
-      __syncwarp();
-      unsigned rm = 0;
-      if (lane == 0 && out_row) rm = row_images<T>(L, B, dst, i0, TX, y, rimg[w]);
-      tm = thread_images<4>(__shfl_sync(0xffffffffu, rm, 0), lane, x0, nx);
-      __syncwarp();
-    }
     const long long pzl = B.pz;
     T* qrow = reinterpret_cast<T*>(L.base) + B.org[dst] + (long long)y * B.py + x0 +
               (long long)k0 * pzl;  // plane k0 of the output row
@@ -615,6 +606,8 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     const bool act1 = yreal && nv > 0;                 // this lane has first-sweep cells
     const bool act2 = out_row && nv > 0;               // ... and second-sweep outputs
     const bool yface = (y == 0) | (y == ny - 1);
+    const bool xface = (lane == 0 && i0 == 0) | xhi_in;  // lanes with an x image
+    const int pyl = B.py;
     auto wait_full = [&](int st, uint32_t ph) {
       if (!mbar_wait_split(smem_u32(&full[st]), ph)) bad = true;
     };
@@ -707,19 +700,27 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
         out[e] = jac_point(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy, cz, omega,
                            inv_diag);
       }
-      T* qk = qrow + (long long)(P - k0) * pzl;  // (P - k0 < zc: 32-bit product)
-      if (nv >= 4) {
-        stv<T, 4>(qk, out);
-      } else {
+      T* qk = qrow + (long long)(P - k0) * pzl;
+      auto put = [&](T* q) {
+        if (nv >= 4) {
+          stv<T, 4>(q, out);
+        } else {
 #pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (e < nv) qk[e] = cvt<T>(out[e]);
-      }
-      if (tm) put_row_images<T, 4>(rimg[w], tm, P, xl, nv, out);
-      if (zlo | zhi) {
-#pragma unroll
-        for (int e = 0; e < 4; ++e)
-          if (e < nv) p_ghost_z<T>(L, B, dst, x0 + e, y, P, cvt<T>(out[e]));
+          for (int e = 0; e < 4; ++e)
+            if (e < nv) q[e] = cvt<T>(out[e]);
+        }
+      };
+      put(qk);
+      // ghost-on-write at the walls (this kernel runs only when all six
+      // faces are walls): the first ghost layer takes the face value, in
+      // the same block, next to the face cell
+      if (__builtin_expect(xface | yface | zlo | zhi, 0)) {
+        if (lane == 0 && i0 == 0) qk[-1] = cvt<T>(out[0]);
+        if (xhi_in) qk[nv] = cvt<T>(pick<4>(out, nv - 1));
+        if (y == 0) put(qk - pyl);
+        if (y == ny - 1) put(qk + pyl);
+        if (zlo) put(qk - pzl);
+        if (zhi) put(qk + pzl);
       }
     };
     // end of iteration t: the first-sweep plane of slot u is written and
