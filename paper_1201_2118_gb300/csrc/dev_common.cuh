@@ -71,6 +71,21 @@ __device__ __forceinline__ T* wptr(const Launch& L, const BlockDev& B, int arr) 
   return reinterpret_cast<T*>(L.base) + B.org[arr];
 }
 
+// ------------------------------------------------------- Jacobi update
+//
+// One weighted Jacobi update of the 7-point operator, p' = p + w((N p - r)
+// / diag - p), N p = sum over axes of (p_- + p_+) / h^2, with every rounding
+// spelled out, so that every sweep kernel (scalar or packed pairs) computes
+// the same bits: nb = fma(zm + zp, cz, fma(ym + yp, cy, (xm + xp) cx)),
+// p' = fma(w, fma(nb - r, 1/diag, -p), p).
+__device__ __forceinline__ float jacobi_update(float c, float xm, float xp, float ym, float yp,
+                                               float zm, float zp, float r, float cx, float cy,
+                                               float cz, float omega, float inv_diag) {
+  const float nb = __fmaf_rn(__fadd_rn(zm, zp), cz,
+                             __fmaf_rn(__fadd_rn(ym, yp), cy, __fmul_rn(__fadd_rn(xm, xp), cx)));
+  return __fmaf_rn(omega, __fmaf_rn(__fsub_rn(nb, r), inv_diag, -c), c);
+}
+
 // ------------------------------------------------------- ghost-on-write
 //
 // A Jacobi sweep writes each new face value of p also into the first ghost

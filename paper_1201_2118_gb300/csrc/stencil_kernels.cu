@@ -638,8 +638,8 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi(Launch L, int zc, int src, i
       for (int e = 0; e < VX; ++e) {
         const float xm = e == 0 ? left : c[e - 1];
         const float xp = e == VX - 1 ? right : c[e + 1];
-        const float nb = (xm + xp) * cx + (dn[e] + up[e]) * cy + (m[e] + q[e]) * cz;
-        out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+        out[e] = jacobi_update(c[e], xm, xp, dn[e], up[e], m[e], q[e], rr[e], cx, cy, cz,
+                                 omega, inv_diag);
       }
       if (j < ny) {
         T* qrow = Q + (long long)k * pz + row;
@@ -929,8 +929,8 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_async(Launch L, int zc, int 
       for (int e = 0; e < VX; ++e) {
         const float xm = e == 0 ? left : c[e - 1];
         const float xp = e == VX - 1 ? right : c[e + 1];
-        const float nb = (xm + xp) * cx + (dn[e] + up[e]) * cy + (zm[e] + zp[e]) * cz;
-        out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+        out[e] = jacobi_update(c[e], xm, xp, dn[e], up[e], zm[e], zp[e], rr[e], cx, cy, cz,
+                                 omega, inv_diag);
       }
       const int k = k0 + q - 1;
       if (out_row) {
@@ -1057,15 +1057,14 @@ __global__ void __launch_bounds__(32 * (TY + 4)) k_jacobi2(Launch L, int zc, int
       for (int e = 0; e < 4; ++e) {
         const float xm = e == 0 ? left : cc[e - 1];
         const float xp = e == 3 ? right : cc[e + 1];
-        const float nb = (xm + xp) * cx + (dd[e] + uu[e]) * cy + (mm[e] + qq[e]) * cz;
-        o[e] = cc[e] + omega * ((nb - rv[e]) * inv_diag - cc[e]);
+        o[e] = jacobi_update(cc[e], xm, xp, dd[e], uu[e], mm[e], qq[e], rv[e], cx, cy, cz,
+                                 omega, inv_diag);
       }
       *reinterpret_cast<float4*>(out + c0) = make_float4(o[0], o[1], o[2], o[3]);
       if (lane == 0 || lane == 31) {  // ring column x = i0 - 1 (index 3) or i0 + TX (132)
         const int c = lane == 0 ? 3 : 132;
-        const float nb = (pc[c - 1] + pc[c + 1]) * cx + (pc[c - RW] + pc[c + RW]) * cy +
-                         (pm[c] + pp[c]) * cz;
-        out[c] = pc[c] + omega * ((nb - rr[c]) * inv_diag - pc[c]);
+        out[c] = jacobi_update(pc[c], pc[c - 1], pc[c + 1], pc[c - RW], pc[c + RW], pm[c], pp[c],
+                               rr[c], cx, cy, cz, omega, inv_diag);
       }
     };
 
@@ -1128,8 +1127,8 @@ __global__ void __launch_bounds__(32 * (TY + 4)) k_jacobi2(Launch L, int zc, int
         for (int e = 0; e < 4; ++e) {
           const float xm = e == 0 ? left : cc[e - 1];
           const float xp = e == 3 ? right : cc[e + 1];
-          const float nb = (xm + xp) * cx + (dd[e] + uu[e]) * cy + (mm[e] + qq[e]) * cz;
-          o[e] = cc[e] + omega * ((nb - rv[e]) * inv_diag - cc[e]);
+          o[e] = jacobi_update(cc[e], xm, xp, dd[e], uu[e], mm[e], qq[e], rv[e], cx, cy, cz,
+                                   omega, inv_diag);
         }
         T* qo = Q + (long long)m * pz + (long long)j * py + x;
         stv<T, 4>(qo, o);
@@ -1196,8 +1195,8 @@ __global__ void __launch_bounds__(32 * TY * TZ) k_jacobi_direct(Launch L, int sr
     for (int e = 0; e < VX; ++e) {
       const float xm = e == 0 ? left : c[e - 1];
       const float xp = e == VX - 1 ? right : c[e + 1];
-      const float nb = (xm + xp) * cx + (ym[e] + yp[e]) * cy + (zm[e] + zp[e]) * cz;
-      out[e] = c[e] + omega * ((nb - rr[e]) * inv_diag - c[e]);
+      out[e] = jacobi_update(c[e], xm, xp, ym[e], yp[e], zm[e], zp[e], rr[e], cx, cy, cz,
+                               omega, inv_diag);
     }
     T* qrow = wptr<T>(L, B, dst) + o;
     if (i + VX <= nx) {
