@@ -86,6 +86,73 @@ __device__ __forceinline__ float jacobi_update(float c, float xm, float xp, floa
   return __fmaf_rn(omega, __fmaf_rn(__fsub_rn(nb, r), inv_diag, -c), c);
 }
 
+// Packed FP32 pairs (two floats in a 64-bit register) for the sm_100-family
+// f32x2 instructions: one issue slot computes the same IEEE round-to-nearest
+// operation on two cells.
+__device__ __forceinline__ unsigned long long pk2(float a, float b) {
+  unsigned long long r;
+  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
+  return r;
+}
+__device__ __forceinline__ void unpk2(unsigned long long v, float& a, float& b) {
+  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
+}
+__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
+  unsigned long long r;
+  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
+  return r;
+}
+__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
+                                                   unsigned long long c) {
+  unsigned long long r;
+  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
+  return r;
+}
+
+// jacobi_update on two cells at once, the same operations in the same order
+// (so the same bits): nb = fma(zm+zp, cz, fma(ym+yp, cy, (xm+xp) cx)),
+// out = fma(omega, fma(nb - r, inv_diag, -c), c).
+struct Jac2 {
+  unsigned long long cx, cy, cz, om, inv, m1;
+  __device__ __forceinline__ Jac2(float cx_, float cy_, float cz_, float om_, float inv_)
+      : cx(pk2(cx_, cx_)), cy(pk2(cy_, cy_)), cz(pk2(cz_, cz_)), om(pk2(om_, om_)),
+        inv(pk2(inv_, inv_)), m1(pk2(-1.f, -1.f)) {}
+  __device__ __forceinline__ unsigned long long operator()(
+      unsigned long long c, unsigned long long xm, unsigned long long xp, unsigned long long ym,
+      unsigned long long yp, unsigned long long zm, unsigned long long zp,
+      unsigned long long r) const {
+    const unsigned long long nb =
+        fma2(add2(zm, zp), cz, fma2(add2(ym, yp), cy, mul2(add2(xm, xp), cx)));
+    return fma2(om, fma2(sub2(nb, r), inv, mul2(c, m1)), c);
+  }
+};
+
+// four cells of a row (VX = 4) with their x neighbours left/right
+__device__ __forceinline__ void jac_row4(const Jac2& J, const float (&c)[4], float left,
+                                         float right, const float (&ym)[4], const float (&yp)[4],
+                                         const float (&zm)[4], const float (&zp)[4],
+                                         const float (&r)[4], float (&out)[4]) {
+  const unsigned long long c01 = pk2(c[0], c[1]), c23 = pk2(c[2], c[3]);
+  const unsigned long long o01 =
+      J(c01, pk2(left, c[0]), pk2(c[1], c[2]), pk2(ym[0], ym[1]), pk2(yp[0], yp[1]),
+        pk2(zm[0], zm[1]), pk2(zp[0], zp[1]), pk2(r[0], r[1]));
+  const unsigned long long o23 =
+      J(c23, pk2(c[1], c[2]), pk2(c[3], right), pk2(ym[2], ym[3]), pk2(yp[2], yp[3]),
+        pk2(zm[2], zm[3]), pk2(zp[2], zp[3]), pk2(r[2], r[3]));
+  unpk2(o01, out[0], out[1]);
+  unpk2(o23, out[2], out[3]);
+}
+
 // ------------------------------------------------------- ghost-on-write
 //
 // A Jacobi sweep writes each new face value of p also into the first ghost

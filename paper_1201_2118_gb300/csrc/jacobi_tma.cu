@@ -139,6 +139,7 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
   }
   __syncthreads();
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
+  const Jac2 J2(cx, cy, cz, omega, inv_diag);
   const int g = L.ghost;
   constexpr int xo = kAlignBytes / (int)sizeof(T);
   uint32_t parity = 0;
@@ -221,12 +222,16 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
       if (lane == 0) left = tof(Pq[row - 1]);
       if (lane == 31) right = tof(Pq[row + VX]);
       float out[VX];
+      if constexpr (VX == 4) {
+        jac_row4(J2, c, left, right, dn, up, m, zp, rr, out);
+      } else {
 #pragma unroll
-      for (int e = 0; e < VX; ++e) {
-        const float xm = e == 0 ? left : c[e - 1];
-        const float xp = e == VX - 1 ? right : c[e + 1];
-        out[e] = jacobi_update(c[e], xm, xp, dn[e], up[e], m[e], zp[e], rr[e], cx, cy, cz,
+        for (int e = 0; e < VX; ++e) {
+          const float xm = e == 0 ? left : c[e - 1];
+          const float xp = e == VX - 1 ? right : c[e + 1];
+          out[e] = jacobi_update(c[e], xm, xp, dn[e], up[e], m[e], zp[e], rr[e], cx, cy, cz,
                                  omega, inv_diag);
+        }
       }
       qrow += pzl;
       if (row_ok) {
@@ -497,73 +502,6 @@ __device__ __forceinline__ float jac_point(float c, float xm, float xp, float ym
                                            float zp, float r, float cx, float cy, float cz,
                                            float omega, float inv_diag) {
   return jacobi_update(c, xm, xp, ym, yp, zm, zp, r, cx, cy, cz, omega, inv_diag);
-}
-
-// Packed FP32 pairs (two floats in a 64-bit register) for the sm_100-family
-// f32x2 instructions: one issue slot computes the same IEEE round-to-nearest
-// operation on two cells.
-__device__ __forceinline__ unsigned long long pk2(float a, float b) {
-  unsigned long long r;
-  asm("mov.b64 %0, {%1, %2};" : "=l"(r) : "f"(a), "f"(b));
-  return r;
-}
-__device__ __forceinline__ void unpk2(unsigned long long v, float& a, float& b) {
-  asm("mov.b64 {%0, %1}, %2;" : "=f"(a), "=f"(b) : "l"(v));
-}
-__device__ __forceinline__ unsigned long long add2(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("add.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long sub2(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("sub.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long mul2(unsigned long long a, unsigned long long b) {
-  unsigned long long r;
-  asm("mul.rn.f32x2 %0, %1, %2;" : "=l"(r) : "l"(a), "l"(b));
-  return r;
-}
-__device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigned long long b,
-                                                   unsigned long long c) {
-  unsigned long long r;
-  asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(r) : "l"(a), "l"(b), "l"(c));
-  return r;
-}
-
-// jacobi_update on two cells at once, the same operations in the same order
-// (so the same bits): nb = fma(zm+zp, cz, fma(ym+yp, cy, (xm+xp) cx)),
-// out = fma(omega, fma(nb - r, inv_diag, -c), c).
-struct Jac2 {
-  unsigned long long cx, cy, cz, om, inv, m1;
-  __device__ __forceinline__ Jac2(float cx_, float cy_, float cz_, float om_, float inv_)
-      : cx(pk2(cx_, cx_)), cy(pk2(cy_, cy_)), cz(pk2(cz_, cz_)), om(pk2(om_, om_)),
-        inv(pk2(inv_, inv_)), m1(pk2(-1.f, -1.f)) {}
-  __device__ __forceinline__ unsigned long long operator()(
-      unsigned long long c, unsigned long long xm, unsigned long long xp, unsigned long long ym,
-      unsigned long long yp, unsigned long long zm, unsigned long long zp,
-      unsigned long long r) const {
-    const unsigned long long nb =
-        fma2(add2(zm, zp), cz, fma2(add2(ym, yp), cy, mul2(add2(xm, xp), cx)));
-    return fma2(om, fma2(sub2(nb, r), inv, mul2(c, m1)), c);
-  }
-};
-
-// four cells of a row (VX = 4) with their x neighbours left/right
-__device__ __forceinline__ void jac_row4(const Jac2& J, const float (&c)[4], float left,
-                                         float right, const float (&ym)[4], const float (&yp)[4],
-                                         const float (&zm)[4], const float (&zp)[4],
-                                         const float (&r)[4], float (&out)[4]) {
-  const unsigned long long c01 = pk2(c[0], c[1]), c23 = pk2(c[2], c[3]);
-  const unsigned long long o01 =
-      J(c01, pk2(left, c[0]), pk2(c[1], c[2]), pk2(ym[0], ym[1]), pk2(yp[0], yp[1]),
-        pk2(zm[0], zm[1]), pk2(zp[0], zp[1]), pk2(r[0], r[1]));
-  const unsigned long long o23 =
-      J(c23, pk2(c[1], c[2]), pk2(c[3], right), pk2(ym[2], ym[3]), pk2(yp[2], yp[3]),
-        pk2(zm[2], zm[3]), pk2(zp[2], zp[3]), pk2(r[2], r[3]));
-  unpk2(o01, out[0], out[1]);
-  unpk2(o23, out[2], out[3]);
 }
 
 // x mod n for 0 <= x < 2n
