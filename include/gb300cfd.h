@@ -250,7 +250,8 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
  * ty in {4,8}; used on single-block grids with nx % 128 == 0 and
  * ny % ty == 0, other grids and odd sweep counts take single sweeps),
  * kind 7 the warp-specialised TMA sweep (a producer warp fills an S-stage
- * ring, ty consumer warps; vx 4, ty in {4,8,16}, stages in {6,8}),
+ * ring, ty consumer warps; vx 4 with ty in {4,8,16} and stages in {6,8}, or
+ * vx 2 (64-wide tiles, for narrow blocks) with ty in {8,16} and 6 stages),
  * kind 9 two sweeps per launch in the warp-specialised TMA form (temporal
  * blocking; vx 4 with (ty, stages) in {(16,6), (16,7), (8,5), (8,6)}; used on
  * single-block grids whose six faces are walls, odd sweep counts and other

@@ -846,8 +846,10 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
                      (((c.ty == 4 || c.ty == 8) && (c.stages == 5 || c.stages == 6)) ||
                       (c.ty == 2 && c.stages == 6));
     const bool ok5 = c.kind == 5 && (c.ty == 4 || c.ty == 8);
-    const bool ok7 = c.kind == 7 && c.vx == 4 && (c.ty == 4 || c.ty == 8 || c.ty == 16) &&
-                     (c.stages == 6 || c.stages == 8);
+    const bool ok7 = c.kind == 7 &&
+                     ((c.vx == 4 && (c.ty == 4 || c.ty == 8 || c.ty == 16) &&
+                       (c.stages == 6 || c.stages == 8)) ||
+                      (c.vx == 2 && (c.ty == 8 || c.ty == 16) && c.stages == 6));
     const bool ok9 = c.kind == 9 && c.vx == 4 &&
                      ((c.ty == 16 && (c.stages == 6 || c.stages == 7)) ||
                       (c.ty == 8 && (c.stages == 5 || c.stages == 6)));
@@ -904,6 +906,9 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   for (int zc : {16, 32, 64, 128})
     for (int ty : {4, 8, 16})
       for (int st : {6, 8}) cands.push_back({7, 4, ty, zc, st});
+  if (g->nblocks > 1)  // narrow blocks: 64-wide tiles waste fewer lanes
+    for (int zc : {32, 64, 128})
+      for (int ty : {8, 16}) cands.push_back({7, 2, ty, zc, 6});
   if (g->nblocks == 1)
     for (int zc : {16, 32, 64, 128})
       for (int ty : {4, 8}) cands.push_back({5, 4, ty, zc, 0});

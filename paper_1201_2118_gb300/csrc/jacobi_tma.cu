@@ -914,6 +914,13 @@ cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* m
                               int src_slot, int dst, float omega) {
   const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
   cudaError_t e = cudaErrorInvalidValue;
+  if (c.kind == 7 && c.vx == 2) {  // 64-wide tiles for narrow blocks
+    CFD_DISPATCH_T(L.dtype, {
+      if (c.ty == 8) e = run_ws<T, 2, 8, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+      else e = run_ws<T, 2, 16, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    });
+    return e;
+  }
   if (c.kind == 7) {
     CFD_DISPATCH_T(L.dtype, {
       if (c.ty == 4 && c.stages == 8) e = run_ws<T, 4, 4, 8>(L, c, maps_dev, src_slot, dst, omega, inv_diag);

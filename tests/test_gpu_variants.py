@@ -25,6 +25,7 @@ JACOBI_CONFIGS = [
     (3, 4, 4, 32, 5), (3, 4, 8, 16, 6), (3, 4, 2, 32, 6), (3, 4, 4, 64, 6),
     (5, 4, 4, 16, 0), (5, 4, 8, 32, 0),
     (7, 4, 4, 16, 6), (7, 4, 8, 32, 8), (7, 4, 16, 128, 6), (7, 4, 4, 7, 8),
+    (7, 2, 8, 32, 6), (7, 2, 16, 9, 6),
 ]
 SIZES = [(45, 37, 21), (150, 77, 40)]
 
@@ -68,7 +69,7 @@ def test_jacobi_variant_matches_oracle(cfg, dims, bc):
 
 @pytest.mark.parametrize("cfg", [(1, 4, 8, 32, 4), (1, 2, 8, 16, 4), (0, 1, 8, 16, 4),
                                  (2, 4, 4, 2, 0), (2, 1, 8, 1, 0), (3, 4, 4, 32, 5),
-                                 (7, 4, 8, 32, 6)], ids=cfg_id)
+                                 (7, 4, 8, 32, 6), (7, 2, 8, 32, 6), (7, 2, 16, 64, 6)], ids=cfg_id)
 def test_jacobi_variant_on_block_set(cfg):
     from oracle import Oracle
     from paper_1201_2118_gb300 import Grid, P, R, WU, WV, WW, mask
