@@ -176,12 +176,11 @@ def file_hash(paths):
 
 # --------------------------------------------------------------- oracle leg
 
-def oracle_sample(seconds_hint=False):
-    """One RK2 step of the same cavity scheme on a 256^3 grid by the FP64
-    oracle on all host cores (bounded sample of the 512^3 workload; the
-    per-cell work is identical)."""
-    from oracle import Oracle
-    n = 256
+def _oracle_step_time(n, threads):
+    """Seconds for one RK2 step of the n^3 cavity by the FP64 oracle on the
+    given number of host threads (0: all)."""
+    from oracle import Oracle, set_threads
+    used = set_threads(threads)
     h = (1.0 / n,) * 3
     o = Oracle((n, n, n), ghost=1, h=h, bc="cavity", nu=1e-3)
     u, p = o.state(workloads.ldc_noise(n, seed=1))
@@ -190,10 +189,29 @@ def oracle_sample(seconds_hint=False):
     t0 = time.perf_counter()
     o.rk2_step(u, p, dt, 50, scratch)
     el = time.perf_counter() - t0
-    cores = int(os.environ.get("OMP_NUM_THREADS", os.cpu_count() or 1))
-    return {"value": n ** 3 / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
-            "sample": "1 RK2 step (2 x 50 Jacobi sweeps) of the 256^3 lid-driven cavity, "
-                      "FP64 C oracle, OpenMP over z; %.1f s" % el}
+    set_threads(0)
+    return el, used
+
+
+def oracle_sample(seconds_hint=False, detail=True):
+    """One RK2 step of the same cavity scheme on a 256^3 grid by the FP64
+    oracle on all host cores (bounded sample of the 512^3 workload; the
+    per-cell work is identical); with detail, also one 128^3 step on one
+    thread and on all threads."""
+    n = 256
+    el, cores = _oracle_step_time(n, 0)
+    out = {"value": n ** 3 / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
+           "sample": "1 RK2 step (2 x 50 Jacobi sweeps) of the 256^3 lid-driven cavity, "
+                     "FP64 C oracle, OpenMP over z; %.1f s" % el}
+    if detail:
+        m = 128
+        e1, _ = _oracle_step_time(m, 1)
+        ea, ca = _oracle_step_time(m, 0)
+        out["scaling_128"] = {"one_thread": m ** 3 / e1 / 1e9, "all_threads": m ** 3 / ea / 1e9,
+                              "threads": ca, "unit": UNIT,
+                              "sample": "1 RK2 step of the 128^3 cavity: %.1f s on 1 thread, "
+                                        "%.2f s on %d" % (e1, ea, ca)}
+    return out
 
 
 def run_reference(a):
@@ -204,10 +222,10 @@ def run_reference(a):
     cfg = workloads.WORKLOADS[name]
     steps = []
     base = None
-    for _ in range(a.warmup if a.warmup < 1 else 0):
-        pass
+    # the warm-up steps are not run: the oracle has no caches, graphs or
+    # compilation to warm, and each step is a seconds-long sample
     for i in range(a.steps):
-        s = oracle_sample()
+        s = oracle_sample(detail=False)
         steps.append(s["value"])
         base = s
     value = statistics.median(steps)
@@ -464,7 +482,10 @@ def run_gpu(a):
                 "bytes_per_launch": bytes_per_launch, "launch_ms": launch_ms,
                 "sweeps_per_launch": per_launch,
                 "peak_source": "%s hbm_gbs (burst copy)" % peak_kind,
-                "sweep_glups": per_launch * cells / (launch_ms * 1e-3) / 1e9}
+                "sweep_glups": per_launch * cells / (launch_ms * 1e-3) / 1e9,
+                # single-sweep bytes per sweep time: what the sweeps would move
+                # without temporal blocking (equals achieved for one sweep per launch)
+                "effective_gbs": per_launch * bytes_per_launch / (launch_ms * 1e-3) / 1e9}
     # the instruction-issue side of the same launch: warp instructions per
     # cell from the ncu record, against 4 issues per SM cycle at the SM
     # clock sampled during the timed steps

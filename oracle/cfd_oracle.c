@@ -17,6 +17,9 @@
  *    zero and p takes a zero-gradient ghost.
  */
 #include "cfd_oracle.h"
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #include <math.h>
 #include <stddef.h>
@@ -331,4 +334,16 @@ double ora_residual(const ora_grid* G, const double* p, const double* r) {
   free(part);
   free(lp);
   return sqrt(s);
+}
+
+int ora_set_threads(int n) {
+#ifdef _OPENMP
+  static int dflt = 0;
+  if (dflt == 0) dflt = omp_get_max_threads();
+  omp_set_num_threads(n > 0 ? n : dflt);
+  return omp_get_max_threads();
+#else
+  (void)n;
+  return 1;
+#endif
 }

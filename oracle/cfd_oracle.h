@@ -82,6 +82,10 @@ void ora_reduce(const ora_grid* G, const double* const u[3], double* ke, double*
 /* ||L p - r||_2 over interior cells (p ghosts filled). */
 double ora_residual(const ora_grid* G, const double* p, const double* r);
 
+/* Host threads used by the OpenMP loops (results do not depend on it);
+ * n <= 0 restores the default.  Returns the count in effect. */
+int ora_set_threads(int n);
+
 /* The 7-point operator itself: lp = L p on the interior (test helper). */
 void ora_laplace_p(const ora_grid* G, const double* p, double* lp);
 

@@ -84,6 +84,8 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = None
+            lib.ora_set_threads.argtypes = [ctypes.c_int]
+            lib.ora_set_threads.restype = ctypes.c_int
             _lib = lib
     return _lib
 
@@ -288,3 +290,9 @@ def exact_poisson_periodic(r_int: np.ndarray, h) -> np.ndarray:
     ph = rh / lam
     ph[0, 0, 0] = 0.0
     return np.real(np.fft.ifftn(ph))
+
+
+def set_threads(n: int) -> int:
+    """Host threads of the oracle's OpenMP loops (n <= 0: the default);
+    returns the count in effect.  Results do not depend on it."""
+    return int(_load().ora_set_threads(int(n)))
