@@ -157,6 +157,16 @@ cfd_status cfd_ghost_fill(cfd_grid* g, unsigned mask);
 cfd_status cfd_stage(cfd_grid* g, double a, int x_set, double b, int y_set, double c,
                      int out_set);
 
+/* Residual-controlled variant of cfd_pressure_solve (an extension: the
+ * paper's step uses a fixed sweep count): R = (D W)/c_dt, then weighted
+ * Jacobi sweeps on P in chunks of check_every until ||L P - R||_2 <=
+ * rtol ||R||_2 (checked before the first chunk and after each) or
+ * max_iters sweeps.  iters_done and residual (either may be NULL) receive
+ * the sweeps taken and the last ||L P - R||_2.  Synchronises once per
+ * chunk; the residual is taken per cell in float-float and summed in FP64. */
+cfd_status cfd_pressure_solve_converged(cfd_grid* g, double c_dt, double rtol, int max_iters,
+                                        int check_every, int* iters_done, double* residual);
+
 /* F(U) into WU, WV, WW (cfd_stage(g, 0, -, 0, U, 1, W)). */
 cfd_status cfd_rhs_eval(cfd_grid* g);
 
@@ -190,7 +200,8 @@ cfd_status cfd_step(cfd_grid* g, double dt, int n);
 cfd_status cfd_reduce(cfd_grid* g, int set, double* kinetic_energy, double* max_abs_u,
                       double* max_abs_div);
 
-/* ||L P - R||_2 over all interior cells, FP64.  Synchronises. */
+/* ||L P - R||_2 over all interior cells (per cell in float-float, summed in
+ * FP64).  Synchronises. */
 cfd_status cfd_residual(cfd_grid* g, double* residual);
 
 /* ------------------------------------------------------------- adjoint */

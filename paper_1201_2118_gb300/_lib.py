@@ -36,6 +36,8 @@ SIGNATURES = {
     "cfd_stage": [c_void_p, c_double, c_int, c_double, c_int, c_double, c_int],
     "cfd_rhs_eval": [c_void_p],
     "cfd_pressure_solve": [c_void_p, c_double, c_int, P(c_double)],
+    "cfd_pressure_solve_converged": [c_void_p, c_double, c_double, c_int, c_int, P(c_int),
+                                     P(c_double)],
     "cfd_project": [c_void_p, c_double, c_int],
     "cfd_jacobi": [c_void_p, c_int],
     "cfd_stats": [c_void_p, P(c_ll)],

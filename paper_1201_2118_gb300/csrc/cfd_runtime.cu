@@ -820,6 +820,35 @@ cfd_status cfd_pressure_solve(cfd_grid* g, double c_dt, int iters, double* resid
   return join_out(g);
 }
 
+cfd_status cfd_pressure_solve_converged(cfd_grid* g, double c_dt, double rtol, int max_iters,
+                                        int check_every, int* iters_done, double* residual) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (!(c_dt > 0.0) || !(rtol >= 0.0) || max_iters < 0 || check_every < 1)
+    return fail(CFD_EINVAL, "need c_dt > 0, rtol >= 0, max_iters >= 0, check_every >= 1");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_solve(g, c_dt, 0)) != CFD_OK) return s;  // R = (D W)/c_dt
+  double out[4];
+  if ((s = run_reduce(g, 2, 0, out)) != CFD_OK) return s;
+  if (out[3] != 0.0) return fail(CFD_ENONFINITE, "right-hand side is not finite");
+  const double target = rtol * std::sqrt(out[0]);
+  int done = 0;
+  double res = 0.0;
+  if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
+  res = std::sqrt(out[0]);
+  while (!(res <= target) && done < max_iters) {
+    const int n = std::min(check_every, max_iters - done);
+    if ((s = enq_sweeps(g, n)) != CFD_OK) return s;
+    done += n;
+    if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
+    res = std::sqrt(out[0]);
+    if (out[3] != 0.0) return fail(CFD_ENONFINITE, "residual is not finite");
+  }
+  if (iters_done) *iters_done = done;
+  if (residual) *residual = res;
+  return join_out(g);
+}
+
 cfd_status cfd_jacobi(cfd_grid* g, int iters) {
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;

@@ -1299,7 +1299,8 @@ __device__ __forceinline__ void block_reduce4(double (&v)[4], double (*sh)[4]) {
 // mode 0: sum |u|^2, max |u_d|, max |D u| and the non-finite count of a
 // velocity set; the per-cell work is float-float, each thread's column sum
 // (at most zc cells) is added to an FP64 accumulator.  mode 1: sum of
-// (L p - r)^2 in FP64.
+// (L p - r)^2, the residual per cell in float-float, the squares summed in
+// FP64.  mode 2: sum of r^2 in FP64.
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, Set3 set,
                                                     int p_arr, int r_arr, double* partials) {
@@ -1344,19 +1345,37 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
         if (ff_gt(div, dmax)) dmax = div;
       }
       acc[0] += ff_to_double(col);
-    } else {
+    } else if (mode == 1) {
+      // e = L p - r per cell in float-float (the sums and differences of
+      // the FP32 values exact, the products by 1/h^2 with their rounding
+      // error kept), e^2 accumulated in FP64
       const T* P = base + B.org[p_arr] + o0;
       const T* Rr = base + B.org[r_arr] + o0;
+      const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
+      const long long step[3] = {1, py, pz};
       for (int q = 0; q < kn; ++q) {
         const long long o = (long long)q * pz;
-        const double pc = ldf<T>(P + o);
-        const double lp =
-            ((double)ldf<T>(P + o + 1) - 2.0 * pc + (double)ldf<T>(P + o - 1)) * (double)L.ih2[0] +
-            ((double)ldf<T>(P + o + py) - 2.0 * pc + (double)ldf<T>(P + o - py)) * (double)L.ih2[1] +
-            ((double)ldf<T>(P + o + pz) - 2.0 * pc + (double)ldf<T>(P + o - pz)) * (double)L.ih2[2];
-        const double e = lp - (double)ldf<T>(Rr + o);
+        const float pc = ldf<T>(P + o);
+        FF lp = {0.f, 0.f};
+#pragma unroll
+        for (int d = 0; d < 3; ++d) {
+          const FF nbs = ff_two_sum(ldf<T>(P + o + step[d]), ldf<T>(P + o - step[d]));
+          const FF sec = ff_add(nbs, FF{-2.f * pc, 0.f});  // 2 pc is exact
+          FF t = ff_two_prod(sec.hi, ih2[d]);
+          t.lo = __fmaf_rn(sec.lo, ih2[d], t.lo);
+          lp = d == 0 ? ff_fast_two_sum(t.hi, t.lo) : ff_add(lp, t);
+        }
+        const double e = ff_to_double(ff_add(lp, FF{-ldf<T>(Rr + o), 0.f}));
         acc[0] += e * e;
         if (!isfinite(e)) acc[3] += 1.0;
+      }
+    } else {
+      // sum of r^2 (the norm the converged solve measures against)
+      const T* Rr = base + B.org[r_arr] + o0;
+      for (int q = 0; q < kn; ++q) {
+        const double rv = ldf<T>(Rr + (long long)q * pz);
+        acc[0] += rv * rv;
+        if (!isfinite(rv)) acc[3] += 1.0;
       }
     }
   }

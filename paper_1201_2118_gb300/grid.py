@@ -163,6 +163,16 @@ class Grid:
              ctypes.byref(r) if residual else None)
         return r.value if residual else None
 
+    def pressure_solve_converged(self, c_dt: float, rtol: float, max_iters: int,
+                                 check_every: int = 10):
+        """Sweeps until ||L P - R|| <= rtol ||R|| (checked every check_every
+        sweeps) or max_iters; returns (sweeps taken, final residual)."""
+        n = ctypes.c_int()
+        r = c_double()
+        call("cfd_pressure_solve_converged", self.handle, float(c_dt), float(rtol), int(max_iters),
+             int(check_every), ctypes.byref(n), ctypes.byref(r))
+        return n.value, r.value
+
     def jacobi(self, iters: int):
         call("cfd_jacobi", self.handle, int(iters))
 

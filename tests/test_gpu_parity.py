@@ -121,6 +121,69 @@ def test_pressure_solve(bc, iters):
     assert res == pytest.approx(o.residual(p, r), rel=1e-4)
 
 
+@pytest.mark.parametrize("cfg", [(0, 4, 4, 32, 4), (1, 4, 16, 16, 4), (9, 4, 16, 16, 6)])
+def test_converged_pressure_solve(cfg):
+    """Residual-controlled sweeps stop at the first check (every 6 sweeps)
+    where ||L p - r|| <= rtol ||r||; the oracle, run in the same chunks,
+    stops at the same check (or one chunk away when FP32 rounding puts a
+    check right at the threshold), the result matches the oracle after
+    the same number of sweeps, and the reported residual is the oracle's."""
+    from paper_1201_2118_gb300 import P, WU, WV, WW, mask
+    bc = "cavity" if cfg[0] == 9 else "periodic"
+    fl = rand_fields(RAGGED, 17)
+    o, grid, u, p = make_pair(RAGGED, bc=bc, fields=fl)
+    grid.set_kernel_config(jacobi=cfg)
+    w = rounded(rand_fields(RAGGED, 18))
+    if bc == "cavity":  # no flux through the walls: D w has zero mean (solvable)
+        w["u"][:, :, -1] = 0.0
+        w["v"][:, -1, :] = 0.0
+        w["w"][-1, :, :] = 0.0
+    for k, a in enumerate((WU, WV, WW)):
+        grid.interior(a).copy_(grid.torch.from_numpy(w["uvw"[k]]).float().cuda())
+    grid.ghost_fill(mask(WU, WV, WW))
+    wo = [o.ghost_fill(o.embed(w["uvw"[k]]), k) for k in range(3)]
+    c_dt, rtol, chunk, cap = 0.037, 0.2, 6, 600
+    iters, res = grid.pressure_solve_converged(c_dt, rtol, cap, chunk)
+    r = o.divergence(wo, c_dt)
+    target = rtol * np.sqrt(np.sum(o.interior(r) ** 2))
+    ref_iters, hist = 0, [o.residual(p, r)]
+    p_at = {0: p.copy()}
+    while hist[-1] > target and ref_iters < cap:
+        o.jacobi(p, r, chunk)
+        ref_iters += chunk
+        hist.append(o.residual(p, r))
+        p_at[ref_iters] = p.copy()
+    assert iters % chunk == 0 and 0 < iters < cap
+    assert abs(iters - ref_iters) <= chunk
+    if iters not in p_at:
+        o.jacobi(p, r, iters - ref_iters)
+        p_at[iters] = p.copy()
+    assert rel_err(grid.download(P), o.interior(p_at[iters])) < 1e-4
+    assert res == pytest.approx(o.residual(p_at[iters], r), rel=1e-3)
+    assert res <= target * (1 + 1e-3)
+    grid.check()
+
+
+def test_converged_pressure_solve_cap_equals_fixed_sweeps():
+    """rtol 0 runs exactly max_iters sweeps: the same bits as
+    cfd_pressure_solve with that sweep count."""
+    from paper_1201_2118_gb300 import P, WU, WV, WW, mask
+    res = []
+    for conv in (False, True):
+        o, grid, u, p = make_pair(RAGGED, bc="periodic", fields=rand_fields(RAGGED, 19))
+        w = rounded(rand_fields(RAGGED, 20))
+        for k, a in enumerate((WU, WV, WW)):
+            grid.interior(a).copy_(grid.torch.from_numpy(w["uvw"[k]]).float().cuda())
+        grid.ghost_fill(mask(WU, WV, WW))
+        if conv:
+            n, _ = grid.pressure_solve_converged(0.05, 0.0, 14, 4)
+            assert n == 14
+        else:
+            grid.pressure_solve(0.05, 14)
+        res.append(grid.download(P))
+    np.testing.assert_array_equal(res[0], res[1])
+
+
 @pytest.mark.parametrize("bc", ["periodic", "cavity"])
 def test_project(bc):
     from paper_1201_2118_gb300 import U1, V1, W1, WU, WV, WW, SET_U1, mask
