@@ -8,6 +8,10 @@
  *  - Advective form (u . grad) u with central differences; the transverse
  *    velocity at a face point is the 4-point (order 2) or 4x4-point cubic
  *    (order 4) interpolation of the neighbouring faces.
+ *  - Or (order 2) the conservative form div(u u_c): around the point of u_c
+ *    the flux of c-momentum through the side normal to d is the product of
+ *    u_c and u_d, each the mean of its two nearest values on that side
+ *    (Eq. 2 makes the two forms agree for the continuous field).
  *  - Viscous term: 3-point (order 2) or 5-point (order 4) Laplacian per axis.
  *  - Pressure: 7-point Poisson operator L = D G, weighted Jacobi sweeps.
  *  - Time: Heun RK2; each stage is projected: w = stage value,
@@ -102,11 +106,34 @@ static double interp(const ora_grid* G, const double* fd, int c, int d, const in
   return s;
 }
 
-/* F_c = -sum_d vel_d * d(f_c)/dx_d + nu * sum_d d2(f_c)/dx_d^2 at point p. */
+/* Flux of c-momentum in direction d through the side of the control volume
+ * of f_c that lies between the points q and q + e_d of f_c (for d = c: the
+ * cell centre between them; otherwise the cell edge).  There f_c is the mean
+ * of f_c(q) and f_c(q + e_d), and f_d the mean of f_d(q) and f_d(q + e_c). */
+static double flux_cd(const ora_grid* G, const double* const f[3], int c, int d, const int q[3]) {
+  const double fc = 0.5 * (val(G, f[c], q, d, 0, d, 0) + val(G, f[c], q, d, 1, d, 0));
+  const double fd = 0.5 * (val(G, f[d], q, c, 0, c, 0) + val(G, f[d], q, c, 1, c, 0));
+  return fc * fd;
+}
+
+/* F_c = -sum_d vel_d * d(f_c)/dx_d + nu * sum_d d2(f_c)/dx_d^2 at point p,
+ * or, in the flux form, F_c = -sum_d (flux_cd(p) - flux_cd(p - e_d)) / h_d
+ * + nu * sum_d d2(f_c)/dx_d^2. */
 static double rhs_point(const ora_grid* G, const double* const f[3], int c, const int p[3]) {
   const double* fc = f[c];
   const double f0 = fc[at3(G, p)];
   double adv = 0.0, lap = 0.0;
+  if (G->form == ORA_FLUX) {
+    for (int d = 0; d < 3; ++d) {
+      const double h = G->h[d];
+      const double p1 = val(G, fc, p, d, 1, d, 0), m1 = val(G, fc, p, d, -1, d, 0);
+      int pm[3] = {p[0], p[1], p[2]};
+      pm[d] -= 1;
+      adv += (flux_cd(G, f, c, d, p) - flux_cd(G, f, c, d, pm)) / h;
+      lap += (p1 - 2.0 * f0 + m1) / (h * h);
+    }
+    return -adv + G->nu * lap;
+  }
   for (int d = 0; d < 3; ++d) {
     const double h = G->h[d];
     const double p1 = val(G, fc, p, d, 1, d, 0), m1 = val(G, fc, p, d, -1, d, 0);

@@ -36,14 +36,22 @@ typedef struct {
   double nu;         /* kinematic viscosity */
   double omega;      /* Jacobi weight */
   int order;         /* 2 or 4 (4 needs g = 2) */
+  int form;          /* advection term: ORA_ADVECTIVE or ORA_FLUX (order 2) */
 } ora_grid;
+
+/* Advection term of the momentum equation (Sec. 4.1, Eq. 1): the advective
+ * form (u . grad) u_c, or, using div u = 0 (Eq. 2), the conservative form
+ * div(u u_c) as face-flux differences.  The adjoint functions below
+ * linearise the advective form only. */
+enum { ORA_ADVECTIVE = 0, ORA_FLUX = 1 };
 
 /* Ghost fill of one field (kind ORA_U..ORA_P), axis passes x, y, z over the
  * full extent of the other two axes, so a later pass wins on edges/corners. */
 void ora_ghost_fill(const ora_grid* G, double* f, int kind);
 
-/* F_c(u) = -(u . grad) u_c + nu * lap u_c for c = u, v, w at every interior
- * point of each component.  Inputs need filled ghosts. */
+/* F_c(u) = -(u . grad) u_c + nu * lap u_c (form ORA_ADVECTIVE) or
+ * F_c(u) = -div(u u_c) + nu * lap u_c (form ORA_FLUX) for c = u, v, w at
+ * every interior point of each component.  Inputs need filled ghosts. */
 void ora_rhs(const ora_grid* G, const double* u, const double* v, const double* w,
              double* fu, double* fv, double* fw);
 

@@ -24,6 +24,7 @@ _lock = threading.Lock()
 _lib = None
 
 PERIODIC, WALL = 0, 1
+FORMS = {"advective": 0, "flux": 1}
 
 
 def build(force: bool = False) -> str:
@@ -43,7 +44,8 @@ def build(force: bool = False) -> str:
 class _Grid(ctypes.Structure):
     _fields_ = [("n", ctypes.c_int * 3), ("g", ctypes.c_int), ("h", ctypes.c_double * 3),
                 ("bc", ctypes.c_int * 6), ("wall", (ctypes.c_double * 3) * 6),
-                ("nu", ctypes.c_double), ("omega", ctypes.c_double), ("order", ctypes.c_int)]
+                ("nu", ctypes.c_double), ("omega", ctypes.c_double), ("order", ctypes.c_int),
+                ("form", ctypes.c_int)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -115,8 +117,13 @@ class Oracle:
     """One block of the FP64 scheme with its boundary table and parameters."""
 
     def __init__(self, dims, ghost=1, h=(1.0, 1.0, 1.0), bc="periodic", nu=0.0, omega=1.0,
-                 order=2, lid=1.0):
+                 order=2, lid=1.0, form="advective"):
+        if form not in FORMS:
+            raise ValueError(f"form must be one of {sorted(FORMS)}")
+        if form == "flux" and int(order) != 2:
+            raise ValueError("the flux form is order 2")
         self.lib = _load()
+        self.form = form
         self.dims = tuple(int(d) for d in dims)
         self.g = int(ghost)
         faces = bc_faces(bc, lid) if isinstance(bc, str) else list(bc)
@@ -129,6 +136,7 @@ class Oracle:
             gr.bc[f] = kind
             gr.wall[f][:] = tuple(float(x) for x in vel)
         gr.nu, gr.omega, gr.order = float(nu), float(omega), int(order)
+        gr.form = FORMS[form]
         self._g = gr
         self.h = tuple(float(x) for x in h)
         self.shape = tuple(d + 2 * self.g for d in self.dims[::-1])
@@ -226,7 +234,12 @@ class Oracle:
         self.lib.ora_ghost_fold(self._G(), _ptr(f), int(kind))
         return f
 
+    def _adjoint_form(self):
+        if self.form != "advective":
+            raise ValueError("the adjoint linearises the advective form only")
+
     def adj_stage(self, a, xbar, b, y, c, ybar, outbar):
+        self._adjoint_form()
         nb = ctypes.c_double(0.0)
         xs = _p3(xbar) if xbar is not None else (_D * 3)()
         self.lib.ora_adj_stage(self._G(), float(a), xs, float(b), _p3(y), float(c), _p3(ybar),
@@ -246,6 +259,7 @@ class Oracle:
 
     def adj_rk2_step(self, un, u1, dt, iters, ubar, pbar, scratch=None):
         """One adjoint step in place on ubar, pbar; returns dL/dnu of it."""
+        self._adjoint_form()
         if scratch is None:
             scratch = [self.zeros() for _ in range(11)]
         nb = ctypes.c_double(0.0)

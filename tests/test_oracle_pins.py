@@ -179,6 +179,113 @@ def test_rhs_converges_at_design_order(order, rate):
     assert 0.7 * rate < r1 < 1.3 * rate, (e, r1, r2)
 
 
+# ------------------------------------------------ conservative (flux) form
+
+def test_flux_form_exact_for_linear_velocity():
+    """div(u u_c) of a linear field u = A x + b is tr(A) u_c + sum_d u_d A[c, d].
+    The side means of a linear field are exact, their product is a quadratic
+    along d and its central difference about the point is exact."""
+    rng = np.random.default_rng(24)
+    A, b = _linear_field(rng)
+    o = Oracle((6, 5, 7), ghost=1, h=H3, nu=0.0, form="flux")
+    comps = "uvw"
+    f = [fill_fn(o, comps[c], lambda x, y, z, c=c: A[c, 0] * x + A[c, 1] * y + A[c, 2] * z + b[c])
+         for c in range(3)]
+    F = o.rhs(*f)
+    for c in range(3):
+        z, y, x = coords_ext(o.dims, 1, o.h, comps[c])
+        vel = [A[d, 0] * x + A[d, 1] * y + A[d, 2] * z + b[d] for d in range(3)]
+        exact = -(np.trace(A) * vel[c] + sum(vel[d] * A[c, d] for d in range(3)))
+        np.testing.assert_allclose(o.interior(F[c]), o.interior(np.broadcast_to(exact, o.shape)),
+                                   rtol=0, atol=1e-12)
+
+
+def _periodic_random_velocity(o, seed):
+    rng = np.random.default_rng(seed)
+    n = o.dims[::-1]
+    return [o.ghost_fill(o.embed(rng.standard_normal(n)), c) for c in range(3)]
+
+
+def test_flux_form_conserves_momentum_on_periodic_grid():
+    """The flux differences telescope: on a periodic grid the advection term
+    sums to zero over each component, for any velocity field."""
+    o = Oracle((7, 6, 5), ghost=1, h=H3, nu=0.0, form="flux")
+    u = _periodic_random_velocity(o, 25)
+    F = o.rhs(*u)
+    for c in range(3):
+        scale = np.abs(o.interior(F[c])).sum()
+        assert abs(o.interior(F[c]).sum()) < 1e-13 * scale
+    # the advective form does not conserve momentum for such a field
+    oa = Oracle((7, 6, 5), ghost=1, h=H3, nu=0.0)
+    Fa = oa.rhs(*u)
+    assert abs(oa.interior(Fa[0]).sum()) > 1e-3 * np.abs(oa.interior(Fa[0])).sum()
+
+
+def test_flux_form_energy_identity():
+    """Summation by parts on a periodic grid: sum_c sum_p u_c A_c equals
+    sum_c sum_p u_c^2 / 2 * (D u(p) + D u(p + e_c)) / 2, with A_c the
+    flux-form advection term and D u the cell-centre divergence.  Every
+    direction enters through its own divergence term, so a dropped or
+    misplaced flux breaks the equality."""
+    o = Oracle((7, 6, 5), ghost=1, h=H3, nu=0.0, form="flux")
+    u = _periodic_random_velocity(o, 26)
+    F = o.rhs(*u)
+    D = o.interior(o.divergence(u))
+    lhs = sum((o.interior(u[c]) * -o.interior(F[c])).sum() for c in range(3))
+    rhs = 0.0
+    for c in range(3):
+        ax = 2 - c  # numpy axis of direction c in (z, y, x) order
+        Dm = 0.5 * (D + np.roll(D, -1, axis=ax))
+        rhs += (0.5 * o.interior(u[c]) ** 2 * Dm).sum()
+    assert abs(lhs - rhs) < 1e-12 * abs(rhs)
+    assert abs(rhs) > 1.0
+
+
+def test_flux_form_conserves_energy_of_div_free_field():
+    """With D u = 0 the identity above makes the advection term do no work:
+    sum_c sum_p u_c A_c = 0 (kinetic-energy conservation)."""
+    dims = (12, 10, 8)
+    fl = workloads.random_div_free(dims, H3, seed=4)
+    o = Oracle(dims, ghost=1, h=H3, nu=0.0, form="flux")
+    u, _ = o.state(fl)
+    F = o.rhs(*u)
+    work = sum((o.interior(u[c]) * o.interior(F[c])).sum() for c in range(3))
+    scale = sum(np.abs(o.interior(u[c]) * o.interior(F[c])).sum() for c in range(3))
+    assert abs(work) < 1e-13 * scale
+
+
+def _tg_rhs_error_flux(n):
+    nu = 0.05
+    h = (2 * math.pi / n, 2 * math.pi / n, 2 * math.pi / 4)
+    o = Oracle((n, n, 4), ghost=1, h=h, nu=nu, form="flux")
+    tg = workloads.taylor_green((n, n, 4), h=h)
+    u, _ = o.state(tg)
+    F = o.rhs(*u)
+    _, y, x = workloads.point_coords((n, n, 4), h, "u")
+    err = np.abs(o.interior(F[0]) - (-0.5 * np.sin(2 * x) - 2 * nu * np.sin(x) * np.cos(y))).max()
+    _, y, x = workloads.point_coords((n, n, 4), h, "v")
+    err = max(err, np.abs(o.interior(F[1]) -
+                          (-0.5 * np.sin(2 * y) + 2 * nu * np.cos(x) * np.sin(y))).max())
+    assert np.abs(o.interior(F[2])).max() == 0.0
+    return err
+
+
+def test_flux_form_converges_at_second_order():
+    """Taylor-Green is divergence-free, so div(u u) = (u.grad)u there and the
+    flux-form F approaches the same exact right-hand side at order 2."""
+    e = [_tg_rhs_error_flux(n) for n in (16, 32, 64)]
+    r1, r2 = e[0] / e[1], e[1] / e[2]
+    assert 3.2 < r2 < 5.0 and 2.8 < r1 < 5.2, (e, r1, r2)
+
+
+def test_flux_form_rejects_order4_and_adjoint():
+    with pytest.raises(ValueError):
+        Oracle((4, 4, 4), ghost=2, order=4, form="flux")
+    o = Oracle((4, 4, 4), form="flux")
+    with pytest.raises(ValueError):
+        o.adj_rk2_step(None, None, 0.1, 1, None, None)
+
+
 # --------------------------------------------------------- pressure solve
 
 def test_divergence_of_linear_field_is_trace():
