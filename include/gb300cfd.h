@@ -75,6 +75,12 @@ typedef enum { CFD_F32 = 0, CFD_BF16 = 1, CFD_F16 = 2 } cfd_dtype;
  * boundary conditions, internal ones copied from neighbours. */
 typedef enum { CFD_BC_PERIODIC = 0, CFD_BC_WALL = 1 } cfd_bc;
 
+/* Form of the advection term of the momentum equation (Sec. 4.1, Eq. 1). */
+typedef enum {
+  CFD_ADVECTIVE = 0,  /* (u . grad) u_c, central differences (default) */
+  CFD_FLUX = 1        /* div(u u_c), the conservative form (order 2) */
+} cfd_advection;
+
 /* Array ids.  State: U, V, W (velocity) and P (pressure, also the Jacobi
  * warm start).  Work arrays: WU..WW (provisional stage velocity), U1..W1
  * (stage-1 velocity), P2 (Jacobi ping-pong), R (Poisson right-hand side).
@@ -142,6 +148,20 @@ cfd_status cfd_set_bc(cfd_grid* g, int face, int kind, const double wall_velocit
  * solve (>= 0), Jacobi weight omega in (0, 2), stencil order 2 or 4
  * (order 4 needs ghost 2). */
 cfd_status cfd_set_params(cfd_grid* g, double nu, int jacobi_iters, double omega, int order);
+
+/* Form of the advection term used by cfd_rhs_eval, cfd_stage and the steps.
+ * CFD_ADVECTIVE (default): -(u . grad) u_c with the transverse velocity
+ * interpolated to the point of u_c.  CFD_FLUX: -div(u u_c), which Eq. 2
+ * (div u = 0) makes equal to the advective term for the continuous field:
+ * around the point of u_c the flux through the side normal to axis d is
+ * the product of the means of u_c and u_d nearest that side, and the term is
+ * the flux difference over h_d.  Its sum over a periodic grid vanishes for
+ * every field (momentum conservation) and, for a discretely divergence-free
+ * field, so does the work sum u_c A_c (energy conservation).  CFD_FLUX is
+ * order 2 only (CFD_EINVAL with order 4, here or in cfd_set_params later);
+ * the adjoint linearises CFD_ADVECTIVE only (CFD_EUNSUPPORTED).  Invalidates
+ * captured step graphs. */
+cfd_status cfd_set_advection(cfd_grid* g, int form);
 
 /* ------------------------------------------------------ steps of the path */
 

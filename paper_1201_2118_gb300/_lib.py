@@ -32,6 +32,7 @@ SIGNATURES = {
     "cfd_block_info": [c_void_p, c_int, P(c_int), P(c_int), P(c_int)],
     "cfd_set_bc": [c_void_p, c_int, c_int, P(c_double)],
     "cfd_set_params": [c_void_p, c_double, c_int, c_double, c_int],
+    "cfd_set_advection": [c_void_p, c_int],
     "cfd_ghost_fill": [c_void_p, c_uint],
     "cfd_stage": [c_void_p, c_double, c_int, c_double, c_int, c_double, c_int],
     "cfd_rhs_eval": [c_void_p],

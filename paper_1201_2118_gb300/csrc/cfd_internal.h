@@ -114,7 +114,13 @@ cudaError_t launch_adj_stage(const Launch& L, const AdjSet& lam, const Ptr3& y, 
 
 cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr,
                          const long long* d_prefix, long long total);
-cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float a,
+// Momentum-advection scheme of the RHS + stage kernels: the advective form
+// of order 2 or 4 (the value is the order) or the order-2 conservative
+// (flux) form.  The stencil reach is scheme_halo() cells per axis.
+enum : int { kSchemeAdv2 = 2, kSchemeFlux2 = 3, kSchemeAdv4 = 4 };
+__host__ __device__ constexpr int scheme_halo(int scheme) { return scheme == kSchemeAdv4 ? 2 : 1; }
+
+cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int scheme, float a,
                          const int* xset, float b, const int* yset, float cdt, const int* oset,
                          float nu);
 cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* wset,

@@ -57,6 +57,7 @@ struct cfd_grid {
   double wall[6][3] = {};
   double nu = 0.0, omega = 1.0;
   int iters = 50, order = 2;
+  int form = CFD_ADVECTIVE;  // advection term (cfd_set_advection)
 
   cudaStream_t user = nullptr, own = nullptr;
   cudaEvent_t ev_in = nullptr, ev_out = nullptr;
@@ -354,7 +355,8 @@ unsigned set_mask(int s) {
 
 cfd_status enq_stage(cfd_grid* g, double a, int xs, double b, int ys, double c, int os) {
   return each_launch(g, [&](const Launch& L) {
-    return launch_stage(L, g->scfg, g->order, (float)a, a != 0.0 ? kSets[xs] : nullptr, (float)b,
+    const int scheme = g->form == CFD_FLUX ? kSchemeFlux2 : g->order;
+    return launch_stage(L, g->scfg, scheme, (float)a, a != 0.0 ? kSets[xs] : nullptr, (float)b,
                         kSets[ys], (float)c, kSets[os], (float)g->nu);
   });
 }
@@ -473,6 +475,8 @@ cfd_status adjoint_supported(cfd_grid* g) {
   if (g->nblocks != 1 || g->dtype != CFD_F32 || g->order != 2 || g->g < 2)
     return fail(CFD_EUNSUPPORTED,
                 "the adjoint needs one FP32 block, order 2 and ghost width 2");
+  if (g->form != CFD_ADVECTIVE)
+    return fail(CFD_EUNSUPPORTED, "the adjoint linearises the advective form only");
   for (int f = 0; f < 6; ++f)
     if (g->bc[f] != CFD_BC_PERIODIC) return fail(CFD_EUNSUPPORTED, "the adjoint needs periodic faces");
   return CFD_OK;
@@ -541,8 +545,8 @@ std::string tune_key(cfd_grid* g) {
   unsigned long long hsh = 1469598103934665603ull;  // FNV-1a of the block dims
   for (char ch : dims) hsh = (hsh ^ (unsigned char)ch) * 1099511628211ull;
   char buf[160];
-  snprintf(buf, sizeof buf, "%s|dt%d|g%d|o%d|nb%d|%016llx", name.c_str(), g->dtype, g->g, g->order,
-           g->nblocks, hsh);
+  snprintf(buf, sizeof buf, "%s|dt%d|g%d|o%d%s|nb%d|%016llx", name.c_str(), g->dtype, g->g, g->order,
+           g->form == CFD_FLUX ? "f" : "", g->nblocks, hsh);
   return buf;
 }
 
@@ -774,10 +778,21 @@ cfd_status cfd_set_params(cfd_grid* g, double nu, int jacobi_iters, double omega
   if (!(omega > 0.0 && omega < 2.0)) return fail(CFD_EINVAL, "omega must be in (0, 2)");
   if (order != 2 && order != 4) return fail(CFD_EINVAL, "order must be 2 or 4");
   if (order == 4 && g->g < 2) return fail(CFD_EINVAL, "order 4 needs ghost width 2");
+  if (order == 4 && g->form == CFD_FLUX) return fail(CFD_EINVAL, "the flux form is order 2");
   g->nu = nu;
   g->iters = jacobi_iters;
   g->omega = omega;
   g->order = order;
+  invalidate_graph(g);
+  return CFD_OK;
+}
+
+cfd_status cfd_set_advection(cfd_grid* g, int form) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (form != CFD_ADVECTIVE && form != CFD_FLUX)
+    return fail(CFD_EINVAL, "form must be CFD_ADVECTIVE or CFD_FLUX");
+  if (form == CFD_FLUX && g->order != 2) return fail(CFD_EINVAL, "the flux form is order 2");
+  g->form = form;
   invalidate_graph(g);
   return CFD_OK;
 }

@@ -119,7 +119,14 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, GhostArrays ga, const l
 
 // ------------------------------------------------------- RHS + stage combine
 
-template <typename F, int ORDER, int C>
+// F_C = nu lap u_C - A_C at the point (i, j, k) of component C.  Advective
+// form (kSchemeAdv2/4): A_C = sum_d vel_d * du_C/dx_d with the transverse
+// velocity interpolated to the point.  Conservative form (kSchemeFlux2,
+// Eq. 1 rewritten with Eq. 2): A_C = sum_d (E_d(p) - E_d(p - e_d)) / h_d,
+// E_d(q) the C-momentum flux through the side between the points q and
+// q + e_d, the product of the means (u_C(q) + u_C(q + e_d)) / 2 and
+// (u_d(q) + u_d(q + e_C)) / 2.
+template <typename F, int SCH, int C>
 __device__ __forceinline__ float rhs_comp(const F (&f)[3], int i, int j, int k,
                                           const float (&ih)[3], const float (&ih2)[3],
                                           float nu) {
@@ -130,44 +137,64 @@ __device__ __forceinline__ float rhs_comp(const F (&f)[3], int i, int j, int k,
     return f[comp](q[0], q[1], q[2]);
   };
   const float f0 = f[C](i, j, k);
-  float adv = 0.f, lap = 0.f;
+  if constexpr (SCH == kSchemeFlux2) {
+    float adv = 0.f, lap = 0.f;
 #pragma unroll
-  for (int d = 0; d < 3; ++d) {
-    const float p1 = at(C, d, 1, d, 0), m1 = at(C, d, -1, d, 0);
-    float deriv, second;
-    if (ORDER == 2) {
-      deriv = (p1 - m1) * (0.5f * ih[d]);
-      second = (p1 - 2.f * f0 + m1) * ih2[d];
-    } else {
-      const float p2 = at(C, d, 2, d, 0), m2 = at(C, d, -2, d, 0);
-      deriv = (8.f * (p1 - m1) - (p2 - m2)) * (ih[d] * (1.f / 12.f));
-      second = (16.f * (p1 + m1) - 30.f * f0 - (p2 + m2)) * (ih2[d] * (1.f / 12.f));
-    }
-    float vel;
-    if (d == C) {
-      vel = f0;
-    } else if (ORDER == 2) {
-      vel = 0.25f * ((at(d, C, 0, d, -1) + at(d, C, 1, d, -1)) + (at(d, C, 0, d, 0) + at(d, C, 1, d, 0)));
-    } else {
-      const float w4[4] = {-1.f / 16.f, 9.f / 16.f, 9.f / 16.f, -1.f / 16.f};
-      vel = 0.f;
-#pragma unroll
-      for (int ad = 0; ad < 4; ++ad) {
-        float s = 0.f;
-#pragma unroll
-        for (int ac = 0; ac < 4; ++ac) s += w4[ac] * at(d, C, ac - 1, d, ad - 2);
-        vel += w4[ad] * s;
+    for (int d = 0; d < 3; ++d) {
+      const float p1 = at(C, d, 1, d, 0), m1 = at(C, d, -1, d, 0);
+      const float ch = f0 + p1, cl = m1 + f0;  // 2 x the u_C side means
+      float dh, dl;                            // 2 x the u_d side means
+      if (d == C) {
+        dh = ch;
+        dl = cl;
+      } else {
+        dh = at(d, C, 0, d, 0) + at(d, C, 1, d, 0);
+        dl = at(d, C, 0, d, -1) + at(d, C, 1, d, -1);
       }
+      adv += (ch * dh - cl * dl) * (0.25f * ih[d]);
+      lap += (p1 - 2.f * f0 + m1) * ih2[d];
     }
-    adv += vel * deriv;
-    lap += second;
+    return nu * lap - adv;
+  } else {
+    float adv = 0.f, lap = 0.f;
+#pragma unroll
+    for (int d = 0; d < 3; ++d) {
+      const float p1 = at(C, d, 1, d, 0), m1 = at(C, d, -1, d, 0);
+      float deriv, second;
+      if (SCH == kSchemeAdv2) {
+        deriv = (p1 - m1) * (0.5f * ih[d]);
+        second = (p1 - 2.f * f0 + m1) * ih2[d];
+      } else {
+        const float p2 = at(C, d, 2, d, 0), m2 = at(C, d, -2, d, 0);
+        deriv = (8.f * (p1 - m1) - (p2 - m2)) * (ih[d] * (1.f / 12.f));
+        second = (16.f * (p1 + m1) - 30.f * f0 - (p2 + m2)) * (ih2[d] * (1.f / 12.f));
+      }
+      float vel;
+      if (d == C) {
+        vel = f0;
+      } else if (SCH == kSchemeAdv2) {
+        vel = 0.25f * ((at(d, C, 0, d, -1) + at(d, C, 1, d, -1)) + (at(d, C, 0, d, 0) + at(d, C, 1, d, 0)));
+      } else {
+        const float w4[4] = {-1.f / 16.f, 9.f / 16.f, 9.f / 16.f, -1.f / 16.f};
+        vel = 0.f;
+#pragma unroll
+        for (int ad = 0; ad < 4; ++ad) {
+          float s = 0.f;
+#pragma unroll
+          for (int ac = 0; ac < 4; ++ac) s += w4[ac] * at(d, C, ac - 1, d, ad - 2);
+          vel += w4[ad] * s;
+        }
+      }
+      adv += vel * deriv;
+      lap += second;
+    }
+    return nu * lap - adv;
   }
-  return nu * lap - adv;
 }
 
 struct Set3 { int a[3]; };
 
-template <typename T, int ORDER, int TY>
+template <typename T, int SCH, int TY>
 __global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Set3 xs, float b,
                                                    Set3 ys, float cdt, Set3 os, float nu) {
   const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
@@ -187,9 +214,9 @@ __global__ void __launch_bounds__(32 * TY) k_stage(Launch L, int zc, float a, Se
                           B.bc[3] == BC_WALL && j == B.n[1] - 1, B.bc[5] == BC_WALL};
     for (int k = k0; k < k1; ++k) {
       float F[3];
-      F[0] = rhs_comp<Fld<T>, ORDER, 0>(y, i, j, k, ih, ih2, nu);
-      F[1] = rhs_comp<Fld<T>, ORDER, 1>(y, i, j, k, ih, ih2, nu);
-      F[2] = rhs_comp<Fld<T>, ORDER, 2>(y, i, j, k, ih, ih2, nu);
+      F[0] = rhs_comp<Fld<T>, SCH, 0>(y, i, j, k, ih, ih2, nu);
+      F[1] = rhs_comp<Fld<T>, SCH, 1>(y, i, j, k, ih, ih2, nu);
+      F[2] = rhs_comp<Fld<T>, SCH, 2>(y, i, j, k, ih, ih2, nu);
       const long long o = (long long)k * B.pz + (long long)j * B.py + i;
 #pragma unroll
       for (int c = 0; c < 3; ++c) {
@@ -216,10 +243,10 @@ struct SFld {
   }
 };
 
-template <typename T, int ORDER, int TZ>
+template <typename T, int SCH, int TZ>
 __global__ void __launch_bounds__(256) k_stage_tile(Launch L, float a, Set3 xs, float b, Set3 ys,
                                                     float cdt, Set3 os, float nu) {
-  constexpr int H = ORDER == 2 ? 1 : 2;
+  constexpr int H = scheme_halo(SCH);
   constexpr int BX = 32, BY = 8, BZ = TZ;
   constexpr int SX = BX + 2 * H, SY = BY + 2 * H, SZ = BZ + 2 * H;
   constexpr int NT = SX * SY * SZ;
@@ -260,9 +287,9 @@ __global__ void __launch_bounds__(256) k_stage_tile(Launch L, float a, Set3 xs, 
       const int k1 = min(k0 + BZ, nz);
       for (int k = k0; k < k1; ++k) {
         float F[3];
-        F[0] = rhs_comp<SFld<SX, SY>, ORDER, 0>(f, i, j, k, ih, ih2, nu);
-        F[1] = rhs_comp<SFld<SX, SY>, ORDER, 1>(f, i, j, k, ih, ih2, nu);
-        F[2] = rhs_comp<SFld<SX, SY>, ORDER, 2>(f, i, j, k, ih, ih2, nu);
+        F[0] = rhs_comp<SFld<SX, SY>, SCH, 0>(f, i, j, k, ih, ih2, nu);
+        F[1] = rhs_comp<SFld<SX, SY>, SCH, 1>(f, i, j, k, ih, ih2, nu);
+        F[2] = rhs_comp<SFld<SX, SY>, SCH, 2>(f, i, j, k, ih, ih2, nu);
         const long long o = (long long)k * pz + (long long)j * py + i;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -294,13 +321,13 @@ struct RingFld {
   }
 };
 
-template <typename T, int ORDER, int TY>
+template <typename T, int SCH, int TY>
 __global__ void __launch_bounds__(32 * TY) k_stage_ring(Launch L, int zc, float a, Set3 xs,
                                                         float b, Set3 ys, float cdt, Set3 os,
                                                         float nu) {
-  constexpr int H = ORDER == 2 ? 1 : 2;
+  constexpr int H = scheme_halo(SCH);
   constexpr int SX = 32 + 2 * H, SY = TY + 2 * H, PL = SX * SY;
-  constexpr int R = ORDER == 2 ? 4 : 8;  // >= 2H + 2, a power of two
+  constexpr int R = H == 1 ? 4 : 8;  // >= 2H + 2, a power of two
   constexpr int NT = 32 * TY;
   constexpr int NL = (3 * PL + NT - 1) / NT;  // plane elements loaded per thread
   __shared__ float ring[R * 3 * PL];
@@ -373,9 +400,9 @@ __global__ void __launch_bounds__(32 * TY) k_stage_ring(Launch L, int zc, float 
       if (more) fetch(kn, nxt);
       if (mine) {
         float F[3];
-        F[0] = rhs_comp<RingFld<SX, PL, R>, ORDER, 0>(f, i, j, k, ih, ih2, nu);
-        F[1] = rhs_comp<RingFld<SX, PL, R>, ORDER, 1>(f, i, j, k, ih, ih2, nu);
-        F[2] = rhs_comp<RingFld<SX, PL, R>, ORDER, 2>(f, i, j, k, ih, ih2, nu);
+        F[0] = rhs_comp<RingFld<SX, PL, R>, SCH, 0>(f, i, j, k, ih, ih2, nu);
+        F[1] = rhs_comp<RingFld<SX, PL, R>, SCH, 1>(f, i, j, k, ih, ih2, nu);
+        F[2] = rhs_comp<RingFld<SX, PL, R>, SCH, 2>(f, i, j, k, ih, ih2, nu);
         const long long o = (long long)k * pz;
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
@@ -747,11 +774,11 @@ __device__ __forceinline__ void stage_issue(uint32_t ring_s, const int (&soff)[N
 // the planes that read it; the stage-2 input is loaded before the plane's
 // barrier so its latency overlaps the wait.  Same arithmetic (rhs_comp) and
 // results as k_stage_ring.
-template <int ORDER, int TY>
+template <int SCH, int TY>
 __global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float a, Set3 xs,
                                                          float b, Set3 ys, float cdt, Set3 os,
                                                          float nu) {
-  constexpr int H = ORDER == 2 ? 1 : 2;
+  constexpr int H = scheme_halo(SCH);
   constexpr int D = 2;  // planes in flight beyond k + H
   constexpr int SX = 32 + 2 * H, SY = TY + 2 * H, PL = SX * SY;
   constexpr int R = 8;  // >= 2H + 1 + D and a power of two
@@ -822,9 +849,9 @@ __global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float
       __syncthreads();
       if (mine) {
         float F[3];
-        F[0] = rhs_comp<RingFld<SX, PL, R>, ORDER, 0>(f, i, j, k, ih, ih2, nu);
-        F[1] = rhs_comp<RingFld<SX, PL, R>, ORDER, 1>(f, i, j, k, ih, ih2, nu);
-        F[2] = rhs_comp<RingFld<SX, PL, R>, ORDER, 2>(f, i, j, k, ih, ih2, nu);
+        F[0] = rhs_comp<RingFld<SX, PL, R>, SCH, 0>(f, i, j, k, ih, ih2, nu);
+        F[1] = rhs_comp<RingFld<SX, PL, R>, SCH, 1>(f, i, j, k, ih, ih2, nu);
+        F[2] = rhs_comp<RingFld<SX, PL, R>, SCH, 2>(f, i, j, k, ih, ih2, nu);
 #pragma unroll
         for (int c = 0; c < 3; ++c) {
           const bool wf = wall[c] && (c != 2 || k == nz - 1);
@@ -1474,77 +1501,69 @@ cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr, const lon
   return cudaGetLastError();
 }
 
-template <typename T, int ORDER, int TZ>
+template <typename T, int SCH, int TZ>
 static void run_stage_tile(const Launch& L, float a, Set3 xs, float b, Set3 ys, float cdt, Set3 os,
                            float nu) {
   const long long tiles = count_tiles(L, 32, 8, TZ);
-  auto kern = k_stage_tile<T, ORDER, TZ>;
+  auto kern = k_stage_tile<T, SCH, TZ>;
   static const int occ = occupancy(kern, 256);
   kern<<<grid_for(L, occ, tiles), 256, 0, L.stream>>>(L, a, xs, b, ys, cdt, os, nu);
 }
 
-template <typename T, int ORDER, int TY>
+template <typename T, int SCH, int TY>
 static void run_stage(const Launch& L, int zc, float a, Set3 xs, float b, Set3 ys, float cdt,
                       Set3 os, float nu) {
   const long long tiles = count_tiles(L, 32, TY, zc);
-  auto kern = k_stage<T, ORDER, TY>;
+  auto kern = k_stage<T, SCH, TY>;
   static const int occ = occupancy(kern, 32 * TY);
   kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
 }
 
-template <typename T, int ORDER, int TY>
+template <typename T, int SCH, int TY>
 static void run_stage_ring(const Launch& L, int zc, float a, Set3 xs, float b, Set3 ys, float cdt,
                            Set3 os, float nu) {
   const long long tiles = count_tiles(L, 32, TY, zc);
   if constexpr (sizeof(T) == 4) {
-    auto kern = k_stage_async<ORDER, TY>;
+    auto kern = k_stage_async<SCH, TY>;
     static const int occ = occupancy(kern, 32 * TY);
     kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
   } else {
-    auto kern = k_stage_ring<T, ORDER, TY>;
+    auto kern = k_stage_ring<T, SCH, TY>;
     static const int occ = occupancy(kern, 32 * TY);
     kern<<<grid_for(L, occ, tiles), dim3(32, TY), 0, L.stream>>>(L, zc, a, xs, b, ys, cdt, os, nu);
   }
 }
 
-cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int order, float a,
-                         const int* xset, float b, const int* yset, float cdt, const int* oset,
-                         float nu) {
-  const Set3 xs = xset ? mk3(xset) : Set3{{0, 0, 0}};
-  if (c.tile_tz == 1) {
-    CFD_DISPATCH_T(L.dtype, {
-      if (order == 4) {
-        if (c.ty == 4) run_stage_ring<T, 4, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-        else run_stage_ring<T, 4, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-      } else {
-        if (c.ty == 4) run_stage_ring<T, 2, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-        else run_stage_ring<T, 2, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-      }
-    });
-    return cudaGetLastError();
-  }
-  if (c.tile_tz == 2 || c.tile_tz == 4) {
-    CFD_DISPATCH_T(L.dtype, {
-      if (order == 4) {
-        if (c.tile_tz == 2) run_stage_tile<T, 4, 2>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-        else run_stage_tile<T, 4, 4>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-      } else {
-        if (c.tile_tz == 2) run_stage_tile<T, 2, 2>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-        else run_stage_tile<T, 2, 4>(L, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-      }
-    });
-    return cudaGetLastError();
-  }
+template <int SCH>
+static cudaError_t launch_stage_s(const Launch& L, const StencilCfg& c, float a, Set3 xs, float b,
+                                  Set3 ys, float cdt, Set3 os, float nu) {
   CFD_DISPATCH_T(L.dtype, {
-    if (order == 4) {
-      if (c.ty == 4) run_stage<T, 4, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-      else run_stage<T, 4, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+    if (c.tile_tz == 1) {
+      if (c.ty == 4) run_stage_ring<T, SCH, 4>(L, c.zc, a, xs, b, ys, cdt, os, nu);
+      else run_stage_ring<T, SCH, 8>(L, c.zc, a, xs, b, ys, cdt, os, nu);
+    } else if (c.tile_tz == 2) {
+      run_stage_tile<T, SCH, 2>(L, a, xs, b, ys, cdt, os, nu);
+    } else if (c.tile_tz == 4) {
+      run_stage_tile<T, SCH, 4>(L, a, xs, b, ys, cdt, os, nu);
     } else {
-      if (c.ty == 4) run_stage<T, 2, 4>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
-      else run_stage<T, 2, 8>(L, c.zc, a, xs, b, mk3(yset), cdt, mk3(oset), nu);
+      if (c.ty == 4) run_stage<T, SCH, 4>(L, c.zc, a, xs, b, ys, cdt, os, nu);
+      else run_stage<T, SCH, 8>(L, c.zc, a, xs, b, ys, cdt, os, nu);
     }
   });
   return cudaGetLastError();
+}
+
+cudaError_t launch_stage(const Launch& L, const StencilCfg& c, int scheme, float a,
+                         const int* xset, float b, const int* yset, float cdt, const int* oset,
+                         float nu) {
+  const Set3 xs = xset ? mk3(xset) : Set3{{0, 0, 0}};
+  const Set3 ys = mk3(yset), os = mk3(oset);
+  switch (scheme) {
+    case kSchemeAdv2: return launch_stage_s<kSchemeAdv2>(L, c, a, xs, b, ys, cdt, os, nu);
+    case kSchemeAdv4: return launch_stage_s<kSchemeAdv4>(L, c, a, xs, b, ys, cdt, os, nu);
+    case kSchemeFlux2: return launch_stage_s<kSchemeFlux2>(L, c, a, xs, b, ys, cdt, os, nu);
+    default: return cudaErrorInvalidValue;
+  }
 }
 
 cudaError_t launch_divergence(const Launch& L, const StencilCfg& c, const int* wset,

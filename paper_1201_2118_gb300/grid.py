@@ -146,6 +146,15 @@ class Grid:
     def set_params(self, nu: float, jacobi_iters: int = 50, omega: float = 1.0, order: int = 2):
         call("cfd_set_params", self.handle, float(nu), int(jacobi_iters), float(omega), int(order))
 
+    ADVECTION_FORMS = {"advective": 0, "flux": 1}
+
+    def set_advection(self, form: str):
+        """Advection term of the momentum equation: 'advective', (u . grad) u_c
+        (the default), or 'flux', the conservative div(u u_c) (order 2)."""
+        if form not in self.ADVECTION_FORMS:
+            raise ValueError(f"form must be one of {sorted(self.ADVECTION_FORMS)}")
+        call("cfd_set_advection", self.handle, self.ADVECTION_FORMS[form])
+
     # -------------------------------------------------------- path steps
     def ghost_fill(self, m: int):
         call("cfd_ghost_fill", self.handle, int(m))

@@ -9,7 +9,7 @@ builds an n^3 lid-driven cavity grid (seeded cavity noise), and for each
 given Jacobi variant (kind,vx,ty,zc,stages) runs the requested number of
 sweeps on the grid's stream, then checks the device error flag.  With
 --stages N it runs N RHS + stage-2 combines per stencil variant
-(ty,zc,tile_tz) instead (--order 2 or 4).  With
+(ty,zc,tile_tz) instead (--order 2 or 4, --form advective or flux).  With
 --time, each variant first runs 4 warm-up sweeps and the timed sweeps are
 bracketed by CUDA events on the grid's stream; the line printed per variant
 gives microseconds per sweep and the algorithmic bytes (read p and r, write
@@ -31,6 +31,7 @@ def main(argv=None):
                     help="instead of sweeps: this many RHS + stage-2 combines per stencil variant")
     ap.add_argument("--stencil", nargs="*", default=[], help="ty,zc,tile_tz ...")
     ap.add_argument("--order", type=int, default=2, choices=[2, 4])
+    ap.add_argument("--form", default="advective", choices=["advective", "flux"])
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -43,6 +44,7 @@ def main(argv=None):
     g = Grid((n, n, n), ghost=1 if a.order == 2 else 2, h=(1.0 / n,) * 3, dtype=a.dtype, stream=s)
     g.set_cavity(1.0)
     g.set_params(1e-3, 50, 1.0, a.order)
+    g.set_advection(a.form)
     g.upload(workloads.ldc_noise(n, seed=1))
     g.pressure_solve(1e-3, 0)
     es = 4 if a.dtype == "f32" else 2
@@ -68,8 +70,8 @@ def main(argv=None):
             torch.cuda.synchronize()
             us = e0.elapsed_time(e1) * 1e3 / a.stages
             gbs = 9 * es * n ** 3 / (us * 1e-6) / 1e9
-            print("%d^3 %s order %d stencil %s %.1f us/stage %.0f GB/s" % (n, a.dtype, a.order, cfg, us, gbs),
-                  flush=True)
+            print("%d^3 %s order %d %s stencil %s %.1f us/stage %.0f GB/s" %
+                  (n, a.dtype, a.order, a.form, cfg, us, gbs), flush=True)
         g.check()
         return
     for c in a.jacobi or [None]:

@@ -27,17 +27,18 @@ def rel_err(got, ref, remove_mean=False):
 
 
 def make_pair(dims, ghost=1, h=None, bc="periodic", nu=0.01, order=2, iters=50, omega=1.0,
-              fields=None, dtype="f32", lid=1.0):
+              fields=None, dtype="f32", lid=1.0, form="advective"):
     """Oracle and GPU grid holding the same (device-rounded) state."""
     from paper_1201_2118_gb300 import Grid
     if h is None:
         h = tuple(2 * math.pi / d for d in dims) if bc == "periodic" else tuple(1.0 / d for d in dims)
-    o = Oracle(dims, ghost=ghost, h=h, bc=bc, nu=nu, order=order, omega=omega, lid=lid)
+    o = Oracle(dims, ghost=ghost, h=h, bc=bc, nu=nu, order=order, omega=omega, lid=lid, form=form)
     g = Grid(dims, ghost=ghost, h=h, dtype=dtype)
     g.fill(float("nan"))
     if bc == "cavity":
         g.set_cavity(lid)
     g.set_params(nu, iters, omega, order)
+    g.set_advection(form)
     f = rounded(fields, dtype)
     g.upload(f)
     u, p = o.state(f)
