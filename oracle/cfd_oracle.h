@@ -97,6 +97,34 @@ int ora_set_threads(int n);
 /* The 7-point operator itself: lp = L p on the interior (test helper). */
 void ora_laplace_p(const ora_grid* G, const double* p, double* lp);
 
+/* ---- geometric multigrid for L p = r (cfd_oracle_mg.c) ---- */
+
+typedef struct {
+  int levels;    /* coarse levels below the grid, 1 .. ora_mg_max_levels */
+  int nu1, nu2;  /* weighted Jacobi sweeps before and after the coarse correction */
+  int ncoarse;   /* sweeps on the coarsest level (>= 1) */
+  double omega;  /* Jacobi weight of every sweep of the cycle */
+} ora_mg;
+
+/* Coarse levels available: halvings while every n_d is even and >= 4. */
+int ora_mg_max_levels(const ora_grid* G);
+
+/* The next coarser level: n / 2, 2 h, same faces, ghost width and order. */
+void ora_mg_coarse_grid(const ora_grid* F, ora_grid* C);
+
+/* rc(I) = mean over the 8 fine cells of coarse cell I of (r - L p); p ghosts
+ * filled; rc is a coarse array (ghosts set to 0). */
+void ora_mg_restrict_residual(const ora_grid* F, const double* p, const double* r, double* rc);
+
+/* p += trilinear interpolation of the coarse correction ec (ghosts filled)
+ * at the fine cell centres (weights 3/4, 1/4 per axis), then ghost fill of p. */
+void ora_mg_prolong_add(const ora_grid* F, const double* ec, double* p);
+
+/* One V-cycle on p (ghosts filled) for L p = r: nu1 sweeps, restriction of
+ * the residual, the same cycle on the coarse level from a zero correction
+ * (ncoarse sweeps on the coarsest), prolongation, nu2 sweeps. */
+void ora_mg_vcycle(const ora_grid* G, const ora_mg* M, double* p, const double* r);
+
 /* ---- discrete adjoint (cfd_oracle_adjoint.c) ---- */
 
 /* Transpose of ora_ghost_fill's linear part: ghost values are added onto

@@ -19,7 +19,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
-_SOURCES = ["cfd_oracle.c", "cfd_oracle_adjoint.c"]
+_SOURCES = ["cfd_oracle.c", "cfd_oracle_adjoint.c", "cfd_oracle_mg.c"]
 _lock = threading.Lock()
 _lib = None
 
@@ -46,6 +46,11 @@ class _Grid(ctypes.Structure):
                 ("bc", ctypes.c_int * 6), ("wall", (ctypes.c_double * 3) * 6),
                 ("nu", ctypes.c_double), ("omega", ctypes.c_double), ("order", ctypes.c_int),
                 ("form", ctypes.c_int)]
+
+
+class _Mg(ctypes.Structure):
+    _fields_ = [("levels", ctypes.c_int), ("nu1", ctypes.c_int), ("nu2", ctypes.c_int),
+                ("ncoarse", ctypes.c_int), ("omega", ctypes.c_double)]
 
 
 _D = ctypes.POINTER(ctypes.c_double)
@@ -86,6 +91,17 @@ def _load():
                 fn = getattr(lib, name)
                 fn.argtypes = args
                 fn.restype = None
+            mg = {
+                "ora_mg_restrict_residual": [G, _D, _D, _D],
+                "ora_mg_prolong_add": [G, _D, _D],
+                "ora_mg_vcycle": [G, ctypes.POINTER(_Mg), _D, _D],
+            }
+            for name, args in mg.items():
+                fn = getattr(lib, name)
+                fn.argtypes = args
+                fn.restype = None
+            lib.ora_mg_max_levels.argtypes = [G]
+            lib.ora_mg_max_levels.restype = ctypes.c_int
             lib.ora_set_threads.argtypes = [ctypes.c_int]
             lib.ora_set_threads.restype = ctypes.c_int
             _lib = lib
@@ -228,6 +244,42 @@ class Oracle:
         out = self.zeros()
         self.lib.ora_laplace_p(self._G(), _ptr(p), _ptr(out))
         return out
+
+    # -- geometric multigrid
+    def mg_max_levels(self):
+        return int(self.lib.ora_mg_max_levels(self._G()))
+
+    def coarse(self):
+        """Oracle of the next coarser level (n / 2, 2 h, same faces)."""
+        if any(d % 2 for d in self.dims):
+            raise ValueError("every dimension must be even")
+        c = Oracle.__new__(Oracle)
+        c.__dict__.update(self.__dict__)
+        gr = _Grid()
+        ctypes.pointer(gr)[0] = self._g
+        gr.n[:] = tuple(d // 2 for d in self.dims)
+        gr.h[:] = tuple(2 * x for x in self.h)
+        c._g = gr
+        c.dims = tuple(d // 2 for d in self.dims)
+        c.h = tuple(2 * x for x in self.h)
+        c.shape = tuple(d + 2 * self.g for d in c.dims[::-1])
+        return c
+
+    def mg_restrict_residual(self, p, r):
+        rc = self.coarse().zeros()
+        self.lib.ora_mg_restrict_residual(self._G(), _ptr(p), _ptr(r), _ptr(rc))
+        return rc
+
+    def mg_prolong_add(self, ec, p):
+        self.lib.ora_mg_prolong_add(self._G(), _ptr(ec), _ptr(p))
+        return p
+
+    def mg_vcycle(self, p, r, levels, nu1=2, nu2=2, ncoarse=30, omega=6.0 / 7.0, cycles=1):
+        """cycles V-cycles in place on p (ghosts filled)."""
+        m = _Mg(int(levels), int(nu1), int(nu2), int(ncoarse), float(omega))
+        for _ in range(cycles):
+            self.lib.ora_mg_vcycle(self._G(), ctypes.byref(m), _ptr(p), _ptr(r))
+        return p
 
     # -- discrete adjoint
     def ghost_fold(self, f, kind):
