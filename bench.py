@@ -395,6 +395,73 @@ def measure_adjoint(torch):
             "note": "backward = recomputation of every segment from its checkpoint + adjoint steps"}
 
 
+def measure_multigrid(torch):
+    """512^3 lid-driven cavity, R = D W / dt with W the seeded cavity noise:
+    the pressure equation solved to ||L P - R|| <= 1e-5 ||R|| by V-cycles
+    (V(2,2), weighted Jacobi 6/7, all levels down to 2^3), against the
+    residual that the same time buys in Jacobi sweeps of the bench's
+    configured kernel."""
+    from paper_1201_2118_gb300 import Grid, P, R, U, V, W, WU, WV, WW, mask
+    n = 512
+    h = (1.0 / n,) * 3
+    dt = workloads.cfl_dt(h)
+    s = torch.cuda.Stream()
+    g = Grid((n, n, n), ghost=1, h=h, stream=s)
+    g.set_cavity(1.0)
+    g.upload(workloads.ldc_noise(n, seed=1))
+    with torch.cuda.stream(s):
+        for a_, b_ in ((U, WU), (V, WV), (W, WW)):
+            g.interior(b_).copy_(g.interior(a_))
+    g.ghost_fill(mask(WU, WV, WW))
+    g.autotune(None)
+    ev = lambda: torch.cuda.Event(enable_timing=True)
+
+    def zero_p():
+        with torch.cuda.stream(s):
+            g.interior(P).zero_()
+        g.ghost_fill(mask(P))
+
+    zero_p()
+    g.pressure_solve_mg(dt, 1e-5, 30)  # warm-up (graphs, caches)
+    zero_p()
+    torch.cuda.synchronize()
+    a_, b_ = ev(), ev()
+    a_.record(s)
+    cycles, res = g.pressure_solve_mg(dt, 1e-5, 30)
+    b_.record(s)
+    torch.cuda.synchronize()
+    solve_ms = a_.elapsed_time(b_)
+    with torch.cuda.stream(s):
+        rnorm = g.interior(R).double().norm().item()
+    a_, b_ = ev(), ev()
+    a_.record(s)
+    g.mg_vcycles(10)
+    b_.record(s)
+    torch.cuda.synchronize()
+    cycle_ms = a_.elapsed_time(b_) / 10
+    # Jacobi from the same start for the same time
+    zero_p()
+    g.jacobi(4)
+    torch.cuda.synchronize()
+    a_, b_ = ev(), ev()
+    a_.record(s)
+    g.jacobi(100)
+    b_.record(s)
+    torch.cuda.synchronize()
+    sweep_ms = a_.elapsed_time(b_) / 100
+    sweeps = max(2, int(round(solve_ms / sweep_ms / 2)) * 2)
+    zero_p()
+    _, jres = g.pressure_solve_converged(dt, 0.0, sweeps, sweeps)
+    g.check()
+    return {"workload": "512^3 cavity, R = D(cavity noise)/dt", "rtol": 1e-5,
+            "cycles": cycles, "solve_ms": solve_ms, "ms_per_vcycle": cycle_ms,
+            "rel_residual": res / rnorm, "levels": g.multigrid_levels(),
+            "cycle": "V(2,2), weighted Jacobi omega 6/7, 30 sweeps on the coarsest level",
+            "jacobi_same_time": {"sweeps": sweeps, "ms_per_sweep": sweep_ms,
+                                 "rel_residual": jres / rnorm,
+                                 "jacobi_config": g.kernel_config()[0]}}
+
+
 # ---------------------------------------------------------------- GPU leg
 
 def run_gpu(a):
@@ -546,7 +613,8 @@ def run_gpu(a):
         torch.cuda.empty_cache()
         secondary = {"precision": measure_precision(torch, a.precision_steps),
                      "blocks": measure_blocks(torch),
-                     "adjoint": measure_adjoint(torch)}
+                     "adjoint": measure_adjoint(torch),
+                     "multigrid": measure_multigrid(torch)}
 
     if rank == 0:
         line = {

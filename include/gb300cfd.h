@@ -187,6 +187,50 @@ cfd_status cfd_stage(cfd_grid* g, double a, int x_set, double b, int y_set, doub
 cfd_status cfd_pressure_solve_converged(cfd_grid* g, double c_dt, double rtol, int max_iters,
                                         int check_every, int* iters_done, double* residual);
 
+/* Geometric multigrid for the pressure equation L P = R (an extension: the
+ * paper fixes no solver).  Cell-centred V-cycle in the correction scheme:
+ * level l + 1 halves every axis of level l (coarse cell I covers fine cells
+ * 2I and 2I + 1) and keeps the faces' kinds; every level uses the 7-point
+ * L with its own cell size 2^l h; smoother: weighted Jacobi of weight omega
+ * (nu1 sweeps before, nu2 after the coarse correction, ncoarse on the
+ * coarsest level); restriction: mean over the 8 fine cells of R - L P;
+ * prolongation: trilinear interpolation of the coarse correction at the
+ * fine cell centres (weights 3/4, 1/4 per axis, coarse ghosts at faces).
+ * Single FP32 blocks whose dims are even down to the coarsest level: the
+ * grid keeps three arrays per level (1/7 of one field in total) in its
+ * memory (cfd_memory_bytes includes them). */
+
+/* Coarse levels available: halvings while every dim is even and >= 4
+ * (0 for block sets, 16-bit storage or odd dims). */
+cfd_status cfd_multigrid_levels(const cfd_grid* g, int* levels);
+
+/* Cycle parameters: levels (0 = all available, else 1..available), nu1,
+ * nu2 >= 0, ncoarse >= 1, omega in (0, 2).  Defaults 0, 2, 2, 30, 6/7.
+ * CFD_EINVAL on a bad value. */
+cfd_status cfd_set_multigrid(cfd_grid* g, int levels, int nu1, int nu2, int ncoarse,
+                             double omega);
+
+/* cycles V-cycles on P for L P = R as they stand (P's ghosts must be
+ * filled; they are on exit).  Asynchronous on the grid's stream.
+ * CFD_EUNSUPPORTED where cfd_multigrid_levels is 0. */
+cfd_status cfd_mg_vcycles(cfd_grid* g, int cycles);
+
+/* R = (D W)/c_dt, then V-cycles on P (warm start) until ||L P - R||_2 <=
+ * rtol ||R||_2 (checked before the first cycle and after each) or
+ * max_cycles.  cycles_done and residual (either may be NULL) receive the
+ * cycles taken and the last ||L P - R||_2.  Synchronises once per cycle. */
+cfd_status cfd_pressure_solve_mg(cfd_grid* g, double c_dt, double rtol, int max_cycles,
+                                 int* cycles_done, double* residual);
+
+/* Pressure solve inside the steps' stages (cfd_rk_step, cfd_step):
+ * CFD_SOLVER_JACOBI (default) takes jacobi_iters sweeps (cfd_set_params);
+ * CFD_SOLVER_MG takes 'cycles' (>= 1) V-cycles of cfd_set_multigrid's
+ * parameters, warm-started from the last pressure.  CFD_EUNSUPPORTED for
+ * CFD_SOLVER_MG where cfd_multigrid_levels is 0; the adjoint needs
+ * CFD_SOLVER_JACOBI.  Invalidates captured step graphs. */
+typedef enum { CFD_SOLVER_JACOBI = 0, CFD_SOLVER_MG = 1 } cfd_solver;
+cfd_status cfd_set_pressure_solver(cfd_grid* g, int solver, int cycles);
+
 /* F(U) into WU, WV, WW (cfd_stage(g, 0, -, 0, U, 1, W)). */
 cfd_status cfd_rhs_eval(cfd_grid* g);
 

@@ -125,6 +125,11 @@ void ora_mg_prolong_add(const ora_grid* F, const double* ec, double* p);
  * (ncoarse sweeps on the coarsest), prolongation, nu2 sweeps. */
 void ora_mg_vcycle(const ora_grid* G, const ora_mg* M, double* p, const double* r);
 
+/* ora_rk2_step with each stage's pressure solve replaced by 'cycles'
+ * V-cycles (warm start from the last pressure).  scratch: 7 arrays. */
+void ora_rk2_step_mg(const ora_grid* G, double* const u[3], double* p, double dt,
+                     const ora_mg* M, int cycles, double* const scratch[8]);
+
 /* ---- discrete adjoint (cfd_oracle_adjoint.c) ---- */
 
 /* Transpose of ora_ghost_fill's linear part: ghost values are added onto

@@ -116,3 +116,30 @@ static void vcycle(const ora_grid* G, const ora_mg* M, int depth, double* p, con
 void ora_mg_vcycle(const ora_grid* G, const ora_mg* M, double* p, const double* r) {
   vcycle(G, M, 0, p, r);
 }
+
+void ora_rk2_step_mg(const ora_grid* G, double* const u[3], double* p, double dt,
+                     const ora_mg* M, int cycles, double* const scratch[8]) {
+  double* const W[3] = {scratch[0], scratch[1], scratch[2]};
+  double* const U1[3] = {scratch[3], scratch[4], scratch[5]};
+  double* R = scratch[6];
+  const double* cu[3] = {u[0], u[1], u[2]};
+  const double* cW[3] = {W[0], W[1], W[2]};
+  const double* cU1[3] = {U1[0], U1[1], U1[2]};
+  for (int c = 0; c < 3; ++c) ora_ghost_fill(G, u[c], c);
+  ora_ghost_fill(G, p, ORA_P);
+  /* the two projected Heun stages of ora_rk2_step, each pressure solve
+   * being 'cycles' V-cycles from the last pressure */
+  for (int stage = 1; stage <= 2; ++stage) {
+    const double cdt = stage == 1 ? dt : 0.5 * dt;
+    if (stage == 1)
+      ora_stage(G, 0.0, NULL, 1.0, cu, dt, W);
+    else
+      ora_stage(G, 0.5, cu, 0.5, cU1, 0.5 * dt, W);
+    for (int c = 0; c < 3; ++c) ora_ghost_fill(G, W[c], c);
+    ora_divergence(G, cW, cdt, R);
+    for (int k = 0; k < cycles; ++k) ora_mg_vcycle(G, M, p, R);
+    double* const* out = stage == 1 ? U1 : u;
+    ora_project(G, cW, p, cdt, out);
+    for (int c = 0; c < 3; ++c) ora_ghost_fill(G, out[c], c);
+  }
+}

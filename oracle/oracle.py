@@ -95,6 +95,8 @@ def _load():
                 "ora_mg_restrict_residual": [G, _D, _D, _D],
                 "ora_mg_prolong_add": [G, _D, _D],
                 "ora_mg_vcycle": [G, ctypes.POINTER(_Mg), _D, _D],
+                "ora_rk2_step_mg": [G, P3, _D, ctypes.c_double, ctypes.POINTER(_Mg), ctypes.c_int,
+                                    _D * 8],
             }
             for name, args in mg.items():
                 fn = getattr(lib, name)
@@ -280,6 +282,18 @@ class Oracle:
         for _ in range(cycles):
             self.lib.ora_mg_vcycle(self._G(), ctypes.byref(m), _ptr(p), _ptr(r))
         return p
+
+    def rk2_step_mg(self, u, p, dt, cycles, levels=0, nu1=2, nu2=2, ncoarse=30,
+                    omega=6.0 / 7.0, steps=1):
+        """steps RK2 steps in place, each pressure solve 'cycles' V-cycles
+        (levels 0: all available)."""
+        m = _Mg(int(levels or self.mg_max_levels()), int(nu1), int(nu2), int(ncoarse),
+                float(omega))
+        scratch = [self.zeros() for _ in range(8)]
+        for _ in range(steps):
+            self.lib.ora_rk2_step_mg(self._G(), _p3(u), _ptr(p), float(dt), ctypes.byref(m),
+                                     int(cycles), (_D * 8)(*[_ptr(s) for s in scratch]))
+        return u, p
 
     # -- discrete adjoint
     def ghost_fold(self, f, kind):

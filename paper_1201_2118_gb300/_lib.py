@@ -33,6 +33,11 @@ SIGNATURES = {
     "cfd_set_bc": [c_void_p, c_int, c_int, P(c_double)],
     "cfd_set_params": [c_void_p, c_double, c_int, c_double, c_int],
     "cfd_set_advection": [c_void_p, c_int],
+    "cfd_multigrid_levels": [c_void_p, P(c_int)],
+    "cfd_set_multigrid": [c_void_p, c_int, c_int, c_int, c_int, c_double],
+    "cfd_mg_vcycles": [c_void_p, c_int],
+    "cfd_set_pressure_solver": [c_void_p, c_int, c_int],
+    "cfd_pressure_solve_mg": [c_void_p, c_double, c_double, c_int, P(c_int), P(c_double)],
     "cfd_ghost_fill": [c_void_p, c_uint],
     "cfd_stage": [c_void_p, c_double, c_int, c_double, c_int, c_double, c_int],
     "cfd_rhs_eval": [c_void_p],

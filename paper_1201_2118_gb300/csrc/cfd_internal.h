@@ -137,6 +137,15 @@ cudaError_t launch_project(const Launch& L, const StencilCfg& c, const int* wset
                            float cdt, const int* oset);
 cudaError_t launch_copy(const Launch& L, const StencilCfg& c, int src, int dst);
 
+// Multigrid grid transfers (FP32 storage).  A view is the interior origin of
+// one array of one level with its pitches and interior dims.
+struct MgView { float* o; int n[3]; int py; long long pz; };
+// coarse_r = mean over each coarse cell's 8 children of (fine_r - L fine_p).
+cudaError_t launch_mg_restrict(cudaStream_t s, const MgView& fine_p, const float* fine_r,
+                               const MgView& coarse_r, const float ih2_fine[3]);
+// fine_p += trilinear interpolation of coarse_e (ghosts current) at the fine centres.
+cudaError_t launch_mg_prolong(cudaStream_t s, const MgView& fine_p, const MgView& coarse_e);
+
 // FP64 reductions: per-CTA partials into 'partials' (nparts x 4 doubles),
 // then a one-CTA fixed-order pass into 'out' (4 doubles).
 // mode 0: velocity set (sum |u|^2, max |u_d|, max |D u|, non-finite count)

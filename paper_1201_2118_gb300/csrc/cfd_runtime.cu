@@ -93,6 +93,24 @@ struct cfd_grid {
   long long graph_nodes = 0;   // kernel launches per replay
   long long launches = 0;      // kernel launches enqueued (incl. replays)
 
+  // geometric multigrid (single FP32 block): coarse levels 1..mg_max, each
+  // with three arrays (correction P, its ping-pong P2, residual R)
+  struct MgLevel {
+    int n[3];
+    int py;
+    long long pz;
+    size_t array_bytes, first_byte;
+  };
+  std::vector<MgLevel> mgl;   // level l at index l - 1
+  std::vector<BlockDev> mg_bdev;
+  std::vector<int> mg_hn;     // 3 ints per level
+  std::vector<long long> mg_prefix;  // 2 per level: {0, ghost cells}
+  size_t mg_table_off = 0, mg_prefix_off = 0;
+  int mg_levels = 0, mg_nu1 = 2, mg_nu2 = 2, mg_ncoarse = 30;  // mg_levels 0: all
+  double mg_omega = 6.0 / 7.0;
+  int solver = CFD_SOLVER_JACOBI;  // pressure solve inside the step's stages
+  int mg_cycles = 2;               // V-cycles per stage solve (CFD_SOLVER_MG)
+
   // rollout graphs: segment recompute and segment adjoint, keyed by length
   struct SegGraph { cudaGraphExec_t exec = nullptr; long long nodes = 0; int len = 0; };
   SegGraph rec_graph[2], adj_graph[2];
@@ -144,6 +162,22 @@ void plan_layout(cfd_grid* g) {
   off = round_up(off + (size_t)kTmaMapBytes * 3 * g->nblocks, 256);
   g->adj_off = off;
   off = round_up(off + 8 * sizeof(double), 256);
+  // multigrid levels: every axis halves while all are even and >= 4
+  g->mgl.clear();
+  if (g->nblocks == 1 && g->dtype == CFD_F32) {
+    int n[3] = {g->hb[0].n[0], g->hb[0].n[1], g->hb[0].n[2]};
+    while (g->mgl.size() < 16 && n[0] % 2 == 0 && n[1] % 2 == 0 && n[2] % 2 == 0 && n[0] >= 4 &&
+           n[1] >= 4 && n[2] >= 4) {
+      cfd_grid::MgLevel m{};
+      for (int a = 0; a < 3; ++a) m.n[a] = (n[a] /= 2);
+      g->mgl.push_back(m);
+    }
+  }
+  const size_t nl = g->mgl.size();
+  g->mg_table_off = off;
+  off = round_up(off + sizeof(BlockDev) * std::max<size_t>(nl, 1), 256);
+  g->mg_prefix_off = off;
+  off = round_up(off + sizeof(long long) * 2 * std::max<size_t>(nl, 1), 256);
   g->arrays_off = off;
   for (auto& b : g->hb) {
     b.py = (int)round_up((size_t)align_e + b.n[0] + g->g, align_e);
@@ -159,6 +193,20 @@ void plan_layout(cfd_grid* g) {
     stage = std::max(stage, (size_t)b.n[0] * b.n[1] * b.n[2] * g->es);
   g->staging_off = off;
   off += round_up(stage, 256);
+  g->mg_hn.clear();
+  g->mg_prefix.clear();
+  for (auto& m : g->mgl) {
+    m.py = (int)round_up((size_t)align_e + m.n[0] + g->g, align_e);
+    m.pz = (long long)m.py * (m.n[1] + 2 * g->g);
+    m.array_bytes = round_up((size_t)m.pz * (m.n[2] + 2 * g->g) * g->es, 256);
+    m.first_byte = off;
+    off += 3 * m.array_bytes;
+    for (int a = 0; a < 3; ++a) g->mg_hn.push_back(m.n[a]);
+    const long long ex = m.n[0] + 2 * g->g, ey = m.n[1] + 2 * g->g;
+    g->mg_prefix.push_back(0);
+    g->mg_prefix.push_back(2LL * g->g * ey * ex + 2LL * g->g * m.n[2] * ex +
+                           2LL * g->g * m.n[2] * m.n[1]);
+  }
   off += 256;  // tail pad: a 4-byte halo copy next to the very last row stays inside
   g->bytes = off;
   // ghost-cell enumeration prefix (z-slabs, y-slabs, x-slabs per block)
@@ -194,6 +242,23 @@ void build_tables(cfd_grid* g) {
       for (int c = 0; c < 3; ++c) d.wall[f][c] = (float)g->wall[f][c];
     }
   }
+  // multigrid levels: one self-neighbouring block each; P, P2 and R are the
+  // level's three arrays, the other ids alias P and are never addressed
+  g->mg_bdev.resize(g->mgl.size());
+  for (size_t l = 0; l < g->mgl.size(); ++l) {
+    const auto& m = g->mgl[l];
+    BlockDev& d = g->mg_bdev[l];
+    memset(&d, 0, sizeof d);
+    for (int a = 0; a < 3; ++a) d.n[a] = m.n[a];
+    d.py = m.py;
+    d.pz = m.pz;
+    const long long lead = (long long)g->g * m.pz + (long long)g->g * m.py + align_e;
+    for (int a = 0; a < kNumArrays; ++a) {
+      const int slot = a == A_P2 ? 1 : a == A_R ? 2 : 0;
+      d.org[a] = (long long)((m.first_byte + m.array_bytes * slot) / g->es) + lead;
+    }
+    for (int f = 0; f < 6; ++f) d.bc[f] = g->bc[f];
+  }
 }
 
 cfd_status refresh_maps(cfd_grid* g);
@@ -206,6 +271,12 @@ cfd_status upload_tables(cfd_grid* g) {
   CK(g, cudaMemcpyAsync(g->base + g->prefix_off, g->ghost_prefix.data(),
                         sizeof(long long) * (g->nblocks + 1), cudaMemcpyHostToDevice, g->own));
   CK(g, cudaMemsetAsync(g->base + g->flag_off, 0, 256, g->own));
+  if (!g->mgl.empty()) {
+    CK(g, cudaMemcpyAsync(g->base + g->mg_table_off, g->mg_bdev.data(),
+                          sizeof(BlockDev) * g->mg_bdev.size(), cudaMemcpyHostToDevice, g->own));
+    CK(g, cudaMemcpyAsync(g->base + g->mg_prefix_off, g->mg_prefix.data(),
+                          sizeof(long long) * g->mg_prefix.size(), cudaMemcpyHostToDevice, g->own));
+  }
   CK(g, cudaStreamSynchronize(g->own));
   return refresh_maps(g);
 }
@@ -375,19 +446,21 @@ bool fused_ok(const cfd_grid* g) {
 
 // One Jacobi sweep src -> dst with the configured variant (the fused
 // variant's single sweeps use the register/shuffle kernel).
-cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst) {
+cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst, float omega) {
   if (g->jcfg.kind == 5 || g->jcfg.kind == 9)
-    return launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, src, dst, A_R, (float)g->omega);
+    return launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, src, dst, A_R, omega);
   if ((g->jcfg.kind == 1 || g->jcfg.kind == 7) && g->maps_ready)
     return launch_jacobi_tma(L, g->jcfg, g->base + g->maps_off, src == A_P ? 0 : 1, dst,
-                             (float)g->omega);
-  if (g->jcfg.kind == 2) return launch_jacobi_direct(L, g->jcfg, src, dst, A_R, (float)g->omega);
-  if (g->jcfg.kind == 3) return launch_jacobi_async(L, g->jcfg, src, dst, A_R, (float)g->omega);
+                             omega);
+  if (g->jcfg.kind == 2) return launch_jacobi_direct(L, g->jcfg, src, dst, A_R, omega);
+  if (g->jcfg.kind == 3) return launch_jacobi_async(L, g->jcfg, src, dst, A_R, omega);
 
-  return launch_jacobi(L, g->jcfg, src, dst, A_R, (float)g->omega);
+  return launch_jacobi(L, g->jcfg, src, dst, A_R, omega);
 }
 
-cfd_status enq_sweeps(cfd_grid* g, int iters) {
+// iters sweeps of weight omega on P (result in P, ghosts current).
+cfd_status enq_sweeps(cfd_grid* g, int iters, double omega) {
+  const float om = (float)omega;
   int cur = A_P, oth = A_P2;
   cfd_status s;
   if (fused_ok(g)) {
@@ -395,21 +468,21 @@ cfd_status enq_sweeps(cfd_grid* g, int iters) {
     for (int it = 0; it + 1 < iters; it += 2) {
       if (g->jcfg.kind == 9)
         CK(g, launch_jacobi2_ws(L, g->jcfg, g->base + g->maps_off, cur == A_P ? 0 : 1, oth,
-                                (float)g->omega));
+                                om));
       else
-        CK(g, launch_jacobi2(L, g->jcfg, cur, oth, A_R, (float)g->omega));
+        CK(g, launch_jacobi2(L, g->jcfg, cur, oth, A_R, om));
       g->launches += 1;
       std::swap(cur, oth);
     }
     if (iters % 2) {
-      CK(g, sweep(g, L, cur, oth));
+      CK(g, sweep(g, L, cur, oth, om));
       g->launches += 1;
       std::swap(cur, oth);
     }
     iters = 0;
   }
   for (int it = 0; it < iters; ++it) {
-    if ((s = each_launch(g, [&](const Launch& L) { return sweep(g, L, cur, oth); })) != CFD_OK)
+    if ((s = each_launch(g, [&](const Launch& L) { return sweep(g, L, cur, oth, om); })) != CFD_OK)
       return s;
     std::swap(cur, oth);
   }
@@ -426,7 +499,7 @@ cfd_status enq_solve(cfd_grid* g, double c_dt, int iters) {
     return launch_divergence(L, g->scfg, kSets[CFD_SET_W], (float)(1.0 / c_dt), A_R);
   });
   if (s != CFD_OK) return s;
-  return enq_sweeps(g, iters);
+  return enq_sweeps(g, iters, g->omega);
 }
 
 cfd_status enq_project(cfd_grid* g, double c_dt, int os) {
@@ -437,19 +510,117 @@ cfd_status enq_project(cfd_grid* g, double c_dt, int os) {
   return enq_ghost(g, set_mask(os));
 }
 
+cfd_status enq_vcycle(cfd_grid* g, int l, int depth);
+int mg_depth(const cfd_grid* g);
+
+// The pressure solve of a step's stage: K Jacobi sweeps, or V-cycles.
+cfd_status enq_stage_solve(cfd_grid* g, double c_dt) {
+  if (g->solver != CFD_SOLVER_MG) return enq_solve(g, c_dt, g->iters);
+  cfd_status s = enq_solve(g, c_dt, 0);
+  for (int c = 0; c < g->mg_cycles && s == CFD_OK; ++c) s = enq_vcycle(g, 0, mg_depth(g));
+  return s;
+}
+
 cfd_status enq_rk_stage(cfd_grid* g, int stage, double dt) {
   cfd_status s;
   if (stage == 1) {
     if ((s = enq_ghost(g, set_mask(CFD_SET_U) | (1u << A_P))) != CFD_OK) return s;
     if ((s = enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, dt, CFD_SET_W)) != CFD_OK) return s;
     if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
-    if ((s = enq_solve(g, dt, g->iters)) != CFD_OK) return s;
+    if ((s = enq_stage_solve(g, dt)) != CFD_OK) return s;
     return enq_project(g, dt, CFD_SET_U1);
   }
   if ((s = enq_stage(g, 0.5, CFD_SET_U, 0.5, CFD_SET_U1, 0.5 * dt, CFD_SET_W)) != CFD_OK) return s;
   if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
-  if ((s = enq_solve(g, 0.5 * dt, g->iters)) != CFD_OK) return s;
+  if ((s = enq_stage_solve(g, 0.5 * dt)) != CFD_OK) return s;
   return enq_project(g, 0.5 * dt, CFD_SET_U);
+}
+
+// ------------------------------------------------------------- multigrid
+
+int mg_depth(const cfd_grid* g) {
+  const int avail = (int)g->mgl.size();
+  return g->mg_levels > 0 ? std::min(g->mg_levels, avail) : avail;
+}
+
+cfd_status mg_supported(cfd_grid* g) {
+  if (g->nblocks != 1 || g->dtype != CFD_F32)
+    return fail(CFD_EUNSUPPORTED, "multigrid needs a single FP32 block");
+  if (g->mgl.empty())
+    return fail(CFD_EUNSUPPORTED, "multigrid needs every dimension even and >= 4");
+  return CFD_OK;
+}
+
+// Launch over level l (0: the grid itself): one block, cell size 2^l h.
+Launch level_launch(cfd_grid* g, int l) {
+  Launch L = make_launch(g);
+  if (l == 0) return L;
+  L.blocks = reinterpret_cast<const BlockDev*>(g->base + g->mg_table_off) + (l - 1);
+  L.b0 = 0;
+  L.nblocks = 1;
+  for (int d = 0; d < 3; ++d) {
+    const double h = std::ldexp(g->h[d], l);
+    L.ih[d] = (float)(1.0 / h);
+    L.ih2[d] = (float)(1.0 / (h * h));
+  }
+  L.hn = reinterpret_cast<const int(*)[3]>(g->mg_hn.data() + 3 * (l - 1));
+  return L;
+}
+
+MgView mg_view(cfd_grid* g, int l, int arr) {
+  const BlockDev& d = l == 0 ? g->bdev[0] : g->mg_bdev[l - 1];
+  MgView v;
+  v.o = reinterpret_cast<float*>(g->base) + d.org[arr];
+  for (int a = 0; a < 3; ++a) v.n[a] = d.n[a];
+  v.py = d.py;
+  v.pz = d.pz;
+  return v;
+}
+
+// n weighted Jacobi sweeps on level l's P for L P = R (result in P).
+cfd_status enq_level_sweeps(cfd_grid* g, int l, int n) {
+  if (l == 0) return enq_sweeps(g, n, g->mg_omega);
+  const Launch L = level_launch(g, l);
+  int cur = A_P, oth = A_P2;
+  for (int it = 0; it < n; ++it) {
+    CK(g, launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, cur, oth, A_R, (float)g->mg_omega));
+    g->launches += 1;
+    std::swap(cur, oth);
+  }
+  if (cur != A_P) {
+    CK(g, launch_copy(L, g->scfg, cur, A_P));
+    g->launches += 1;
+  }
+  return CFD_OK;
+}
+
+// Every ghost cell of level l's P (the prolongation reads edges and corners).
+cfd_status enq_level_ghost(cfd_grid* g, int l) {
+  if (l == 0) return enq_ghost(g, 1u << A_P);
+  const int arr = A_P;
+  const long long* prefix = reinterpret_cast<const long long*>(g->base + g->mg_prefix_off) + 2 * (l - 1);
+  CK(g, launch_ghost(level_launch(g, l), &arr, 1, prefix, g->mg_prefix[2 * (l - 1) + 1]));
+  g->launches += 1;
+  return CFD_OK;
+}
+
+// One V-cycle from level l down to level depth (correction scheme).
+cfd_status enq_vcycle(cfd_grid* g, int l, int depth) {
+  cfd_status s;
+  if (l == depth) return enq_level_sweeps(g, l, g->mg_ncoarse);
+  if ((s = enq_level_sweeps(g, l, g->mg_nu1)) != CFD_OK) return s;
+  const Launch L = level_launch(g, l);
+  CK(g, launch_mg_restrict(g->own, mg_view(g, l, A_P), mg_view(g, l, A_R).o,
+                           mg_view(g, l + 1, A_R), L.ih2));
+  g->launches += 1;
+  const auto& c = g->mgl[l];
+  CK(g, cudaMemsetAsync(g->base + c.first_byte, 0, c.array_bytes, g->own));  // zero correction
+  if ((s = enq_vcycle(g, l + 1, depth)) != CFD_OK) return s;
+  if ((s = enq_level_ghost(g, l + 1)) != CFD_OK) return s;
+  CK(g, launch_mg_prolong(g->own, mg_view(g, l, A_P), mg_view(g, l + 1, A_P)));
+  g->launches += 1;
+  if ((s = enq_level_ghost(g, l)) != CFD_OK) return s;
+  return enq_level_sweeps(g, l, g->mg_nu2);
 }
 
 cfd_status run_reduce(cfd_grid* g, int mode, int set, double out[4]) {
@@ -477,6 +648,8 @@ cfd_status adjoint_supported(cfd_grid* g) {
                 "the adjoint needs one FP32 block, order 2 and ghost width 2");
   if (g->form != CFD_ADVECTIVE)
     return fail(CFD_EUNSUPPORTED, "the adjoint linearises the advective form only");
+  if (g->solver != CFD_SOLVER_JACOBI)
+    return fail(CFD_EUNSUPPORTED, "the adjoint transposes the Jacobi pressure solve only");
   for (int f = 0; f < 6; ++f)
     if (g->bc[f] != CFD_BC_PERIODIC) return fail(CFD_EUNSUPPORTED, "the adjoint needs periodic faces");
   return CFD_OK;
@@ -508,7 +681,7 @@ cfd_status enq_adjoint_step(cfd_grid* g, double dt, const Ptr3& un, const Ptr3& 
     if ((s = enq_ghost(g, 1u << A_P)) != CFD_OK) return s;
     int cur = A_P, oth = A_P2;
     for (int it = 0; it < g->iters; ++it) {
-      CK(g, sweep(g, L, cur, oth));
+      CK(g, sweep(g, L, cur, oth, (float)g->omega));
       std::swap(cur, oth);
     }
     // cur = b_{K+1}, oth = b_K (for K = 0, b_1 in both roles: lam_r = 0 path)
@@ -561,7 +734,7 @@ cfd_status time_region(cfd_grid* g, int reps, float* ms, int what) {
     // kernels are timed in both of a step's forms (stage 1 reads one
     // velocity set, stage 2 two)
     if (what == 0) {
-      s = enq_sweeps(g, 4);
+      s = enq_sweeps(g, 4, g->omega);
     } else {
       s = enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, 1e-3, CFD_SET_W);
       if (s == CFD_OK) s = enq_stage(g, 0.5, CFD_SET_U, 0.5, CFD_SET_U1, 1e-3, CFD_SET_W);
@@ -853,7 +1026,7 @@ cfd_status cfd_pressure_solve_converged(cfd_grid* g, double c_dt, double rtol, i
   res = std::sqrt(out[0]);
   while (!(res <= target) && done < max_iters) {
     const int n = std::min(check_every, max_iters - done);
-    if ((s = enq_sweeps(g, n)) != CFD_OK) return s;
+    if ((s = enq_sweeps(g, n, g->omega)) != CFD_OK) return s;
     done += n;
     if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
     res = std::sqrt(out[0]);
@@ -864,12 +1037,88 @@ cfd_status cfd_pressure_solve_converged(cfd_grid* g, double c_dt, double rtol, i
   return join_out(g);
 }
 
+cfd_status cfd_multigrid_levels(const cfd_grid* g, int* levels) {
+  if (!g || !levels) return fail(CFD_EINVAL, "null argument");
+  *levels = (int)g->mgl.size();
+  return CFD_OK;
+}
+
+cfd_status cfd_set_multigrid(cfd_grid* g, int levels, int nu1, int nu2, int ncoarse,
+                             double omega) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (levels < 0 || nu1 < 0 || nu2 < 0 || ncoarse < 1 || !(omega > 0.0 && omega < 2.0))
+    return fail(CFD_EINVAL, "need levels >= 0, nu1, nu2 >= 0, ncoarse >= 1, omega in (0, 2)");
+  if (levels > (int)g->mgl.size())
+    return fail(CFD_EINVAL, "only %d coarse levels are available", (int)g->mgl.size());
+  g->mg_levels = levels;
+  g->mg_nu1 = nu1;
+  g->mg_nu2 = nu2;
+  g->mg_ncoarse = ncoarse;
+  g->mg_omega = omega;
+  invalidate_graph(g);
+  return CFD_OK;
+}
+
+cfd_status cfd_set_pressure_solver(cfd_grid* g, int solver, int cycles) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (solver != CFD_SOLVER_JACOBI && solver != CFD_SOLVER_MG)
+    return fail(CFD_EINVAL, "solver must be CFD_SOLVER_JACOBI or CFD_SOLVER_MG");
+  if (solver == CFD_SOLVER_MG) {
+    cfd_status s = mg_supported(g);
+    if (s != CFD_OK) return s;
+    if (cycles < 1) return fail(CFD_EINVAL, "cycles must be >= 1");
+    g->mg_cycles = cycles;
+  }
+  g->solver = solver;
+  invalidate_graph(g);
+  return CFD_OK;
+}
+
+cfd_status cfd_mg_vcycles(cfd_grid* g, int cycles) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if ((s = mg_supported(g)) != CFD_OK) return s;
+  if (cycles < 0) return fail(CFD_EINVAL, "cycles must be >= 0");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  for (int c = 0; c < cycles; ++c)
+    if ((s = enq_vcycle(g, 0, mg_depth(g))) != CFD_OK) return s;
+  return join_out(g);
+}
+
+cfd_status cfd_pressure_solve_mg(cfd_grid* g, double c_dt, double rtol, int max_cycles,
+                                 int* cycles_done, double* residual) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if ((s = mg_supported(g)) != CFD_OK) return s;
+  if (!(c_dt > 0.0) || !(rtol >= 0.0) || max_cycles < 0)
+    return fail(CFD_EINVAL, "need c_dt > 0, rtol >= 0, max_cycles >= 0");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  if ((s = enq_solve(g, c_dt, 0)) != CFD_OK) return s;  // R = (D W)/c_dt
+  double out[4];
+  if ((s = run_reduce(g, 2, 0, out)) != CFD_OK) return s;
+  if (out[3] != 0.0) return fail(CFD_ENONFINITE, "right-hand side is not finite");
+  const double target = rtol * std::sqrt(out[0]);
+  if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
+  double res = std::sqrt(out[0]);
+  int done = 0;
+  while (!(res <= target) && done < max_cycles) {
+    if ((s = enq_vcycle(g, 0, mg_depth(g))) != CFD_OK) return s;
+    ++done;
+    if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
+    res = std::sqrt(out[0]);
+    if (out[3] != 0.0) return fail(CFD_ENONFINITE, "residual is not finite");
+  }
+  if (cycles_done) *cycles_done = done;
+  if (residual) *residual = res;
+  return join_out(g);
+}
+
 cfd_status cfd_jacobi(cfd_grid* g, int iters) {
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (iters < 0) return fail(CFD_EINVAL, "iters must be >= 0");
   if ((s = join_in(g)) != CFD_OK) return s;
-  if ((s = enq_sweeps(g, iters)) != CFD_OK) return s;
+  if ((s = enq_sweeps(g, iters, g->omega)) != CFD_OK) return s;
   return join_out(g);
 }
 

@@ -185,6 +185,37 @@ class Grid:
     def jacobi(self, iters: int):
         call("cfd_jacobi", self.handle, int(iters))
 
+    # ------------------------------------------------------------ multigrid
+    def multigrid_levels(self) -> int:
+        n = ctypes.c_int()
+        call("cfd_multigrid_levels", self.handle, ctypes.byref(n))
+        return n.value
+
+    def set_multigrid(self, levels: int = 0, nu1: int = 2, nu2: int = 2, ncoarse: int = 30,
+                      omega: float = 6.0 / 7.0):
+        call("cfd_set_multigrid", self.handle, int(levels), int(nu1), int(nu2), int(ncoarse),
+             float(omega))
+
+    def set_pressure_solver(self, solver: str = "jacobi", cycles: int = 2):
+        """Pressure solve of the steps' stages: 'jacobi' (jacobi_iters sweeps)
+        or 'mg' (cycles V-cycles)."""
+        kinds = {"jacobi": 0, "mg": 1}
+        if solver not in kinds:
+            raise ValueError("solver must be 'jacobi' or 'mg'")
+        call("cfd_set_pressure_solver", self.handle, kinds[solver], int(cycles))
+
+    def mg_vcycles(self, cycles: int):
+        call("cfd_mg_vcycles", self.handle, int(cycles))
+
+    def pressure_solve_mg(self, c_dt: float, rtol: float, max_cycles: int):
+        """V-cycles until ||L P - R|| <= rtol ||R|| or max_cycles; returns
+        (cycles taken, final residual)."""
+        n = ctypes.c_int()
+        r = c_double()
+        call("cfd_pressure_solve_mg", self.handle, float(c_dt), float(rtol), int(max_cycles),
+             ctypes.byref(n), ctypes.byref(r))
+        return n.value, r.value
+
     @property
     def launches(self) -> int:
         n = c_ll()

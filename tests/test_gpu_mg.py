@@ -1,0 +1,215 @@
+"""Multigrid V-cycles on the CUDA path against the oracle's V-cycle.
+
+Same cycle on both sides (levels, nu1, nu2, ncoarse, omega); FP32 storage,
+so the pressure after k cycles agrees to e(p) <= 1e-5 (mean removed; the
+problems with periodic or zero-gradient faces fix p up to a constant).
+Dims span several 128 x 4 sweep tiles on the fine level and fall to 2-3
+cells per axis on the coarsest.
+"""
+import math
+
+import numpy as np
+import pytest
+
+from gpu_helpers import rel_err, rounded
+
+pytestmark = pytest.mark.gpu
+
+
+def _setup(dims, bc, seed, h=None):
+    from oracle import Oracle
+    from paper_1201_2118_gb300 import Grid, P, R, mask
+    if h is None:
+        h = tuple(1.0 / d for d in dims)
+    o = Oracle(dims, ghost=1, h=h, bc=bc)
+    grid = Grid(dims, ghost=1, h=h)
+    grid.fill(float("nan"))
+    if bc == "cavity":
+        grid.set_cavity(1.0)
+    r = np.random.default_rng(seed).uniform(-1, 1, dims[::-1])
+    r = rounded({"r": r - r.mean()})["r"]
+    grid.interior(R).copy_(grid.torch.from_numpy(r).float().cuda())
+    grid.interior(P).zero_()
+    grid.ghost_fill(mask(P))
+    p = o.ghost_fill(o.zeros(), 3)
+    return o, grid, p, o.embed(r)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+@pytest.mark.parametrize("dims", [(64, 32, 48), (40, 24, 56)])
+@pytest.mark.parametrize("cycles", [1, 3])
+def test_mg_vcycles_match_oracle(bc, dims, cycles):
+    from paper_1201_2118_gb300 import P
+    o, grid, p, r = _setup(dims, bc, 1)
+    levels = grid.multigrid_levels()
+    assert levels == o.mg_max_levels() > 0
+    grid.mg_vcycles(cycles)
+    o.mg_vcycle(p, r, levels, cycles=cycles)
+    assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
+    grid.check()
+
+
+@pytest.mark.parametrize("jacobi", [(0, 4, 4, 32, 4), (1, 4, 16, 16, 4), (9, 4, 16, 16, 6),
+                                    (9, 4, 8, 7, 5)])
+def test_mg_with_each_fine_smoother(jacobi):
+    """The fine level smooths with the grid's configured sweep kernel (the
+    two-sweep kernels on walled grids, odd counts ending with one sweep)."""
+    from paper_1201_2118_gb300 import P
+    dims = (64, 48, 40)
+    o, grid, p, r = _setup(dims, "cavity", 2)
+    grid.set_kernel_config(jacobi=jacobi)
+    grid.set_multigrid(0, 3, 2, 30, 6.0 / 7.0)
+    grid.mg_vcycles(2)
+    o.mg_vcycle(p, r, grid.multigrid_levels(), nu1=3, nu2=2, cycles=2)
+    assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
+
+
+def test_mg_cycle_parameters():
+    from paper_1201_2118_gb300 import P
+    dims = (48, 32, 64)
+    o, grid, p, r = _setup(dims, "periodic", 3, h=(0.02, 0.025, 0.03))
+    grid.set_multigrid(2, 1, 3, 40, 0.8)
+    grid.mg_vcycles(2)
+    o.mg_vcycle(p, r, 2, nu1=1, nu2=3, ncoarse=40, omega=0.8, cycles=2)
+    assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
+
+
+def test_pressure_solve_mg_converges_like_oracle():
+    """R = D W / c_dt from a wall-compatible W, V-cycles to rtol 1e-5: the
+    oracle, checking the same criterion after each cycle, stops at the same
+    cycle (or one away when FP32 rounding puts a check at the threshold);
+    the result and the reported residual match the oracle's."""
+    from oracle import Oracle
+    from paper_1201_2118_gb300 import Grid, P, WU, WV, WW, mask
+    dims = (64, 64, 64)
+    h = tuple(1.0 / d for d in dims)
+    o = Oracle(dims, ghost=1, h=h, bc="cavity")
+    grid = Grid(dims, ghost=1, h=h)
+    grid.set_cavity(1.0)
+    rng = np.random.default_rng(7)
+    w = rounded({c: rng.uniform(-1, 1, dims[::-1]) for c in "uvw"})
+    w["u"][:, :, -1] = 0.0
+    w["v"][:, -1, :] = 0.0
+    w["w"][-1, :, :] = 0.0
+    for k, a in enumerate((WU, WV, WW)):
+        grid.interior(a).copy_(grid.torch.from_numpy(w["uvw"[k]]).float().cuda())
+    grid.ghost_fill(mask(WU, WV, WW))
+    grid.interior(P).zero_()
+    grid.ghost_fill(mask(P))
+    c_dt = 0.01
+    n, res = grid.pressure_solve_mg(c_dt, 1e-5, 30)
+    wo = [o.ghost_fill(o.embed(w["uvw"[k]]), k) for k in range(3)]
+    r = o.divergence(wo, c_dt)
+    p = o.ghost_fill(o.zeros(), 3)
+    target = 1e-5 * np.linalg.norm(o.interior(r))
+    m = 0
+    while o.residual(p, r) > target and m < 30:
+        o.mg_vcycle(p, r, o.mg_max_levels())
+        m += 1
+    assert 3 <= n <= 20 and abs(n - m) <= 1, (n, m)
+    assert res <= target * 1.0001
+    q = o.ghost_fill(o.zeros(), 3)
+    o.mg_vcycle(q, r, o.mg_max_levels(), cycles=n)
+    assert rel_err(grid.download(P), o.interior(q), remove_mean=True) < 1e-5
+    assert res == pytest.approx(o.residual(q, r), rel=0.05)
+
+
+def test_mg_unsupported_cases():
+    from paper_1201_2118_gb300 import CfdError, Grid
+    import workloads
+    for g in (Grid((33, 16, 16), ghost=1, h=(0.1,) * 3),
+              Grid((32, 16, 16), ghost=1, h=(0.1,) * 3, dtype="bf16")):
+        assert g.multigrid_levels() == 0
+        with pytest.raises(CfdError) as e:
+            g.mg_vcycles(1)
+        assert e.value.status == 5
+    gd, blocks = workloads.block_tiling(seed=2, lo=8, hi=20)
+    bs = Grid(ghost=1, h=(0.1,) * 3, blocks=[(b["dims"], b["origin"]) for b in blocks],
+              global_dims=gd)
+    assert bs.multigrid_levels() == 0
+    g = Grid((32, 16, 16), ghost=1, h=(0.1,) * 3)
+    assert g.multigrid_levels() == 3  # (32, 16, 16) -> (16, 8, 8) -> (8, 4, 4) -> (4, 2, 2)
+    with pytest.raises(CfdError) as e:
+        g.set_multigrid(4)
+    assert e.value.status == 1
+    with pytest.raises(CfdError) as e:
+        g.set_multigrid(0, omega=2.0)
+    assert e.value.status == 1
+    g.check()
+
+
+def test_mg_full_size_cavity_solve():
+    """512^3 cavity (the step's workload), R from the divergence of seeded
+    cavity noise: V-cycles reach rtol 1e-5 in at most 12 cycles, and the
+    reported residual equals ||L P - R||_2 recomputed in FP64 from the
+    stored P and R."""
+    import torch
+    import workloads
+    from paper_1201_2118_gb300 import Grid, P, R, WU, WV, WW, U, V, W, mask
+    n = 512
+    h = (1.0 / n,) * 3
+    grid = Grid((n, n, n), ghost=1, h=h)
+    grid.set_cavity(1.0)
+    grid.upload(workloads.ldc_noise(n, seed=1))
+    for a, b in ((U, WU), (V, WV), (W, WW)):
+        grid.interior(b).copy_(grid.interior(a))
+    grid.ghost_fill(mask(WU, WV, WW))
+    dt = workloads.cfl_dt(h)
+    k, res = grid.pressure_solve_mg(dt, 1e-5, 20)
+    assert 2 <= k <= 12, k
+    p = grid.array(P).double()
+    r = grid.interior(R).double()
+    c = 1.0 / h[0] ** 2
+    lp = (p[1:-1, 1:-1, 2:] + p[1:-1, 1:-1, :-2] + p[1:-1, 2:, 1:-1] + p[1:-1, :-2, 1:-1] +
+          p[2:, 1:-1, 1:-1] + p[:-2, 1:-1, 1:-1] - 6 * p[1:-1, 1:-1, 1:-1]) * c
+    ref = torch.linalg.vector_norm(lp - r).item()
+    assert res == pytest.approx(ref, rel=1e-3)
+    assert res <= 1e-5 * torch.linalg.vector_norm(r).item() * 1.0001
+    grid.check()
+
+
+@pytest.mark.parametrize("bc,dims,form", [("cavity", (32, 32, 32), "advective"),
+                                          ("cavity", (32, 32, 32), "flux"),
+                                          ("periodic", (64, 32, 48), "advective")])
+def test_mg_projected_steps_match_oracle(bc, dims, form):
+    """The graph-replayed RK2 step with each stage's pressure solve taken as
+    two V-cycles: 1 step at 1e-5, 5 steps at 1e-4 (velocity) / 1e-3
+    (pressure) against the oracle's multigrid step."""
+    import workloads
+    from gpu_helpers import compare_state, make_pair
+    if bc == "cavity":
+        h = tuple(1.0 / d for d in dims)
+        fl = workloads.ldc_noise(dims[0], seed=1)
+    else:
+        h = tuple(2 * math.pi / d for d in dims)
+        fl = workloads.random_div_free(dims, h, seed=3)
+    o, grid, u, p = make_pair(dims, bc=bc, h=h, nu=1e-3 if bc == "cavity" else 0.01,
+                              fields=fl, form=form)
+    grid.set_pressure_solver("mg", 2)
+    dt = workloads.cfl_dt(h)
+    grid.step(dt, 1)
+    o.rk2_step_mg(u, p, dt, 2)
+    compare_state(o, grid, u, p, 1e-5, 1e-5, "mg step 1")
+    grid.step(dt, 4)
+    o.rk2_step_mg(u, p, dt, 2, steps=4)
+    compare_state(o, grid, u, p, 1e-4, 1e-3, "mg step 5")
+    ke, umax, divmax = grid.reduce(0)
+    assert divmax < 1e-3 * umax / min(h)
+
+
+def test_mg_solver_selection_errors():
+    from paper_1201_2118_gb300 import CfdError, Grid
+    g = Grid((33, 16, 16), ghost=1, h=(0.1,) * 3)
+    with pytest.raises(CfdError) as e:
+        g.set_pressure_solver("mg", 2)
+    assert e.value.status == 5
+    g = Grid((32, 32, 32), ghost=2, h=(0.2,) * 3)
+    with pytest.raises(CfdError) as e:
+        g.set_pressure_solver("mg", 0)
+    assert e.value.status == 1
+    g.set_pressure_solver("mg", 2)
+    with pytest.raises(CfdError) as e:  # the adjoint transposes the Jacobi solve only
+        g.rollout_forward(0.01, 4, 2, 0, 0)
+    assert e.value.status == 5
+    g.set_pressure_solver("jacobi")
+    g.check()

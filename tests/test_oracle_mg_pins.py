@@ -140,3 +140,51 @@ def test_unweighted_jacobi_does_not_smooth():
     -1), so the cycle's factor approaches 1 while omega = 6/7 stays small."""
     assert _factor(32, "periodic", 1.0, cycles=12) > 0.85
     assert _factor(32, "periodic", 6.0 / 7.0, cycles=12) < 0.4
+
+
+def _exact_projection_step(o, u, dt, solve):
+    """Heun step with each stage's pressure equation solved exactly by
+    'solve' (FFT or DCT), composed from the pinned stage, divergence and
+    projection functions."""
+    def ghosts(f):
+        return [o.ghost_fill(a, k) for k, a in enumerate(f)]
+
+    def project(w, cdt):
+        r = o.divergence(w, cdt)
+        p = o.ghost_fill(o.embed(solve(o.interior(r), o.h)), 3)
+        return ghosts(o.project(w, p, cdt)), p
+
+    w = ghosts(o.stage(0.0, None, 1.0, u, dt))
+    u1, _ = project(w, dt)
+    w = ghosts(o.stage(0.5, u, 0.5, u1, 0.5 * dt))
+    return project(w, 0.5 * dt)
+
+
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+def test_mg_step_converges_to_exact_projection_step(bc):
+    """With enough V-cycles per solve the multigrid step equals the step whose
+    pressure equations are solved exactly (velocity 1e-10, pressure up to a
+    constant), and its velocity is discretely divergence-free."""
+    import workloads
+    dims = (32, 16, 24)
+    if bc == "periodic":
+        h = (2 * math.pi / 32, 2 * math.pi / 16, 2 * math.pi / 24)
+        fl = workloads.random_div_free(dims, h, seed=3)
+        solve = exact_poisson_periodic
+    else:
+        h = (1 / 32, 1 / 16, 1 / 24)
+        rng = np.random.default_rng(8)
+        fl = {c: 1e-2 * rng.uniform(-1, 1, dims[::-1]) for c in "uvwp"}
+        solve = exact_poisson_neumann
+    o = Oracle(dims, h=h, bc=bc, nu=0.01)
+    u, p = o.state(fl)
+    dt = 0.2 * min(h)
+    ue, pe = _exact_projection_step(o, [a.copy() for a in u], dt, solve)
+    o.rk2_step_mg(u, p, dt, 40)
+    for k in range(3):
+        scale = np.abs(o.interior(ue[k])).max()
+        assert np.abs(o.interior(u[k]) - o.interior(ue[k])).max() < 1e-10 * scale, k
+    gp, ep = o.interior(p) - o.interior(p).mean(), o.interior(pe) - o.interior(pe).mean()
+    assert np.abs(gp - ep).max() < 1e-9 * np.abs(ep).max()
+    assert np.abs(o.interior(o.divergence(u))).max() < 1e-10 * max(
+        np.abs(o.interior(a)).max() for a in u) / min(h)
