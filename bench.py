@@ -452,8 +452,20 @@ def measure_multigrid(torch):
     sweeps = max(2, int(round(solve_ms / sweep_ms / 2)) * 2)
     zero_p()
     _, jres = g.pressure_solve_converged(dt, 0.0, sweeps, sweeps)
+    # the cavity step with 50 Jacobi sweeps per stage solve against 2 V-cycles
+    steps = {}
+    for solver in ("jacobi", "mg"):
+        g.upload(workloads.ldc_noise(n, seed=1))
+        g.set_pressure_solver(solver, 2)
+        ms = _time_steps(torch, g, dt, 3, 10)
+        _, _, divmax = g.reduce(0)
+        steps[solver] = {"ms_per_step": ms, "glups": n ** 3 / (ms * 1e-3) / 1e9,
+                         "max_abs_div_after_13_steps": divmax}
+    steps["jacobi"]["solve"] = "50 weighted Jacobi sweeps (omega 1) per stage"
+    steps["mg"]["solve"] = "2 V-cycles per stage"
     g.check()
     return {"workload": "512^3 cavity, R = D(cavity noise)/dt", "rtol": 1e-5,
+            "steps": steps,
             "cycles": cycles, "solve_ms": solve_ms, "ms_per_vcycle": cycle_ms,
             "rel_residual": res / rnorm, "levels": g.multigrid_levels(),
             "cycle": "V(2,2), weighted Jacobi omega 6/7, 30 sweeps on the coarsest level",

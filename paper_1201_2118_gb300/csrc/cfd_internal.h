@@ -143,8 +143,34 @@ struct MgView { float* o; int n[3]; int py; long long pz; };
 // coarse_r = mean over each coarse cell's 8 children of (fine_r - L fine_p).
 cudaError_t launch_mg_restrict(cudaStream_t s, const MgView& fine_p, const float* fine_r,
                                const MgView& coarse_r, const float ih2_fine[3]);
-// fine_p += trilinear interpolation of coarse_e (ghosts current) at the fine centres.
-cudaError_t launch_mg_prolong(cudaStream_t s, const MgView& fine_p, const MgView& coarse_e);
+// fine_p += trilinear interpolation of coarse_e (ghosts current) at the fine
+// centres; the face ghost images of fine_p (periodic or mirror per axis) are
+// written too (edges and corners are not).
+cudaError_t launch_mg_prolong(cudaStream_t s, const MgView& fine_p, const MgView& coarse_e,
+                              const int periodic[3]);
+
+// The bottom of a V-cycle in one CTA: levels 0 .. levels - 1 of it (level 0
+// = the first level with at most kMgBottomCells cells) live in shared
+// memory.  r_in is level 0's R (from the restriction above it); p_out
+// receives level 0's correction with its first ghost layer (edges and
+// corners included).
+constexpr int kMgBottomLevels = 12;
+constexpr int kMgBottomCells = 8192;
+struct MgBottom {
+  int levels;
+  int n[kMgBottomLevels][3];
+  float c[kMgBottomLevels][3];     // 1/h^2 per axis
+  float inv_diag[kMgBottomLevels];
+  int per[3];                      // axis periodic (else walls, zero-gradient ghosts)
+  int nu1, nu2, ncoarse;
+  float omega;
+  MgView r_in, p_out;
+};
+size_t mg_bottom_smem(const MgBottom& b);
+// Raises the bottom kernel's shared-memory limit (once per process, before
+// any stream capture that may launch it).
+cudaError_t prepare_mg_bottom();
+cudaError_t launch_mg_bottom(cudaStream_t s, const MgBottom& b);
 
 // FP64 reductions: per-CTA partials into 'partials' (nparts x 4 doubles),
 // then a one-CTA fixed-order pass into 'out' (4 doubles).

@@ -108,6 +108,9 @@ struct cfd_grid {
   size_t mg_table_off = 0, mg_prefix_off = 0;
   int mg_levels = 0, mg_nu1 = 2, mg_nu2 = 2, mg_ncoarse = 30;  // mg_levels 0: all
   double mg_omega = 6.0 / 7.0;
+  cudaGraphExec_t mg_exec = nullptr;  // one V-cycle, captured on first use
+  bool mg_valid = false;
+  long long mg_nodes = 0;
   int solver = CFD_SOLVER_JACOBI;  // pressure solve inside the step's stages
   int mg_cycles = 2;               // V-cycles per stage solve (CFD_SOLVER_MG)
 
@@ -151,7 +154,7 @@ void plan_layout(cfd_grid* g) {
   off = round_up(off + sizeof(BlockDev) * g->nblocks, 256);
   g->prefix_off = off;
   off = round_up(off + sizeof(long long) * (g->nblocks + 1), 256);
-  g->nparts = 4 * g->sms;
+  g->nparts = 8 * g->sms;  // reduction CTAs: 8 per SM of 256 threads (full occupancy)
   g->partial_off = off;
   off = round_up(off + sizeof(double) * 4 * g->nparts, 256);
   g->out_off = off;
@@ -350,6 +353,8 @@ cfd_status common_init(cfd_grid* g, int ghost, const double h[3], int storage, v
     for (int d = 0; d < 3; ++d) g->hn[3 * b + d] = g->hb[b].n[d];
   g->jcfg = JacobiCfg{0, 4, 8, 32, 4};
   plan_layout(g);
+  if (!g->mgl.empty() && (e = prepare_mg_bottom()) != cudaSuccess)
+    return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
   return CFD_OK;
 }
 
@@ -366,6 +371,7 @@ void drop_seg_graphs(cfd_grid* g) {
 void destroy_handles(cfd_grid* g) {
   drop_seg_graphs(g);
   if (g->gexec) cudaGraphExecDestroy(g->gexec);
+  if (g->mg_exec) cudaGraphExecDestroy(g->mg_exec);
   if (g->own) cudaStreamSynchronize(g->own);
   if (g->owns && g->base) cudaFree(g->base);
   if (g->h_out) cudaFreeHost(g->h_out);
@@ -458,10 +464,12 @@ cudaError_t sweep(cfd_grid* g, const Launch& L, int src, int dst, float omega) {
   return launch_jacobi(L, g->jcfg, src, dst, A_R, omega);
 }
 
-// iters sweeps of weight omega on P (result in P, ghosts current).
-cfd_status enq_sweeps(cfd_grid* g, int iters, double omega) {
+// iters sweeps of weight omega from 'start' (P or P2, ghosts current).
+// With end == nullptr the result is copied into P if it lands in P2;
+// otherwise *end receives the array holding it (ghosts current).
+cfd_status enq_sweeps(cfd_grid* g, int iters, double omega, int start = A_P, int* end = nullptr) {
   const float om = (float)omega;
-  int cur = A_P, oth = A_P2;
+  int cur = start, oth = start == A_P ? A_P2 : A_P;
   cfd_status s;
   if (fused_ok(g)) {
     const Launch L = make_launch(g);
@@ -485,6 +493,10 @@ cfd_status enq_sweeps(cfd_grid* g, int iters, double omega) {
     if ((s = each_launch(g, [&](const Launch& L) { return sweep(g, L, cur, oth, om); })) != CFD_OK)
       return s;
     std::swap(cur, oth);
+  }
+  if (end) {
+    *end = cur;
+    return CFD_OK;
   }
   if (cur != A_P) {
     const Launch L = make_launch(g);
@@ -510,14 +522,13 @@ cfd_status enq_project(cfd_grid* g, double c_dt, int os) {
   return enq_ghost(g, set_mask(os));
 }
 
-cfd_status enq_vcycle(cfd_grid* g, int l, int depth);
-int mg_depth(const cfd_grid* g);
+cfd_status enq_vcycle_p(cfd_grid* g);
 
 // The pressure solve of a step's stage: K Jacobi sweeps, or V-cycles.
 cfd_status enq_stage_solve(cfd_grid* g, double c_dt) {
   if (g->solver != CFD_SOLVER_MG) return enq_solve(g, c_dt, g->iters);
   cfd_status s = enq_solve(g, c_dt, 0);
-  for (int c = 0; c < g->mg_cycles && s == CFD_OK; ++c) s = enq_vcycle(g, 0, mg_depth(g));
+  for (int c = 0; c < g->mg_cycles && s == CFD_OK; ++c) s = enq_vcycle_p(g);
   return s;
 }
 
@@ -577,50 +588,133 @@ MgView mg_view(cfd_grid* g, int l, int arr) {
   return v;
 }
 
-// n weighted Jacobi sweeps on level l's P for L P = R (result in P).
-cfd_status enq_level_sweeps(cfd_grid* g, int l, int n) {
-  if (l == 0) return enq_sweeps(g, n, g->mg_omega);
+// n weighted Jacobi sweeps on level l for L P = R from the array 'start'
+// (P or P2); *end receives the array holding the result.  Coarse levels use
+// the register sweep with a z chunk small enough to give every SM a few
+// tiles (they are latency-bound, not bandwidth-bound).
+cfd_status enq_level_sweeps(cfd_grid* g, int l, int n, int start, int* end) {
+  if (l == 0) return enq_sweeps(g, n, g->mg_omega, start, end);
   const Launch L = level_launch(g, l);
-  int cur = A_P, oth = A_P2;
+  const int* dn = g->mg_hn.data() + 3 * (l - 1);
+  const long long txy = (long long)((dn[0] + 127) / 128) * ((dn[1] + 3) / 4);
+  const int zc = (int)std::max(1LL, std::min(32LL, dn[2] * txy / (4LL * g->sms)));
+  int cur = start, oth = start == A_P ? A_P2 : A_P;
   for (int it = 0; it < n; ++it) {
-    CK(g, launch_jacobi(L, JacobiCfg{0, 4, 4, 32, 4}, cur, oth, A_R, (float)g->mg_omega));
+    CK(g, launch_jacobi(L, JacobiCfg{0, 4, 4, zc, 4}, cur, oth, A_R, (float)g->mg_omega));
     g->launches += 1;
     std::swap(cur, oth);
   }
-  if (cur != A_P) {
-    CK(g, launch_copy(L, g->scfg, cur, A_P));
-    g->launches += 1;
-  }
+  *end = cur;
   return CFD_OK;
 }
 
-// Every ghost cell of level l's P (the prolongation reads edges and corners).
-cfd_status enq_level_ghost(cfd_grid* g, int l) {
-  if (l == 0) return enq_ghost(g, 1u << A_P);
-  const int arr = A_P;
+// Every ghost cell of level l's array arr (the prolongation reads edges and
+// corners).
+cfd_status enq_level_ghost(cfd_grid* g, int l, int arr) {
+  if (l == 0) return enq_ghost(g, 1u << arr);
   const long long* prefix = reinterpret_cast<const long long*>(g->base + g->mg_prefix_off) + 2 * (l - 1);
   CK(g, launch_ghost(level_launch(g, l), &arr, 1, prefix, g->mg_prefix[2 * (l - 1) + 1]));
   g->launches += 1;
   return CFD_OK;
 }
 
-// One V-cycle from level l down to level depth (correction scheme).
-cfd_status enq_vcycle(cfd_grid* g, int l, int depth) {
+// First level (>= 1) small enough for the one-CTA bottom of the cycle.
+int mg_bottom_level(const cfd_grid* g, int depth) {
+  for (int l = 1; l <= depth; ++l) {
+    const int* n = g->mg_hn.data() + 3 * (l - 1);
+    if ((long long)n[0] * n[1] * n[2] <= kMgBottomCells) return l;
+  }
+  return depth + 1;  // none
+}
+
+MgBottom mg_bottom_args(cfd_grid* g, int lb, int depth) {
+  MgBottom b;
+  memset(&b, 0, sizeof b);
+  b.levels = depth - lb + 1;
+  for (int q = 0; q < b.levels; ++q) {
+    const Launch L = level_launch(g, lb + q);
+    for (int a = 0; a < 3; ++a) {
+      b.n[q][a] = g->mg_hn[3 * (lb + q - 1) + a];
+      b.c[q][a] = L.ih2[a];
+    }
+    b.inv_diag[q] = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+  }
+  for (int a = 0; a < 3; ++a) b.per[a] = g->bc[2 * a] == CFD_BC_PERIODIC;
+  b.nu1 = g->mg_nu1;
+  b.nu2 = g->mg_nu2;
+  b.ncoarse = g->mg_ncoarse;
+  b.omega = (float)g->mg_omega;
+  b.r_in = mg_view(g, lb, A_R);
+  b.p_out = mg_view(g, lb, A_P);
+  return b;
+}
+
+// One V-cycle from level l down to level depth (correction scheme).  *cur:
+// the array (P or P2) holding level l's iterate, on entry and on exit.
+cfd_status enq_vcycle(cfd_grid* g, int l, int depth, int* cur) {
   cfd_status s;
-  if (l == depth) return enq_level_sweeps(g, l, g->mg_ncoarse);
-  if ((s = enq_level_sweeps(g, l, g->mg_nu1)) != CFD_OK) return s;
+  if (l == depth) return enq_level_sweeps(g, l, g->mg_ncoarse, *cur, cur);
+  if ((s = enq_level_sweeps(g, l, g->mg_nu1, *cur, cur)) != CFD_OK) return s;
   const Launch L = level_launch(g, l);
-  CK(g, launch_mg_restrict(g->own, mg_view(g, l, A_P), mg_view(g, l, A_R).o,
+  CK(g, launch_mg_restrict(g->own, mg_view(g, l, *cur), mg_view(g, l, A_R).o,
                            mg_view(g, l + 1, A_R), L.ih2));
   g->launches += 1;
-  const auto& c = g->mgl[l];
-  CK(g, cudaMemsetAsync(g->base + c.first_byte, 0, c.array_bytes, g->own));  // zero correction
-  if ((s = enq_vcycle(g, l + 1, depth)) != CFD_OK) return s;
-  if ((s = enq_level_ghost(g, l + 1)) != CFD_OK) return s;
-  CK(g, launch_mg_prolong(g->own, mg_view(g, l, A_P), mg_view(g, l + 1, A_P)));
+  int ccur = A_P;
+  if (l + 1 == mg_bottom_level(g, depth)) {
+    // levels l + 1 .. depth in one CTA; it writes level l + 1's P and ghosts
+    CK(g, launch_mg_bottom(g->own, mg_bottom_args(g, l + 1, depth)));
+    g->launches += 1;
+  } else {
+    const auto& c = g->mgl[l];
+    CK(g, cudaMemsetAsync(g->base + c.first_byte, 0, c.array_bytes, g->own));  // zero correction
+    if ((s = enq_vcycle(g, l + 1, depth, &ccur)) != CFD_OK) return s;
+    if ((s = enq_level_ghost(g, l + 1, ccur)) != CFD_OK) return s;
+  }
+  const int per[3] = {g->bc[0] == CFD_BC_PERIODIC, g->bc[2] == CFD_BC_PERIODIC,
+                      g->bc[4] == CFD_BC_PERIODIC};
+  CK(g, launch_mg_prolong(g->own, mg_view(g, l, *cur), mg_view(g, l + 1, ccur), per));
   g->launches += 1;
-  if ((s = enq_level_ghost(g, l)) != CFD_OK) return s;
-  return enq_level_sweeps(g, l, g->mg_nu2);
+  return enq_level_sweeps(g, l, g->mg_nu2, *cur, cur);
+}
+
+// One V-cycle on the grid's P (result in P).
+cfd_status enq_vcycle_p(cfd_grid* g) {
+  int cur = A_P;
+  cfd_status s = enq_vcycle(g, 0, mg_depth(g), &cur);
+  if (s != CFD_OK || cur == A_P) return s;
+  CK(g, launch_copy(make_launch(g), g->scfg, cur, A_P));
+  g->launches += 1;
+  return CFD_OK;
+}
+
+// One V-cycle as a CUDA graph (captured once per configuration) and its
+// replay: the coarse levels are many small launches.
+cfd_status enq_vcycle_graph(cfd_grid* g) {
+  if (!g->mg_valid) {
+    if (g->mg_exec) {
+      cudaGraphExecDestroy(g->mg_exec);
+      g->mg_exec = nullptr;
+    }
+    CK(g, cudaStreamBeginCapture(g->own, cudaStreamCaptureModeThreadLocal));
+    const long long before = g->launches;
+    const cfd_status s = enq_vcycle_p(g);
+    cudaGraph_t graph = nullptr;
+    cudaError_t e = cudaStreamEndCapture(g->own, &graph);
+    if (s != CFD_OK) {
+      if (graph) cudaGraphDestroy(graph);
+      return s;
+    }
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaStreamEndCapture");
+    e = cudaGraphInstantiate(&g->mg_exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (e != cudaSuccess) return cuda_fail(g, e, "cudaGraphInstantiate");
+    g->mg_nodes = g->launches - before;
+    g->launches = before;
+    g->mg_valid = true;
+  }
+  CK(g, cudaGraphLaunch(g->mg_exec, g->own));
+  g->launches += g->mg_nodes;
+  return CFD_OK;
 }
 
 cfd_status run_reduce(cfd_grid* g, int mode, int set, double out[4]) {
@@ -637,6 +731,7 @@ cfd_status run_reduce(cfd_grid* g, int mode, int set, double out[4]) {
 
 void invalidate_graph(cfd_grid* g) {
   g->graph_valid = false;
+  g->mg_valid = false;
   drop_seg_graphs(g);
 }
 
@@ -1081,7 +1176,7 @@ cfd_status cfd_mg_vcycles(cfd_grid* g, int cycles) {
   if (cycles < 0) return fail(CFD_EINVAL, "cycles must be >= 0");
   if ((s = join_in(g)) != CFD_OK) return s;
   for (int c = 0; c < cycles; ++c)
-    if ((s = enq_vcycle(g, 0, mg_depth(g))) != CFD_OK) return s;
+    if ((s = enq_vcycle_graph(g)) != CFD_OK) return s;
   return join_out(g);
 }
 
@@ -1102,7 +1197,7 @@ cfd_status cfd_pressure_solve_mg(cfd_grid* g, double c_dt, double rtol, int max_
   double res = std::sqrt(out[0]);
   int done = 0;
   while (!(res <= target) && done < max_cycles) {
-    if ((s = enq_vcycle(g, 0, mg_depth(g))) != CFD_OK) return s;
+    if ((s = enq_vcycle_graph(g)) != CFD_OK) return s;
     ++done;
     if ((s = run_reduce(g, 1, 0, out)) != CFD_OK) return s;
     res = std::sqrt(out[0]);

@@ -44,6 +44,16 @@ __device__ __forceinline__ bool ff_gt(FF x, FF y) {
 
 __device__ __forceinline__ double ff_to_double(FF x) { return (double)x.hi + (double)x.lo; }
 
+// x^2 of a float-float value: hi^2 exact (TwoProd) plus 2 hi lo (lo^2 is
+// below the result's precision).  Exact-product range: |hi| < kFFSquareMax.
+constexpr float kFFSquareMax = 1e18f;
+__device__ __forceinline__ FF ff_square(FF x) {
+  if (!(fabsf(x.hi) < kFFSquareMax)) return FF{0.f, 0.f};  // the caller takes it in FP64
+  FF s = ff_two_prod(x.hi, x.hi);
+  s.lo = __fmaf_rn(2.f * x.hi, x.lo, s.lo);
+  return ff_fast_two_sum(s.hi, s.lo);
+}
+
 // Per-cell contributions of a MAC velocity (x[c] at the cell's + faces,
 // xm[c] at its - faces) to sum |u|^2 and to the divergence
 // sum_c (x[c] - xm[c]) ih[c]: the squares and differences are exact, the

@@ -1326,8 +1326,8 @@ __device__ __forceinline__ void block_reduce4(double (&v)[4], double (*sh)[4]) {
 // mode 0: sum |u|^2, max |u_d|, max |D u| and the non-finite count of a
 // velocity set; the per-cell work is float-float, each thread's column sum
 // (at most zc cells) is added to an FP64 accumulator.  mode 1: sum of
-// (L p - r)^2, the residual per cell in float-float, the squares summed in
-// FP64.  mode 2: sum of r^2 in FP64.
+// (L p - r)^2, the residual per cell in float-float, its square in
+// float-float, the same column sums.  mode 2: sum of r^2, likewise.
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, Set3 set,
                                                     int p_arr, int r_arr, double* partials) {
@@ -1375,7 +1375,12 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
     } else if (mode == 1) {
       // e = L p - r per cell in float-float (the sums and differences of
       // the FP32 values exact, the products by 1/h^2 with their rounding
-      // error kept), e^2 accumulated in FP64
+      // error kept), e^2 in float-float summed over the column, each
+      // column's sum added to an FP64 accumulator (FP64 issues at a small
+      // fraction of the FP32 rate here, so it is kept out of the per-cell
+      // work); cells whose square would leave the FP32 range go to FP64
+      FF col = {0.f, 0.f};
+      double big = 0.0;
       const T* P = base + B.org[p_arr] + o0;
       const T* Rr = base + B.org[r_arr] + o0;
       const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
@@ -1392,25 +1397,32 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
           t.lo = __fmaf_rn(sec.lo, ih2[d], t.lo);
           lp = d == 0 ? ff_fast_two_sum(t.hi, t.lo) : ff_add(lp, t);
         }
-        const double e = ff_to_double(ff_add(lp, FF{-ldf<T>(Rr + o), 0.f}));
-        acc[0] += e * e;
-        if (!isfinite(e)) acc[3] += 1.0;
+        const FF e = ff_add(lp, FF{-ldf<T>(Rr + o), 0.f});
+        col = ff_add(col, ff_square(e));
+        if (fabsf(e.hi) >= kFFSquareMax) big += (double)e.hi * e.hi;
+        bad += !isfinite(e.hi);
       }
+      acc[0] += ff_to_double(col) + big;
     } else {
-      // sum of r^2 (the norm the converged solve measures against)
+      // sum of r^2 (the norm the converged solve measures against), the
+      // same float-float column sums
+      FF col = {0.f, 0.f};
+      double big = 0.0;
       const T* Rr = base + B.org[r_arr] + o0;
       for (int q = 0; q < kn; ++q) {
-        const double rv = ldf<T>(Rr + (long long)q * pz);
-        acc[0] += rv * rv;
-        if (!isfinite(rv)) acc[3] += 1.0;
+        const float rv = ldf<T>(Rr + (long long)q * pz);
+        col = ff_add(col, ff_square(FF{rv, 0.f}));
+        if (fabsf(rv) >= kFFSquareMax) big += (double)rv * rv;
+        bad += !isfinite(rv);
       }
+      acc[0] += ff_to_double(col) + big;
     }
   }
   if (mode == 0) {
     acc[1] = umax;
     acc[2] = ff_to_double(dmax);
-    acc[3] = bad;
   }
+  acc[3] = bad;
   block_reduce4<32 * TY>(acc, sh);
   if (threadIdx.x == 0 && threadIdx.y == 0) {
 #pragma unroll

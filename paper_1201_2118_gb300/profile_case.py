@@ -10,6 +10,9 @@ given Jacobi variant (kind,vx,ty,zc,stages) runs the requested number of
 sweeps on the grid's stream, then checks the device error flag.  With
 --stages N it runs N RHS + stage-2 combines per stencil variant
 (ty,zc,tile_tz) instead (--order 2 or 4, --form advective or flux).  With
+--vcycles N it runs N multigrid V-cycles (V(2,2), all levels) on the
+pressure equation with R = D U / 1e-3 from the cavity noise, the fine level
+smoothed by the first --jacobi variant (default: the grid's).  With
 --time, each variant first runs 4 warm-up sweeps and the timed sweeps are
 bracketed by CUDA events on the grid's stream; the line printed per variant
 gives microseconds per sweep and the algorithmic bytes (read p and r, write
@@ -32,6 +35,8 @@ def main(argv=None):
     ap.add_argument("--stencil", nargs="*", default=[], help="ty,zc,tile_tz ...")
     ap.add_argument("--order", type=int, default=2, choices=[2, 4])
     ap.add_argument("--form", default="advective", choices=["advective", "flux"])
+    ap.add_argument("--vcycles", type=int, default=0,
+                    help="instead of sweeps: this many multigrid V-cycles")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -48,6 +53,28 @@ def main(argv=None):
     g.upload(workloads.ldc_noise(n, seed=1))
     g.pressure_solve(1e-3, 0)
     es = 4 if a.dtype == "f32" else 2
+    if a.vcycles:
+        from paper_1201_2118_gb300 import P, U, V, W, WU, WV, WW, mask
+        if a.jacobi:
+            g.set_kernel_config(jacobi=tuple(int(x) for x in a.jacobi[0].split(",")))
+        with torch.cuda.stream(s):
+            for x, y in ((U, WU), (V, WV), (W, WW)):
+                g.interior(y).copy_(g.interior(x))
+            g.interior(P).zero_()
+        g.ghost_fill(mask(WU, WV, WW, P))
+        g.pressure_solve(1e-3, 0)
+        g.mg_vcycles(1)  # captures the cycle's graph
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(s)
+        g.mg_vcycles(a.vcycles)
+        e1.record(s)
+        torch.cuda.synchronize()
+        print("%d^3 %s jacobi %s levels %d: %.3f ms per V-cycle" %
+              (n, a.dtype, g.kernel_config()[0], g.multigrid_levels(),
+               e0.elapsed_time(e1) / a.vcycles), flush=True)
+        g.check()
+        return
     if a.stages:
         from paper_1201_2118_gb300 import SET_U, SET_U1, SET_W
         for c in a.stencil or [None]:

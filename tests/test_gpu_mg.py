@@ -64,13 +64,37 @@ def test_mg_with_each_fine_smoother(jacobi):
     assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
 
 
-def test_mg_cycle_parameters():
+@pytest.mark.parametrize("dims,levels,nu1,nu2", [((48, 32, 64), 2, 1, 3),
+                                                 ((128, 64, 32), 1, 2, 1),
+                                                 ((96, 32, 64), 0, 0, 2)])
+def test_mg_cycle_parameters(dims, levels, nu1, nu2):
+    """Partial hierarchies (the one-CTA bottom covering only the coarsest
+    level, or not used at all), odd sweep counts, no pre-smoothing."""
     from paper_1201_2118_gb300 import P
-    dims = (48, 32, 64)
     o, grid, p, r = _setup(dims, "periodic", 3, h=(0.02, 0.025, 0.03))
-    grid.set_multigrid(2, 1, 3, 40, 0.8)
+    grid.set_multigrid(levels, nu1, nu2, 40, 0.8)
     grid.mg_vcycles(2)
-    o.mg_vcycle(p, r, 2, nu1=1, nu2=3, ncoarse=40, omega=0.8, cycles=2)
+    o.mg_vcycle(p, r, levels or o.mg_max_levels(), nu1=nu1, nu2=nu2, ncoarse=40, omega=0.8,
+                cycles=2)
+    assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
+
+
+def test_mg_ghost_width_2():
+    from oracle import Oracle
+    from paper_1201_2118_gb300 import Grid, P, R, mask
+    dims = (64, 32, 32)
+    h = (0.03, 0.03, 0.03)
+    o = Oracle(dims, ghost=2, h=h)
+    grid = Grid(dims, ghost=2, h=h)
+    grid.fill(float("nan"))
+    r = np.random.default_rng(9).uniform(-1, 1, dims[::-1])
+    r = rounded({"r": r - r.mean()})["r"]
+    grid.interior(R).copy_(grid.torch.from_numpy(r).float().cuda())
+    grid.interior(P).zero_()
+    grid.ghost_fill(mask(P))
+    p = o.ghost_fill(o.zeros(), 3)
+    grid.mg_vcycles(2)
+    o.mg_vcycle(p, o.embed(r), o.mg_max_levels(), cycles=2)
     assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
 
 
