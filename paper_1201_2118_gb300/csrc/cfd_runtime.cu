@@ -514,9 +514,9 @@ cfd_status enq_solve(cfd_grid* g, double c_dt, int iters) {
   return enq_sweeps(g, iters, g->omega);
 }
 
-cfd_status enq_project(cfd_grid* g, double c_dt, int os) {
+cfd_status enq_project(cfd_grid* g, double c_dt, int os, int p_arr = A_P) {
   cfd_status s = each_launch(g, [&](const Launch& L) {
-    return launch_project(L, g->scfg, kSets[CFD_SET_W], A_P, (float)c_dt, kSets[os]);
+    return launch_project(L, g->scfg, kSets[CFD_SET_W], p_arr, (float)c_dt, kSets[os]);
   });
   if (s != CFD_OK) return s;
   return enq_ghost(g, set_mask(os));
@@ -524,27 +524,49 @@ cfd_status enq_project(cfd_grid* g, double c_dt, int os) {
 
 cfd_status enq_vcycle_p(cfd_grid* g);
 
-// The pressure solve of a step's stage: K Jacobi sweeps, or V-cycles.
-cfd_status enq_stage_solve(cfd_grid* g, double c_dt) {
-  if (g->solver != CFD_SOLVER_MG) return enq_solve(g, c_dt, g->iters);
+// The pressure solve of a step's stage from the pressure in 'start' (P or
+// P2): K Jacobi sweeps, or V-cycles; *end receives the array holding the
+// result (the V-cycles keep it in P).
+cfd_status enq_stage_solve(cfd_grid* g, double c_dt, int start, int* end) {
+  if (g->solver != CFD_SOLVER_MG) {
+    cfd_status s = enq_solve(g, c_dt, 0);
+    return s != CFD_OK ? s : enq_sweeps(g, g->iters, g->omega, start, end);
+  }
+  if (start != A_P) {
+    CK(g, launch_copy(make_launch(g), g->scfg, start, A_P));
+    g->launches += 1;
+  }
   cfd_status s = enq_solve(g, c_dt, 0);
   for (int c = 0; c < g->mg_cycles && s == CFD_OK; ++c) s = enq_vcycle_p(g);
+  *end = A_P;
   return s;
 }
 
-cfd_status enq_rk_stage(cfd_grid* g, int stage, double dt) {
+// One projected Heun stage.  pcur: the array holding the pressure on entry,
+// updated to the one holding it on exit (a step's second stage starts from
+// where the first left it, so an odd number of ping-pong launches per solve
+// needs no copy); with pcur == nullptr the pressure starts and ends in P.
+cfd_status enq_rk_stage(cfd_grid* g, int stage, double dt, int* pcur = nullptr) {
   cfd_status s;
+  int cur = pcur ? *pcur : A_P;
+  const double cdt = stage == 1 ? dt : 0.5 * dt;
   if (stage == 1) {
-    if ((s = enq_ghost(g, set_mask(CFD_SET_U) | (1u << A_P))) != CFD_OK) return s;
+    if ((s = enq_ghost(g, set_mask(CFD_SET_U) | (1u << cur))) != CFD_OK) return s;
     if ((s = enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, dt, CFD_SET_W)) != CFD_OK) return s;
-    if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
-    if ((s = enq_stage_solve(g, dt)) != CFD_OK) return s;
-    return enq_project(g, dt, CFD_SET_U1);
+  } else {
+    if ((s = enq_stage(g, 0.5, CFD_SET_U, 0.5, CFD_SET_U1, 0.5 * dt, CFD_SET_W)) != CFD_OK)
+      return s;
   }
-  if ((s = enq_stage(g, 0.5, CFD_SET_U, 0.5, CFD_SET_U1, 0.5 * dt, CFD_SET_W)) != CFD_OK) return s;
   if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
-  if ((s = enq_stage_solve(g, 0.5 * dt)) != CFD_OK) return s;
-  return enq_project(g, 0.5 * dt, CFD_SET_U);
+  if ((s = enq_stage_solve(g, cdt, cur, &cur)) != CFD_OK) return s;
+  if ((s = enq_project(g, cdt, stage == 1 ? CFD_SET_U1 : CFD_SET_U, cur)) != CFD_OK) return s;
+  if (pcur) {
+    *pcur = cur;
+  } else if (cur != A_P) {
+    CK(g, launch_copy(make_launch(g), g->scfg, cur, A_P));
+    g->launches += 1;
+  }
+  return CFD_OK;
 }
 
 // ------------------------------------------------------------- multigrid
@@ -1511,8 +1533,14 @@ cfd_status ensure_step_graph(cfd_grid* g, double dt) {
   }
   CK(g, cudaStreamBeginCapture(g->own, cudaStreamCaptureModeThreadLocal));
   const long long before = g->launches;
-  cfd_status s1 = enq_rk_stage(g, 1, dt);
-  cfd_status s2 = s1 == CFD_OK ? enq_rk_stage(g, 2, dt) : s1;
+  int pcur = A_P;  // the step leaves the pressure in P
+  cfd_status s1 = enq_rk_stage(g, 1, dt, &pcur);
+  cfd_status s2 = s1 == CFD_OK ? enq_rk_stage(g, 2, dt, &pcur) : s1;
+  if (s2 == CFD_OK && pcur != A_P) {
+    const cudaError_t ce = launch_copy(make_launch(g), g->scfg, pcur, A_P);
+    g->launches += 1;
+    if (ce != cudaSuccess) s2 = cuda_fail(g, ce, "launch_copy");
+  }
   cudaGraph_t graph = nullptr;
   cudaError_t e = cudaStreamEndCapture(g->own, &graph);
   if (s2 != CFD_OK) {

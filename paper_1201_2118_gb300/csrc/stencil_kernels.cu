@@ -1323,6 +1323,8 @@ __device__ __forceinline__ void block_reduce4(double (&v)[4], double (*sh)[4]) {
   }
 }
 
+// The column loops are unrolled four deep so that several cells' loads are
+// in flight per thread (each thread walks zc cells of one column).
 // mode 0: sum |u|^2, max |u_d|, max |D u| and the non-finite count of a
 // velocity set; the per-cell work is float-float, each thread's column sum
 // (at most zc cells) is added to an FP64 accumulator.  mode 1: sum of
@@ -1356,6 +1358,7 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
                        base + B.org[set.a[2]] + o0};
       const long long back[3] = {1, py, pz};
       FF col = {0.f, 0.f};
+#pragma unroll 4
       for (int q = 0; q < kn; ++q) {
         const long long o = (long long)q * pz;
         float x[3], xm[3];
@@ -1385,6 +1388,7 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
       const T* Rr = base + B.org[r_arr] + o0;
       const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
       const long long step[3] = {1, py, pz};
+#pragma unroll 4
       for (int q = 0; q < kn; ++q) {
         const long long o = (long long)q * pz;
         const float pc = ldf<T>(P + o);
@@ -1409,6 +1413,7 @@ __global__ void __launch_bounds__(32 * TY) k_reduce(Launch L, int zc, int mode, 
       FF col = {0.f, 0.f};
       double big = 0.0;
       const T* Rr = base + B.org[r_arr] + o0;
+#pragma unroll 4
       for (int q = 0; q < kn; ++q) {
         const float rv = ldf<T>(Rr + (long long)q * pz);
         col = ff_add(col, ff_square(FF{rv, 0.f}));
