@@ -32,11 +32,16 @@ def make_pair(dims, ghost=1, h=None, bc="periodic", nu=0.01, order=2, iters=50, 
     from paper_1201_2118_gb300 import Grid
     if h is None:
         h = tuple(2 * math.pi / d for d in dims) if bc == "periodic" else tuple(1.0 / d for d in dims)
+    # (a face table gets h = 1 / n as well)
     o = Oracle(dims, ghost=ghost, h=h, bc=bc, nu=nu, order=order, omega=omega, lid=lid, form=form)
     g = Grid(dims, ghost=ghost, h=h, dtype=dtype)
     g.fill(float("nan"))
-    if bc == "cavity":
-        g.set_cavity(lid)
+    if isinstance(bc, str):
+        if bc == "cavity":
+            g.set_cavity(lid)
+    else:  # a face table [(kind, wall velocity), ...] for faces -x, +x, -y, +y, -z, +z
+        for f, (kind, vel) in enumerate(bc):
+            g.set_bc(f, kind, vel)
     g.set_params(nu, iters, omega, order)
     g.set_advection(form)
     f = rounded(fields, dtype)
@@ -60,6 +65,13 @@ def compare_state(o, g, u, p, tol_u, tol_p=None, tag=""):
     if tol_p is not None:
         assert errs["p"] <= tol_p, (tag, errs)
     return errs
+
+
+def channel_faces(lid=1.0):
+    """Periodic in x and z, walls at the y faces, the +y wall moving in x."""
+    from oracle import PERIODIC, WALL
+    return [(PERIODIC, (0.0, 0.0, 0.0))] * 2 + [(WALL, (0.0, 0.0, 0.0)), (WALL, (lid, 0.0, 0.0))] + \
+        [(PERIODIC, (0.0, 0.0, 0.0))] * 2
 
 
 def tg_fields(dims, h=None):

@@ -299,3 +299,73 @@ def test_nan_watchdog_and_errors():
         grid.set_params(-1.0)
     assert e.value.status == 1
     grid.check()
+
+
+@pytest.mark.parametrize("dims,ghost", [((2, 3, 2), 1), ((4, 4, 5), 2), ((2, 2, 2), 1)])
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+def test_degenerate_small_grids_step(dims, ghost, bc):
+    """The smallest grids the ghost width allows (two cells on an axis, a
+    periodic neighbour that is the cell itself one over): one step and three
+    more against the oracle, ghosts included in the comparison's inputs."""
+    rng = np.random.default_rng(21)
+    fl = {c: rng.uniform(-1, 1, dims[::-1]) for c in "uvwp"}
+    o, grid, u, p = make_pair(dims, ghost=ghost, bc=bc, nu=0.05, fields=fl, iters=7,
+                              order=2 * ghost)
+    dt = 0.05 * min(o.h)
+    grid.step(dt, 1)
+    o.rk2_step(u, p, dt, 7)
+    compare_state(o, grid, u, p, 1e-5, 1e-5, "small step 1")
+    grid.step(dt, 3)
+    o.run(u, p, dt, 7, 3)
+    compare_state(o, grid, u, p, 1e-4, 1e-3, "small step 4")
+
+
+def test_cavity_full_run_32():
+    """The cavity case over a whole run (Re 1000, CFL 0.2, 1000 steps at 32^3)
+    against the oracle at the full-run bar (1e-3), with the invariants the
+    scheme keeps: wall-normal face values exactly 0 and no net mass flux."""
+    n, steps = 32, 1000
+    h = (1.0 / n,) * 3
+    dt = workloads.cfl_dt(h)
+    o, grid, u, p = make_pair((n, n, n), bc="cavity", h=h, nu=1e-3,
+                              fields=workloads.ldc_noise(n, seed=1))
+    grid.step(dt, steps)
+    o.run(u, p, dt, 50, steps)
+    errs = compare_state(o, grid, u, p, 1e-3, 1e-3, "ldc32 step %d" % steps)
+    from paper_1201_2118_gb300 import U, V, W
+    gu, gv, gw = grid.download(U), grid.download(V), grid.download(W)
+    assert (gu[:, :, -1] == 0).all() and (gv[:, -1, :] == 0).all() and (gw[-1, :, :] == 0).all()
+    div = ((gu - np.pad(gu, ((0, 0), (0, 0), (1, 0)))[:, :, :-1]) / h[0] +
+           (gv - np.pad(gv, ((0, 0), (1, 0), (0, 0)))[:, :-1, :]) / h[1] +
+           (gw - np.pad(gw, ((1, 0), (0, 0), (0, 0)))[:-1, :, :]) / h[2])
+    assert abs(div.sum()) * h[0] * h[1] * h[2] < 1e-6
+    print("ldc32 errors after %d steps" % steps, errs)
+
+
+def test_cavity_256_first_steps():
+    """The 256^3 cavity workload itself: the first two steps against the
+    oracle.  u, v and p at the one-step bar (1e-5).  w is the 1e-3 seeded
+    noise alone while the lid drives p to O(1): the projection changes w by
+    dt dp/dz, and storing p in FP32 already costs ulp(max|p|) dt / h_z in
+    absolute terms (one ulp of each of the two values differenced, and as
+    much again from the solve's own last-place error), so e(w) is held to
+    four times ulp(max|p|) dt / h_z over max|w| (about 3.2e-5 at this step)
+    where that exceeds 1e-5."""
+    from paper_1201_2118_gb300 import P, W
+    n = 256
+    h = (1.0 / n,) * 3
+    dt = workloads.cfl_dt(h)
+    o, grid, u, p = make_pair((n, n, n), bc="cavity", h=h, nu=1e-3,
+                              fields=workloads.ldc_noise(n, seed=1))
+    for step, tol_p in ((1, 1e-5), (2, 1e-4)):
+        grid.step(dt, 1)
+        o.rk2_step(u, p, dt, 50)
+        errs = {c: rel_err(grid.download(a), o.interior(u[k]))
+                for k, (c, a) in enumerate(zip("uv", (0, 1)))}
+        assert max(errs.values()) < 1e-5, (step, errs)
+        pmax = np.abs(o.interior(p)).max()
+        floor = 4 * np.spacing(np.float32(pmax)) * dt / h[2] / np.abs(o.interior(u[2])).max()
+        ew = rel_err(grid.download(W), o.interior(u[2]))
+        assert ew < max(1e-5, floor), (step, ew, floor)
+        assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < tol_p
+        print("ldc256 step", step, errs, "w", ew, "w floor", floor)
