@@ -582,6 +582,27 @@ def run_gpu(a):
                                 % (sms, clk_summary["sm_mhz"])}
     roofline["issue"] = issue
 
+    # the plain sweep (one weighted Jacobi sweep per launch, the TMA-staged
+    # kernel) on the same grid, for the single-sweep roofline fraction
+    if a.dtype == "f32" and fused:
+        plain_cfg = (1, 4, 16, 16, 4)
+        g.set_kernel_config(jacobi=plain_cfg)
+        g.jacobi(4)
+        torch.cuda.synchronize()
+        p0, p1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        p0.record(stream)
+        g.jacobi(40)
+        p1.record(stream)
+        torch.cuda.synchronize()
+        plain_ms = p0.elapsed_time(p1) / 40
+        roofline["plain_sweep"] = {"kernel": "k_jacobi_tma, config %s" % list(plain_cfg),
+                                   "launch_ms": plain_ms,
+                                   "achieved": bytes_per_launch / (plain_ms * 1e-3) / 1e9,
+                                   "frac": bytes_per_launch / (plain_ms * 1e-3) / 1e9 / peak}
+        g.set_kernel_config(jacobi=jcfg[0])
+        g.step(dt, 1)  # re-captures the step graph outside any timed region
+        torch.cuda.synchronize()
+
     # ---- end to end through the C ABI with pinned host buffers
     e2e = None
     if not a.no_e2e:
