@@ -353,6 +353,9 @@ cfd_status common_init(cfd_grid* g, int ghost, const double h[3], int storage, v
     for (int d = 0; d < 3; ++d) g->hn[3 * b + d] = g->hb[b].n[d];
   g->jcfg = JacobiCfg{0, 4, 8, 32, 4};
   plan_layout(g);
+  for (int b = 0; b < g->nblocks; ++b)  // the ghost kernel indexes a block's ghost cells in 32 bits
+    if (g->ghost_prefix[b + 1] - g->ghost_prefix[b] >= (1LL << 31))
+      return fail(CFD_EINVAL, "block %d has too many ghost cells (>= 2^31)", b);
   if (!g->mgl.empty() && (e = prepare_mg_bottom()) != cudaSuccess)
     return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
   return CFD_OK;

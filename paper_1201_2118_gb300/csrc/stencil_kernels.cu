@@ -43,12 +43,12 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, GhostArrays ga, const l
   }
   __syncthreads();
   const int g = L.ghost;
-  const long long all = total * ga.n;
-  for (long long tt = (long long)blockIdx.x * blockDim.x + threadIdx.x; tt < all;
-       tt += (long long)gridDim.x * blockDim.x) {
-    const int arr = ga.arr[tt / total];
-    const long long t = tt % total;
-    const int kind = array_kind(arr);
+  // one thread per ghost cell of the block set; the cell's position and its
+  // source (block and cell, walls met on the way) are found once and serve
+  // every array of the launch.  A block's ghost cells number below 2^31
+  // (checked at grid creation), so the per-block index arithmetic is 32-bit.
+  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
+       t += (long long)gridDim.x * blockDim.x) {
     // block of this ghost cell (binary search over the prefix sums)
     int lo = 0, hi = L.nblocks - 1;
     while (lo < hi) {
@@ -58,33 +58,35 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, GhostArrays ga, const l
     const int b = lo;
     const BlockDev& B = sb[b];
     const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
-    const long long ex = nx + 2 * g, ey = ny + 2 * g;
-    long long l = t - spre[b];
+    const unsigned ex = nx + 2 * g, ey = ny + 2 * g;
+    unsigned l = (unsigned)(t - spre[b]);
     int q[3];
-    const long long zc = 2LL * g * ey * ex, yc = 2LL * g * nz * ex;
+    const unsigned zc = 2u * g * ey * ex, yc = 2u * g * nz * ex;
     if (l < zc) {
       const int s2 = (int)(l / (ey * ex));
-      const long long rem = l % (ey * ex);
+      const unsigned rem = l % (ey * ex);
       q[2] = s2 < g ? s2 - g : nz + s2 - g;
       q[1] = (int)(rem / ex) - g;
       q[0] = (int)(rem % ex) - g;
     } else if ((l -= zc) < yc) {
       const int s2 = (int)(l / (nz * ex));
-      const long long rem = l % (nz * ex);
+      const unsigned rem = l % (nz * ex);
       q[1] = s2 < g ? s2 - g : ny + s2 - g;
       q[2] = (int)(rem / ex);
       q[0] = (int)(rem % ex) - g;
     } else {
       l -= yc;
-      const int s2 = (int)(l / ((long long)nz * ny));
-      const long long rem = l % ((long long)nz * ny);
+      const int s2 = (int)(l / ((unsigned)nz * ny));
+      const unsigned rem = l % ((unsigned)nz * ny);
       q[0] = s2 < g ? s2 - g : nx + s2 - g;
       q[2] = (int)(rem / ny);
       q[1] = (int)(rem % ny);
     }
     const int dst[3] = {q[0], q[1], q[2]};
+    // source cell: axis by axis, across a periodic/neighbour face to the
+    // neighbouring block, or mirrored at a wall (recorded for the rules)
     int sbk = b;
-    float A = 0.f, S = 1.f;
+    int wface[3] = {-1, -1, -1}, wblk[3] = {0, 0, 0};
 #pragma unroll
     for (int d = 0; d < 3; ++d) {
       const BlockDev& C = sb[sbk];
@@ -98,22 +100,39 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, GhostArrays ga, const l
         sbk = nb;
       } else {
         q[d] = low ? -1 - q[d] : 2 * N - 1 - q[d];
+        wface[d] = face;
+        wblk[d] = sbk;
+      }
+    }
+    const BlockDev& Sd = sb[sbk];
+    const long long so = (long long)q[2] * Sd.pz + (long long)q[1] * Sd.py + q[0];
+    const long long dof = (long long)dst[2] * B.pz + (long long)dst[1] * B.py + dst[0];
+    // every array's source value first, then the stores: a load after a
+    // store through the same base pointer would wait behind it
+    float src[kNumArrays];
+#pragma unroll
+    for (int ai = 0; ai < kNumArrays; ++ai)
+      if (ai < ga.n) src[ai] = ldf<T>(reinterpret_cast<const T*>(L.base) + Sd.org[ga.arr[ai]] + so);
+#pragma unroll
+    for (int ai = 0; ai < kNumArrays; ++ai) {
+      if (ai >= ga.n) break;
+      const int arr = ga.arr[ai];
+      const int kind = array_kind(arr);
+      // the wall rules compose as affine maps v -> A + S v, axis by axis
+      float A = 0.f, S = 1.f;
+#pragma unroll
+      for (int d = 0; d < 3; ++d) {
+        if (wface[d] < 0) continue;
         float a, s1;
         if (kind == 3) { a = 0.f; s1 = 1.f; }
         else if (kind == d) { a = 0.f; s1 = 0.f; }
-        else { a = 2.f * C.wall[face][kind]; s1 = -1.f; }
+        else { a = 2.f * sb[wblk[d]].wall[wface[d]][kind]; s1 = -1.f; }
         A = a + s1 * A;
         S = s1 * S;
       }
+      const float v = S != 0.f ? A + S * src[ai] : A;
+      reinterpret_cast<T*>(L.base)[B.org[arr] + dof] = cvt<T>(v);
     }
-    float v = A;
-    if (S != 0.f) {
-      const BlockDev& Sd = sb[sbk];
-      v += S * ldf<T>(reinterpret_cast<const T*>(L.base) + Sd.org[arr] + (long long)q[2] * Sd.pz +
-                      (long long)q[1] * Sd.py + q[0]);
-    }
-    T* out = reinterpret_cast<T*>(L.base) + B.org[arr];
-    out[(long long)dst[2] * B.pz + (long long)dst[1] * B.py + dst[0]] = cvt<T>(v);
   }
 }
 
@@ -751,18 +770,26 @@ __device__ __forceinline__ void cp_async4_s(uint32_t saddr, const void* gmem) {
   asm volatile("cp.async.ca.shared.global [%0], [%1], 4;" ::"r"(saddr), "l"(gmem));
 }
 
-// Copies of plane kk of u, v, w (this thread's share) into its ring slot,
-// then one commit group (empty past the last plane, so that "all but the
-// newest D groups" always means the same planes).
-template <int NL, int R, int PL>
-__device__ __forceinline__ void stage_issue(uint32_t ring_s, const int (&soff)[NL],
-                                            const long long (&goff)[NL], const bool (&lok)[NL],
+__device__ __forceinline__ void cp_async16_s(uint32_t saddr, const void* gmem) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(saddr), "l"(gmem));
+}
+
+// Copies of plane kk of u, v, w (this thread's share: 16-byte pieces of the
+// rows' interior, 4-byte halo cells) into its ring slot, then one commit
+// group (empty past the last plane, so that "all but the newest D groups"
+// always means the same planes).  width[q]: 16, 4, or 0 (nothing to copy).
+template <int NL, int SLOT_BYTES>
+__device__ __forceinline__ void stage_issue(uint32_t ring_s, int ring_mask, const int (&soff)[NL],
+                                            const long long (&goff)[NL], const int (&width)[NL],
                                             const float* base, int kk, long long pz, bool live) {
   if (live) {
-    const uint32_t slot = ring_s + (uint32_t)((kk & (R - 1)) * (3 * PL) * 4);
+    const uint32_t slot = ring_s + (uint32_t)((kk & ring_mask) * SLOT_BYTES);
 #pragma unroll
-    for (int q = 0; q < NL; ++q)
-      if (lok[q]) cp_async4_s(slot + 4u * soff[q], base + goff[q] + (long long)kk * pz);
+    for (int q = 0; q < NL; ++q) {
+      const float* src = base + goff[q] + (long long)kk * pz;
+      if (width[q] == 16) cp_async16_s(slot + soff[q], src);
+      else if (width[q] == 4) cp_async4_s(slot + soff[q], src);
+    }
   }
   cp_commit_group();
 }
@@ -780,12 +807,18 @@ __global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float
                                                          float nu) {
   constexpr int H = scheme_halo(SCH);
   constexpr int D = 2;  // planes in flight beyond k + H
-  constexpr int SX = 32 + 2 * H, SY = TY + 2 * H, PL = SX * SY;
+  // a ring row holds x = i0 - XP .. i0 + 31 + XP: the 32 interior cells start
+  // 16-byte aligned (column XP), so they arrive as eight 16-byte copies; the
+  // H halo cells on each side as 4-byte copies
+  constexpr int XP = 4;
+  constexpr int SX = 32 + 2 * XP, SY = TY + 2 * H, PL = SX * SY;
   constexpr int R = 8;  // >= 2H + 1 + D and a power of two
-  static_assert(2 * H + 1 + D <= R, "ring too small");
+  static_assert(2 * H + 1 + D <= R && H <= XP, "ring too small");
   constexpr int NT = 32 * TY;
-  constexpr int NL = (3 * PL + NT - 1) / NT;
-  __shared__ float ring[R * 3 * PL];
+  constexpr int U = 8 + 2 * H;  // copies per row
+  constexpr int NU = 3 * SY * U;
+  constexpr int NL = (NU + NT - 1) / NT;
+  __shared__ __align__(16) float ring[R * 3 * PL];
   __shared__ TileTable tt;
   tile_table_build(tt, L, 32, TY, zc);
   const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
@@ -802,18 +835,25 @@ __global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float
     const int py = B.py;
     const long long pz = B.pz;
     const int k1 = min(k0 + zc, nz);
-    int soff[NL];
+    // this thread's copies of a plane: ring byte offset, field offset
+    // (plane 0) and width.  A copy starting beyond the allocated extent
+    // (partial tiles) is dropped; a 16-byte piece that starts inside may
+    // run up to 3 cells past the row's last allocated cell, which stays
+    // inside the arena (row pitch, or its 256-byte tail), and only threads
+    // outside the block read those cells
+    int soff[NL], width[NL];
     long long goff[NL];
-    bool lok[NL];
 #pragma unroll
     for (int q = 0; q < NL; ++q) {
       const int idx = tid + q * NT;
-      const int c = idx / PL, rem = idx % PL;
-      const int xx = rem % SX, yy = rem / SX;
-      const int i = i0 - H + xx, j = j0 - H + yy;
-      lok[q] = idx < 3 * PL && i <= nx + g - 1 && j <= ny + g - 1;
-      soff[q] = c * PL + rem;
-      goff[q] = lok[q] ? B.org[ys.a[c]] + (long long)j * py + i : 0;
+      const int c = idx / (SY * U), rem = idx % (SY * U);
+      const int yy = rem / U, cu = rem % U;
+      const int x = cu < 8 ? i0 + 4 * cu : (cu - 8 < H ? i0 - H + (cu - 8) : i0 + 32 + (cu - 8 - H));
+      const int j = j0 - H + yy;
+      const bool ok = idx < NU && x <= nx + g - 1 && j <= ny + g - 1;
+      width[q] = ok ? (cu < 8 ? 16 : 4) : 0;
+      soff[q] = 4 * (c * PL + yy * SX + XP + (x - i0));
+      goff[q] = ok ? B.org[ys.a[c]] + (long long)j * py + x : 0;
     }
     const int kmax = nz + g - 1;
     const int klast = k1 - 1 + H;  // last plane the tile reads
@@ -821,7 +861,8 @@ __global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float
     // "all but the newest D groups" always means "up to plane k + H"
     const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
     for (int kk = k0 - H; kk <= k0 + H + D - 1; ++kk)
-      stage_issue<NL, R, PL>(ring_s, soff, goff, lok, base, kk, pz, kk <= klast && kk <= kmax);
+      stage_issue<NL, 3 * PL * 4>(ring_s, R - 1, soff, goff, width, base, kk, pz,
+                                    kk <= klast && kk <= kmax);
     const int i = i0 + tx, j = j0 + ty;
     const bool mine = i < nx && j < ny;
     const bool wall[3] = {B.bc[1] == BC_WALL && i == nx - 1, B.bc[3] == BC_WALL && j == ny - 1,
@@ -832,12 +873,13 @@ __global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float
     float* O[3] = {reinterpret_cast<float*>(L.base) + B.org[os.a[0]] + o0,
                    reinterpret_cast<float*>(L.base) + B.org[os.a[1]] + o0,
                    reinterpret_cast<float*>(L.base) + B.org[os.a[2]] + o0};
-    const RingFld<SX, PL, R> f[3] = {{ring, i0 - H, j0 - H}, {ring + PL, i0 - H, j0 - H},
-                                     {ring + 2 * PL, i0 - H, j0 - H}};
+    const RingFld<SX, PL, R> f[3] = {{ring, i0 - XP, j0 - H}, {ring + PL, i0 - XP, j0 - H},
+                                     {ring + 2 * PL, i0 - XP, j0 - H}};
     for (int k = k0; k < k1; ++k) {
       {  // plane k + H + D; its slot was last read D + 1 planes ago or more
         const int kk = k + H + D;
-        stage_issue<NL, R, PL>(ring_s, soff, goff, lok, base, kk, pz, kk <= klast && kk <= kmax);
+        stage_issue<NL, 3 * PL * 4>(ring_s, R - 1, soff, goff, width, base, kk, pz,
+                                    kk <= klast && kk <= kmax);
       }
       const long long o = (long long)k * pz;
       float xv[3] = {0.f, 0.f, 0.f};
@@ -1498,8 +1540,7 @@ static cudaError_t run_ghost(const Launch& L, const GhostArrays& ga, const long 
     if (e != cudaSuccess) return e;
     set_for = smem;
   }
-  const long long work = total * ga.n;
-  long long grid = (work + 255) / 256;
+  long long grid = (total + 255) / 256;
   const long long cap = (long long)L.sms * 8;
   if (grid > cap) grid = cap;
   k_ghost<T><<<(unsigned)grid, 256, smem, L.stream>>>(L, ga, d_prefix, total);
