@@ -332,12 +332,15 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
  * single-block grids whose six faces are walls, odd sweep counts and other
  * grids take single sweeps of kind 0);
  * zc = z-planes per tile.
- * stencil = {ty in {4,8}, zc, tile_tz in {0,1,2,4}} for the point kernels:
+ * stencil = {ty in {4,8}, zc, tile_tz in {0..4}} for the point kernels:
  * rows per CTA, z chunk, and for the RHS + stage kernel either neighbour
  * reads through L1 (tile_tz 0), a z-streaming ring of shared-memory planes
- * of 32 x ty cells plus halo (tile_tz 1), or a shared-memory box of
- * 32 x 8 x tile_tz cells plus halo (2, 4).  NULL leaves a part unchanged.  Results do not depend on the
- * variant. */
+ * of 32 x ty cells plus halo (tile_tz 1), the same ring 64 cells wide with
+ * two x-neighbouring cells per thread in packed FP32x2 arithmetic (tile_tz
+ * 3: FP32 storage and order-2 schemes, 4 rows per CTA whatever ty says;
+ * elsewhere it acts as 1), or a shared-memory box of 32 x 8 x tile_tz
+ * cells plus halo (2, 4).  NULL leaves a part unchanged.  Results agree
+ * across variants to FP32 rounding (the same formula per cell). */
 cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int stencil[3]);
 cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[3]);
 

@@ -1277,7 +1277,7 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
   }
   if (stencil) {
     if ((stencil[0] != 4 && stencil[0] != 8) || stencil[1] < 1 ||
-        (stencil[2] != 0 && stencil[2] != 1 && stencil[2] != 2 && stencil[2] != 4))
+        (stencil[2] < 0 || stencil[2] > 4))
       return fail(CFD_EINVAL, "unsupported stencil config");
     g->scfg = StencilCfg{stencil[0], stencil[1], stencil[2]};
   }
@@ -1364,10 +1364,12 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
   CK(g, launch_copy(L, g->scfg, A_U1, A_P));
   StencilCfg sbest = g->scfg;
   float sbest_ms = 1e30f;
-  for (int tz : {0, 1, 2, 4})
+  const bool pair_ok = g->dtype == CFD_F32 && (g->order == 2 || g->form == CFD_FLUX);
+  for (int tz : {0, 1, 2, 3, 4})
   for (int ty : {4, 8})
     for (int zc : {8, 16, 32, 64}) {
-      if (tz == 1 && zc < 16) continue;
+      if ((tz == 1 || tz == 3) && zc < 16) continue;
+      if (tz == 3 && (ty != 4 || !pair_ok)) continue;  // the pair kernel's rows are fixed at 4
       g->scfg = StencilCfg{ty, zc, tz};
       float ms = 0.f;
       if ((s = time_region(g, 1, &ms, 1)) != CFD_OK) return s;

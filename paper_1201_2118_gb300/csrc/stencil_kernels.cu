@@ -908,6 +908,181 @@ __global__ void __launch_bounds__(32 * TY) k_stage_async(Launch L, int zc, float
   }
 }
 
+// Two x-neighbouring cells per thread (FP32, order-2 schemes): the same
+// ring as k_stage_async, 64 cells wide, and the right-hand side of
+// rhs_comp evaluated on the pair with packed f32x2 operations (one issue
+// for both cells).  A pair of values at x offsets (di, di + 1) from the
+// thread's first cell is one aligned 8-byte shared load for even di, or the
+// high and low halves of the two aligned pairs around it for odd di.
+__device__ __forceinline__ unsigned long long pair_join(unsigned long long a, unsigned long long b) {
+  float a0, a1, b0, b1;
+  unpk2(a, a0, a1);
+  unpk2(b, b0, b1);
+  return pk2(a1, b0);
+}
+
+template <int SCH, int C, typename LD>
+__device__ __forceinline__ unsigned long long rhs_pair(const LD& ld, const float (&ih)[3],
+                                                       const float (&ih2)[3], float nu) {
+  // offset (0, 0, 0) moved by o1 along axis d1 and o2 along axis d2
+  auto at = [&](int comp, int d1, int o1, int d2, int o2) {
+    int q[3] = {0, 0, 0};
+    q[d1] += o1;
+    q[d2] += o2;
+    return ld(comp, q[0], q[1], q[2]);
+  };
+  const unsigned long long f0 = at(C, 0, 0, 0, 0);
+  const unsigned long long m2 = pk2(-2.f, -2.f);
+  unsigned long long adv = pk2(0.f, 0.f), lap = pk2(0.f, 0.f);
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const unsigned long long p1 = at(C, d, 1, d, 0), m1 = at(C, d, -1, d, 0);
+    const unsigned long long second = mul2(add2(fma2(m2, f0, p1), m1), pk2(ih2[d], ih2[d]));
+    if constexpr (SCH == kSchemeFlux2) {
+      const unsigned long long ch = add2(f0, p1), cl = add2(m1, f0);
+      unsigned long long dh, dl;
+      if (d == C) {
+        dh = ch;
+        dl = cl;
+      } else {
+        dh = add2(at(d, C, 0, d, 0), at(d, C, 1, d, 0));
+        dl = add2(at(d, C, 0, d, -1), at(d, C, 1, d, -1));
+      }
+      const float q = 0.25f * ih[d];
+      adv = fma2(sub2(mul2(ch, dh), mul2(cl, dl)), pk2(q, q), adv);
+    } else {
+      const float hh = 0.5f * ih[d];
+      const unsigned long long deriv = mul2(sub2(p1, m1), pk2(hh, hh));
+      unsigned long long vel;
+      if (d == C) {
+        vel = f0;
+      } else {
+        vel = mul2(pk2(0.25f, 0.25f),
+                   add2(add2(at(d, C, 0, d, -1), at(d, C, 1, d, -1)),
+                        add2(at(d, C, 0, d, 0), at(d, C, 1, d, 0))));
+      }
+      adv = fma2(vel, deriv, adv);
+    }
+    lap = add2(lap, second);
+  }
+  return fma2(pk2(nu, nu), lap, mul2(adv, pk2(-1.f, -1.f)));
+}
+
+template <int SCH, int TY>
+__global__ void __launch_bounds__(32 * TY) k_stage_pair(Launch L, int zc, float a, Set3 xs,
+                                                        float b, Set3 ys, float cdt, Set3 os,
+                                                        float nu) {
+  static_assert(SCH == kSchemeAdv2 || SCH == kSchemeFlux2, "order-2 schemes only");
+  constexpr int H = 1;
+  constexpr int D = 2;    // planes in flight beyond k + H
+  constexpr int TX = 64;  // cells per CTA row
+  constexpr int XP = 4;   // ring column of x = i0 - XP is 0: the interior starts 16-byte aligned
+  constexpr int SX = TX + 2 * XP, SY = TY + 2 * H, PL = SX * SY;
+  constexpr int R = 8;
+  static_assert(2 * H + 1 + D <= R, "ring too small");
+  constexpr int NT = 32 * TY;
+  constexpr int U = TX / 4 + 2 * H;  // copies per row: 16-byte interior pieces, 4-byte halo cells
+  constexpr int NU = 3 * SY * U;
+  constexpr int NL = (NU + NT - 1) / NT;
+  __shared__ __align__(16) float ring[R * 3 * PL];
+  __shared__ TileTable tt;
+  tile_table_build(tt, L, TX, TY, zc);
+  const float ih[3] = {L.ih[0], L.ih[1], L.ih[2]};
+  const float ih2[3] = {L.ih2[0], L.ih2[1], L.ih2[2]};
+  const int tx = threadIdx.x, ty = threadIdx.y, tid = ty * 32 + tx;
+  const float* base = reinterpret_cast<const float*>(L.base);
+  int blk = L.b0;
+  for (long long t = blockIdx.x;; t += gridDim.x) {
+    int i0, j0, k0;
+    if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
+    const BlockDev& B = L.blocks[blk];
+    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
+    const int g = L.ghost;
+    const int py = B.py;
+    const long long pz = B.pz;
+    const int k1 = min(k0 + zc, nz);
+    // this thread's copies of a plane (as in k_stage_async)
+    int soff[NL], width[NL];
+    long long goff[NL];
+#pragma unroll
+    for (int q = 0; q < NL; ++q) {
+      const int idx = tid + q * NT;
+      const int c = idx / (SY * U), rem = idx % (SY * U);
+      const int yy = rem / U, cu = rem % U;
+      constexpr int NC = TX / 4;
+      const int x = cu < NC ? i0 + 4 * cu : (cu - NC < H ? i0 - H + (cu - NC) : i0 + TX + (cu - NC - H));
+      const int j = j0 - H + yy;
+      const bool ok = idx < NU && x <= nx + g - 1 && j <= ny + g - 1;
+      width[q] = ok ? (cu < NC ? 16 : 4) : 0;
+      soff[q] = 4 * (c * PL + yy * SX + XP + (x - i0));
+      goff[q] = ok ? B.org[ys.a[c]] + (long long)j * py + x : 0;
+    }
+    const int kmax = nz + g - 1;
+    const int klast = k1 - 1 + H;
+    const uint32_t ring_s = static_cast<uint32_t>(__cvta_generic_to_shared(ring));
+    for (int kk = k0 - H; kk <= k0 + H + D - 1; ++kk)
+      stage_issue<NL, 3 * PL * 4>(ring_s, R - 1, soff, goff, width, base, kk, pz,
+                                  kk <= klast && kk <= kmax);
+    const int i = i0 + 2 * tx, j = j0 + ty;
+    const bool mine = i < nx && j < ny;
+    const bool two = i + 1 < nx;  // the second cell of the pair is inside the block
+    const bool wall_y = B.bc[3] == BC_WALL && j == ny - 1;
+    const bool wall_z = B.bc[5] == BC_WALL;
+    // wall-normal u on the +x wall face: the last cell in x, either lane
+    const bool wx0 = B.bc[1] == BC_WALL && i == nx - 1, wx1 = B.bc[1] == BC_WALL && i + 1 == nx - 1;
+    const long long o0 = (long long)j * py + i;
+    const int cell = (ty + H) * SX + XP + 2 * tx;
+    for (int k = k0; k < k1; ++k) {
+      {
+        const int kk = k + H + D;
+        stage_issue<NL, 3 * PL * 4>(ring_s, R - 1, soff, goff, width, base, kk, pz,
+                                    kk <= klast && kk <= kmax);
+      }
+      const long long o = (long long)k * pz + o0;
+      unsigned long long xv[3] = {0ull, 0ull, 0ull};
+      if (a != 0.f && mine) {
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          const float* xp = base + B.org[xs.a[c]] + o;
+          xv[c] = two ? __ldg(reinterpret_cast<const unsigned long long*>(xp)) : pk2(__ldg(xp), 0.f);
+        }
+      }
+      cp_wait_group<D>();
+      __syncthreads();
+      if (mine) {
+        auto ld = [&](int comp, int di, int dj, int dk) -> unsigned long long {
+          const float* pl = ring + ((k + dk) & (R - 1)) * (3 * PL) + comp * PL + cell + dj * SX;
+          if ((di & 1) == 0) return *reinterpret_cast<const unsigned long long*>(pl + di);
+          return pair_join(*reinterpret_cast<const unsigned long long*>(pl + di - 1),
+                           *reinterpret_cast<const unsigned long long*>(pl + di + 1));
+        };
+        unsigned long long F[3];
+        F[0] = rhs_pair<SCH, 0>(ld, ih, ih2, nu);
+        F[1] = rhs_pair<SCH, 1>(ld, ih, ih2, nu);
+        F[2] = rhs_pair<SCH, 2>(ld, ih, ih2, nu);
+#pragma unroll
+        for (int c = 0; c < 3; ++c) {
+          unsigned long long v = fma2(pk2(cdt, cdt), F[c], mul2(pk2(b, b), ld(c, 0, 0, 0)));
+          if (a != 0.f) v = fma2(pk2(a, a), xv[c], v);
+          float v0, v1;
+          unpk2(v, v0, v1);
+          bool w0, w1;
+          if (c == 0) { w0 = wx0; w1 = wx1; }
+          else if (c == 1) { w0 = w1 = wall_y; }
+          else { w0 = w1 = wall_z && k == nz - 1; }
+          if (w0) v0 = 0.f;
+          if (w1) v1 = 0.f;
+          float* op = reinterpret_cast<float*>(L.base) + B.org[os.a[c]] + o;
+          if (two) *reinterpret_cast<unsigned long long*>(op) = pk2(v0, v1);
+          else *op = v0;
+        }
+      }
+    }
+    cp_wait_group<0>();
+    __syncthreads();
+  }
+}
+
 template <typename T, int VX, int TY, int S>
 struct AsyncGeom {
   static constexpr int TX = 32 * VX;
@@ -1595,8 +1770,17 @@ static void run_stage_ring(const Launch& L, int zc, float a, Set3 xs, float b, S
 template <int SCH>
 static cudaError_t launch_stage_s(const Launch& L, const StencilCfg& c, float a, Set3 xs, float b,
                                   Set3 ys, float cdt, Set3 os, float nu) {
+  if constexpr (SCH != kSchemeAdv4) {
+    if (c.tile_tz == 3 && L.dtype == 0) {
+      const long long tiles = count_tiles(L, 64, 4, c.zc);
+      auto kern = k_stage_pair<SCH, 4>;
+      static const int occ = occupancy(kern, 128);
+      kern<<<grid_for(L, occ, tiles), dim3(32, 4), 0, L.stream>>>(L, c.zc, a, xs, b, ys, cdt, os, nu);
+      return cudaGetLastError();
+    }
+  }
   CFD_DISPATCH_T(L.dtype, {
-    if (c.tile_tz == 1) {
+    if (c.tile_tz == 1 || c.tile_tz == 3) {
       if (c.ty == 4) run_stage_ring<T, SCH, 4>(L, c.zc, a, xs, b, ys, cdt, os, nu);
       else run_stage_ring<T, SCH, 8>(L, c.zc, a, xs, b, ys, cdt, os, nu);
     } else if (c.tile_tz == 2) {

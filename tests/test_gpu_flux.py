@@ -37,7 +37,7 @@ def _stage2(o, grid, dims, seed, dtype="f32"):
 
 
 @pytest.mark.parametrize("stencil", [(8, 16, 2), (4, 8, 4), (8, 32, 0), (4, 32, 0), (8, 32, 1),
-                                     (4, 16, 1), (8, 7, 1)])
+                                     (4, 16, 1), (8, 7, 1), (4, 32, 3), (4, 5, 3)])
 @pytest.mark.parametrize("bc", ["periodic", "cavity"])
 def test_flux_stage_variants_match_oracle(stencil, bc):
     from paper_1201_2118_gb300 import WU, WV, WW, SET_U, SET_U1, SET_W
@@ -162,8 +162,10 @@ def _wrap_box(t, start, size):
     return t.index_select(0, idx[0]).index_select(1, idx[1]).index_select(2, idx[2])
 
 
-def test_flux_full_size_sampled_boxes_and_momentum():
-    """512^3 periodic grid in one launch: sampled 6^3 boxes (interior, faces,
+@pytest.mark.parametrize("stencil", [(8, 32, 1), (4, 64, 3)])
+def test_flux_full_size_sampled_boxes_and_momentum(stencil):
+    """512^3 periodic grid in one launch (the ring kernel, and the pair kernel
+    with two cells per thread): sampled 6^3 boxes (interior, faces,
     corners of the periodic wrap) against the oracle fed the device's own
     neighbour values, and the momentum identity sum_p F_c = 0 (viscous and
     advective sums both telescope) over all 134M points of each component."""
@@ -176,6 +178,7 @@ def test_flux_full_size_sampled_boxes_and_momentum():
     grid = Grid((n, n, n), ghost=1, h=h)
     grid.set_params(nu, 10, 1.0, 2)
     grid.set_advection("flux")
+    grid.set_kernel_config(stencil=stencil)
     gen = torch.Generator(device="cuda").manual_seed(12)
     for a in (U, V, W):
         grid.interior(a).copy_(torch.rand((n, n, n), generator=gen, device="cuda") * 2 - 1)

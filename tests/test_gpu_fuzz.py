@@ -13,7 +13,8 @@ pytestmark = pytest.mark.gpu
 JACOBI = [(0, 4, 8, 32, 4), (0, 2, 4, 16, 4), (0, 1, 8, 7, 4), (1, 4, 16, 16, 4), (1, 4, 8, 32, 6),
           (1, 2, 8, 16, 4), (2, 4, 4, 2, 0), (3, 4, 4, 32, 5), (5, 4, 4, 16, 0), (7, 4, 16, 64, 8),
           (7, 2, 8, 32, 6), (9, 4, 16, 16, 6), (9, 4, 8, 7, 5)]
-STENCIL = [(8, 32, 0), (4, 16, 0), (8, 32, 1), (4, 16, 1), (8, 7, 1), (8, 16, 2), (4, 8, 4)]
+STENCIL = [(8, 32, 0), (4, 16, 0), (8, 32, 1), (4, 16, 1), (8, 7, 1), (8, 16, 2), (4, 8, 4),
+           (4, 32, 3), (4, 9, 3)]
 
 
 def _case(seed):

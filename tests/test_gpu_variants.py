@@ -232,7 +232,8 @@ def test_16bit_jacobi_variants_agree_with_register_sweep(dtype, cfg):
     assert (np.abs(a[inner] - b[inner]) <= 2 * half_ulp * np.abs(b[inner]) + 1e-30).all()
 
 
-@pytest.mark.parametrize("stencil", [(8, 16, 2), (4, 8, 4), (8, 32, 0), (8, 32, 1), (4, 16, 1), (8, 7, 1)])
+@pytest.mark.parametrize("stencil", [(8, 16, 2), (4, 8, 4), (8, 32, 0), (8, 32, 1), (4, 16, 1), (8, 7, 1),
+                                     (4, 32, 3), (4, 7, 3)])
 @pytest.mark.parametrize("order,g,bc", [(2, 1, "periodic"), (4, 2, "periodic"), (2, 1, "cavity")])
 def test_stage_variants_match_oracle(stencil, order, g, bc):
     """RHS + stage kernels (L1 neighbours or shared-memory box) against the
