@@ -94,9 +94,12 @@ cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* m
 // into the array, 1 gathers the array into the buffer.
 cudaError_t launch_pack(const Launch& L, int arr, void* compact, int to_compact);
 
-// Two sweeps per launch (kind 9), src -> dst; single block, walls on all faces.
+// Two sweeps per launch (kind 9), src -> dst; single block, walls on all
+// faces, or (periodic) all faces periodic with ghost width >= 2, src's two
+// ghost layers and R's first filled before the launch, dst's ghosts not
+// written.
 cudaError_t launch_jacobi2_ws(const Launch& L, const JacobiCfg& c, const void* maps_dev,
-                              int src_slot, int dst, float omega);
+                              int src_slot, int dst, float omega, bool periodic);
 
 long long count_tiles(const Launch& L, int tx, int ty, int tz);
 

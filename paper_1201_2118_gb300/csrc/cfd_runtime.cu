@@ -441,13 +441,21 @@ cfd_status enq_stage(cfd_grid* g, double a, int xs, double b, int ys, double c, 
   });
 }
 
+// The two-sweep kernel's periodic form: every face periodic and two ghost
+// layers (the first sweep is also taken on the first ghost layer).
+bool ws2_periodic(const cfd_grid* g) {
+  for (int f = 0; f < 6; ++f)
+    if (g->bc[f] != CFD_BC_PERIODIC) return false;
+  return g->g >= 2;
+}
+
 // Fused two-sweep launches apply (single block, tiles dividing x and y).
 bool fused_ok(const cfd_grid* g) {
   if (g->jcfg.kind == 9) {
     if (g->nblocks != 1 || !g->maps_ready) return false;
-    for (int f = 0; f < 6; ++f)
-      if (g->bdev[0].bc[f] != BC_WALL) return false;
-    return true;
+    bool walls = true;
+    for (int f = 0; f < 6; ++f) walls &= g->bdev[0].bc[f] == BC_WALL;
+    return walls || ws2_periodic(g);
   }
   return g->jcfg.kind == 5 && g->nblocks == 1 && g->hb[0].n[0] % 128 == 0 &&
          g->hb[0].n[1] % g->jcfg.ty == 0 && g->hb[0].n[1] >= 2 && g->hb[0].n[2] >= 2;
@@ -476,14 +484,20 @@ cfd_status enq_sweeps(cfd_grid* g, int iters, double omega, int start = A_P, int
   cfd_status s;
   if (fused_ok(g)) {
     const Launch L = make_launch(g);
+    // periodic two-sweep launches read two ghost layers of the iterate and
+    // one of R, and write none: fill them before the first launch and the
+    // output's after each
+    const bool per = g->jcfg.kind == 9 && ws2_periodic(g);
+    if (per && iters >= 2 && (s = enq_ghost(g, (1u << A_R) | (1u << cur))) != CFD_OK) return s;
     for (int it = 0; it + 1 < iters; it += 2) {
       if (g->jcfg.kind == 9)
         CK(g, launch_jacobi2_ws(L, g->jcfg, g->base + g->maps_off, cur == A_P ? 0 : 1, oth,
-                                om));
+                                om, per));
       else
         CK(g, launch_jacobi2(L, g->jcfg, cur, oth, A_R, om));
       g->launches += 1;
       std::swap(cur, oth);
+      if (per && (s = enq_ghost(g, 1u << cur)) != CFD_OK) return s;
     }
     if (iters % 2) {
       CK(g, sweep(g, L, cur, oth, om));

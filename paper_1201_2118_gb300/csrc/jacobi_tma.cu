@@ -482,7 +482,12 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
 // so NS1 >= 5; it is 8.  First-sweep values outside the block (walls:
 // p'_ghost = p'_face) come from the face cell: the x images are written
 // into the ring by the face cell's lane, the y and z images are selected
-// in the second sweep of face rows and planes.
+// in the second sweep of face rows and planes.  PER (every face periodic,
+// ghost width >= 2, P's two ghost layers and R's first layer filled before
+// the launch): the first sweep is taken on the ghost layer too, from the
+// wrapped copies there, which is the first sweep on the cells they copy;
+// the second sweep then needs no substitution and writes no ghost images
+// (the caller fills the output's ghosts after the launch).
 
 template <typename T, int TY>
 struct Ws2Geom {
@@ -508,7 +513,7 @@ __device__ __forceinline__ float jac_point(float c, float xm, float xp, float ym
 template <int N>
 __device__ __forceinline__ int wrapn(int x) { return x >= N ? x - N : x; }
 
-template <typename T, int TY, int S>
+template <typename T, int TY, int S, bool PER>
 __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const CUtensorMap* maps,
                                                               int zc, int src_slot, int dst,
                                                               float omega, float inv_diag) {
@@ -587,6 +592,8 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     const int y = j0 - 1 + w;  // row of a row warp
     const bool yreal = rowwarp && y >= 0 && y < ny;
     const bool out_row = w >= 1 && w <= TY && yreal;  // second-sweep rows of this tile
+    // first-sweep rows: inside the block, or (PER) also the ghost rows
+    const bool y1 = PER ? rowwarp && y >= -1 && y <= ny : yreal;
     const int xl = lane * 4;
     const int x0 = i0 + xl;
     const int nv = min(4, nx - x0);          // cells of this lane inside the block
@@ -608,7 +615,8 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     // sweep iterations are numbered across tiles (u = it1 + t), slot u % 8
     int sq = (int)(seq % S);
     uint32_t phq = (seq / S) & 1u;
-    const bool act1 = yreal && nv > 0;                 // this lane has first-sweep cells
+    // this lane has first-sweep cells (PER: also the ghost column x = nx)
+    const bool act1 = y1 && (PER ? x0 <= nx : nv > 0);
     const bool act2 = out_row && nv > 0;               // ... and second-sweep outputs
     const bool yface = (y == 0) | (y == ny - 1);
     const bool xface = (lane == 0 && i0 == 0) | xhi_in;  // lanes with an x image
@@ -629,7 +637,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       const T* Pc = ring + sc * STAGE_T;
       const T* Pp = ring + sp * STAGE_T;
       float* S1 = s1 + (int)((it1 + t) & (NS1 - 1)) * G::SPLANE;
-      const bool mreal = (m >= 0) & (m < nz);
+      const bool mreal = PER ? (m >= -1) & (m <= nz) : (m >= 0) & (m < nz);
       if (act1 && mreal) {
         float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
         ldv<4>(Pc + prow, c);
@@ -645,15 +653,19 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
 #pragma unroll
         for (int e = 0; e < 4; ++e) o[e] = tof(cvt<T>(o[e]));
         *reinterpret_cast<float4*>(S1 + srow) = make_float4(o[0], o[1], o[2], o[3]);
-        if (lane == 0 && i0 == 0) S1[srow - 1] = o[0];   // x = -1 <- x = 0
-        if (xhi_in) S1[srow + nv] = pick<4>(o, nv - 1);  // x = nx <- x = nx - 1
+        if constexpr (!PER) {
+          if (lane == 0 && i0 == 0) S1[srow - 1] = o[0];   // x = -1 <- x = 0
+          if (xhi_in) S1[srow + nv] = pick<4>(o, nv - 1);  // x = nx <- x = nx - 1
+        }
       }
       if (!rowwarp && mreal) {
 #pragma unroll
         for (int q = 0; q < NE; ++q) {
           const int ce = lane + 32 * q;
           const int er = ce >> 1, ex = (ce & 1) ? i0 + TX : i0 - 1, ey = j0 - 1 + er;
-          if (ce < 2 * NW && ex >= 0 && ex < nx && ey >= 0 && ey < ny) {
+          const bool in = PER ? ex >= -1 && ex <= nx && ey >= -1 && ey <= ny
+                              : ex >= 0 && ex < nx && ey >= 0 && ey < ny;
+          if (ce < 2 * NW && in) {
             const int epi = (er + 1) * PW + HX + (ex - i0);
             const int eri = RS_T + er * PW + HX + (ex - i0);
             S1[er * SW + 4 + (ex - i0)] = tof(cvt<T>(
@@ -682,8 +694,8 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       ldv<4>(Rp + rrow, rr);
       const float left = Bc[-1];
       const float right = Bc[4];
-      const bool zlo = P == 0, zhi = P == nz - 1;
-      if (yface | zlo | zhi) {
+      const bool zlo = !PER && P == 0, zhi = !PER && P == nz - 1;
+      if (!PER && (yface | zlo | zhi)) {
         // face rows and planes: the first sweep's ghost is the face value
 #pragma unroll
         for (int e = 0; e < 4; ++e) {
@@ -709,7 +721,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       // ghost-on-write at the walls (this kernel runs only when all six
       // faces are walls): the first ghost layer takes the face value, in
       // the same block, next to the face cell
-      if (__builtin_expect(xface | yface | zlo | zhi, 0)) {
+      if (!PER && __builtin_expect(xface | yface | zlo | zhi, 0)) {
         if (lane == 0 && i0 == 0) qk[-1] = cvt<T>(out[0]);
         if (xhi_in) qk[nv] = cvt<T>(pick<4>(out, nv - 1));
         if (y == 0) put(qk - pyl);
@@ -776,11 +788,11 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       mbar_wait(smem_u32(&full[f % S]), (f / S) & 1u);
 }
 
-template <typename T, int TY, int S>
+template <typename T, int TY, int S, bool PER>
 cudaError_t run_ws2(const Launch& L, const JacobiCfg& c, const void* maps, int src_slot, int dst,
                     float omega, float inv_diag) {
   using G = Ws2Geom<T, TY>;
-  auto kern = k_jacobi2_ws<T, TY, S>;
+  auto kern = k_jacobi2_ws<T, TY, S, PER>;
   const int smem = S * G::STAGE + G::NS1 * G::SPLANE * 4 + 8 * (2 * S + G::NS1);
   static int occ = -1;
   if (occ < 0) {
@@ -897,17 +909,24 @@ bool encode_jacobi_maps(void* out_host, const TmaArray* arrays, int narrays, int
     default: { using T = __half; __VA_ARGS__; } break;       \
   }
 
-cudaError_t launch_jacobi2_ws(const Launch& L, const JacobiCfg& c, const void* maps_dev,
-                              int src_slot, int dst, float omega) {
-  const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+template <bool PER>
+static cudaError_t dispatch_ws2(const Launch& L, const JacobiCfg& c, const void* maps_dev,
+                                int src_slot, int dst, float omega, float inv_diag) {
   cudaError_t e = cudaErrorInvalidValue;
   CFD_DISPATCH_T(L.dtype, {
-    if (c.ty == 16 && c.stages == 7) e = run_ws2<T, 16, 7>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
-    else if (c.ty == 16) e = run_ws2<T, 16, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
-    else if (c.stages == 6) e = run_ws2<T, 8, 6>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
-    else e = run_ws2<T, 8, 5>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    if (c.ty == 16 && c.stages == 7) e = run_ws2<T, 16, 7, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.ty == 16) e = run_ws2<T, 16, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.stages == 6) e = run_ws2<T, 8, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else e = run_ws2<T, 8, 5, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
   });
   return e;
+}
+
+cudaError_t launch_jacobi2_ws(const Launch& L, const JacobiCfg& c, const void* maps_dev,
+                              int src_slot, int dst, float omega, bool periodic) {
+  const float inv_diag = 1.f / (2.f * (L.ih2[0] + L.ih2[1] + L.ih2[2]));
+  return periodic ? dispatch_ws2<true>(L, c, maps_dev, src_slot, dst, omega, inv_diag)
+                  : dispatch_ws2<false>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
 }
 
 cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* maps_dev,
