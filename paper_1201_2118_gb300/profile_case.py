@@ -10,6 +10,8 @@ given Jacobi variant (kind,vx,ty,zc,stages) runs the requested number of
 sweeps on the grid's stream, then checks the device error flag.  With
 --stages N it runs N RHS + stage-2 combines per stencil variant
 (ty,zc,tile_tz) instead (--order 2 or 4, --form advective or flux).  With
+--descriptor N it times N projections u = w - c dt G p by the library's
+kernel and by the kernel generated from the equivalent descriptor.  With
 --vcycles N it runs N multigrid V-cycles (V(2,2), all levels) on the
 pressure equation with R = D U / 1e-3 from the cavity noise, the fine level
 smoothed by the first --jacobi variant (default: the grid's).  With
@@ -37,6 +39,9 @@ def main(argv=None):
     ap.add_argument("--form", default="advective", choices=["advective", "flux"])
     ap.add_argument("--vcycles", type=int, default=0,
                     help="instead of sweeps: this many multigrid V-cycles")
+    ap.add_argument("--descriptor", type=int, default=0,
+                    help="instead of sweeps: this many projections by the library's kernel "
+                         "and by the same projection generated from a kernel descriptor")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -53,6 +58,44 @@ def main(argv=None):
     g.upload(workloads.ldc_noise(n, seed=1))
     g.pressure_solve(1e-3, 0)
     es = 4 if a.dtype == "f32" else 2
+    if a.descriptor:
+        from paper_1201_2118_gb300 import (Descriptor, GeneratedKernel, P, SET_U1, U1, V1, W1, WU,
+                                           WV, WW)
+        d = Descriptor(
+            name="update_velocity", inputs={"wu": "cached", "wv": "cached", "ww": "cached",
+                                            "p": "cached"},
+            outputs=["u", "v", "w"], params=["cdt"], stencil=(0, 1, 0, 1, 0, 1),
+            body='''
+              const float pc = at(p, 0, 0, 0);
+              out(u) = at(wu, 0, 0, 0) - cdt * ((at(p, 1, 0, 0) - pc) * idx);
+              out(v) = at(wv, 0, 0, 0) - cdt * ((at(p, 0, 1, 0) - pc) * idy);
+              out(w) = at(ww, 0, 0, 0) - cdt * ((at(p, 0, 0, 1) - pc) * idz);
+            ''')
+        kern = GeneratedKernel(d)
+        d_direct = Descriptor(name="update_velocity_direct",
+                              inputs={v: "direct" for v in d.inputs}, outputs=d.outputs,
+                              params=d.params, stencil=d.stencil, body=d.body)
+        kern_direct = GeneratedKernel(d_direct)
+        bind = {"wu": WU, "wv": WV, "ww": WW, "p": P, "u": U1, "v": V1, "w": W1}
+        runs = {"library cfd_project (kernel + ghost fill of the output)":
+                    lambda: g.project(1e-3, SET_U1),
+                "generated, inputs cached in the plane ring": lambda: kern(g, bind, cdt=1e-3),
+                "generated, inputs read directly": lambda: kern_direct(g, bind, cdt=1e-3)}
+        for name, fn in runs.items():
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(s)
+            for _ in range(a.descriptor):
+                fn()
+            e1.record(s)
+            torch.cuda.synchronize()
+            us = e0.elapsed_time(e1) * 1e3 / a.descriptor
+            gbs = 7 * es * n ** 3 / (us * 1e-6) / 1e9  # read w (3), p; write u (3)
+            print("%d^3 projection, %s: %.1f us %.0f GB/s" % (n, name, us, gbs), flush=True)
+        g.check()
+        return
     if a.vcycles:
         from paper_1201_2118_gb300 import P, U, V, W, WU, WV, WW, mask
         if a.jacobi:
