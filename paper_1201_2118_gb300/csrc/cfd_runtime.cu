@@ -574,7 +574,11 @@ cfd_status enq_rk_stage(cfd_grid* g, int stage, double dt, int* pcur = nullptr) 
     if ((s = enq_stage(g, 0.5, CFD_SET_U, 0.5, CFD_SET_U1, 0.5 * dt, CFD_SET_W)) != CFD_OK)
       return s;
   }
-  if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
+  // the stage output's ghosts: read only by the divergence (the normal
+  // component below each low face), which takes a wall's value itself
+  bool walls = true;
+  for (int f = 0; f < 6; ++f) walls &= g->bc[f] == CFD_BC_WALL;
+  if (!walls && (s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
   if ((s = enq_stage_solve(g, cdt, cur, &cur)) != CFD_OK) return s;
   if ((s = enq_project(g, cdt, stage == 1 ? CFD_SET_U1 : CFD_SET_U, cur)) != CFD_OK) return s;
   if (pcur) {

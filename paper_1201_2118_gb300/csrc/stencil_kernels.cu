@@ -442,7 +442,9 @@ __global__ void __launch_bounds__(32 * TY) k_stage_ring(Launch L, int zc, float 
 // Both walk 32 x TY columns along z with one cell per thread; the block's
 // pointers are taken into registers once per tile (the output stores could
 // alias the block table as far as the compiler knows) and the z-neighbour
-// read by one plane is kept for the next.
+// read by one plane is kept for the next.  The divergence takes the wall
+// rule for the normal component below a low wall face itself, so on an
+// all-wall grid its input needs no ghost fill.
 
 template <typename T, int TY>
 __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, float inv_cdt,
@@ -466,13 +468,17 @@ __global__ void __launch_bounds__(32 * TY) k_div(Launch L, int zc, Set3 ws, floa
     const T* v = base + B.org[ws.a[1]] + o0;
     const T* w = base + B.org[ws.a[2]] + o0;
     T* r = reinterpret_cast<T*>(L.base) + B.org[r_arr] + o0;
-    float wm = ldf<T>(w - pz);
+    // the normal component one cell below a low face: at a wall it is the
+    // wall's normal velocity, 0 (the ghost rule), read without the ghost
+    const bool wx = B.bc[0] == BC_WALL && i == 0, wy = B.bc[2] == BC_WALL && j == 0;
+    float wm = (B.bc[4] == BC_WALL && k0 == 0) ? 0.f : ldf<T>(w - pz);
 #pragma unroll 1
     for (int q = 0; q < kn; ++q) {
       const long long o = (long long)q * pz;
       const float wc = ldf<T>(w + o);
-      const float d = (ldf<T>(u + o) - ldf<T>(u + o - 1)) * ihx +
-                      (ldf<T>(v + o) - ldf<T>(v + o - py)) * ihy + (wc - wm) * ihz;
+      const float um = wx ? 0.f : ldf<T>(u + o - 1);
+      const float vm = wy ? 0.f : ldf<T>(v + o - py);
+      const float d = (ldf<T>(u + o) - um) * ihx + (ldf<T>(v + o) - vm) * ihy + (wc - wm) * ihz;
       r[o] = cvt<T>(d * inv_cdt);
       wm = wc;
     }
