@@ -42,7 +42,7 @@ typedef struct {
 /* Advection term of the momentum equation (Sec. 4.1, Eq. 1): the advective
  * form (u . grad) u_c, or, using div u = 0 (Eq. 2), the conservative form
  * div(u u_c) as face-flux differences.  The adjoint functions below
- * linearise the advective form only. */
+ * linearise either form. */
 enum { ORA_ADVECTIVE = 0, ORA_FLUX = 1 };
 
 /* Ghost fill of one field (kind ORA_U..ORA_P), axis passes x, y, z over the

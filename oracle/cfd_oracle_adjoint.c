@@ -78,10 +78,44 @@ void ora_ghost_fold(const ora_grid* G, double* f, int kind) {
 
 static const double W4[4] = {-1.0 / 16, 9.0 / 16, 9.0 / 16, -1.0 / 16};
 
+/* Scatter of w * dF_c(y)/dy for the conservative (flux) form, order 2:
+ * F_c(p) = -sum_d (E(p) - E(p - e_d)) / h_d + nu lap y_c with
+ * E(q) = A(q) B(q) / 4, A = y_c(q) + y_c(q + e_d), B = y_d(q) + y_d(q + e_c);
+ * dE = (B dA + A dB) / 4 (for d = c, A = B and both terms add).  Returns
+ * sum_d second_d(y_c). */
+static double rhs_point_adj_flux(const ora_grid* G, const double* const y[3], int c,
+                                 const int p[3], double w, double* const ybar[3]) {
+  const double* fc = y[c];
+  const double f0 = fc[at3(G, p)];
+  double lap = 0.0;
+  for (int d = 0; d < 3; ++d) {
+    const double h = G->h[d];
+    const double p1 = fc[off(G, p, d, 1, d, 0)], m1 = fc[off(G, p, d, -1, d, 0)];
+    lap += (p1 - 2.0 * f0 + m1) / (h * h);
+    const double v = w * G->nu / (h * h);
+    ybar[c][off(G, p, d, 1, d, 0)] += v;
+    ybar[c][off(G, p, d, -1, d, 0)] += v;
+    ybar[c][at3(G, p)] += -2.0 * v;
+    for (int side = 0; side < 2; ++side) {  /* E(p) with -1/h_d, E(p - e_d) with +1/h_d */
+      int q[3] = {p[0], p[1], p[2]};
+      q[d] -= side;
+      const double wq = (side == 0 ? -w : w) / h;
+      const double A = y[c][at3(G, q)] + y[c][off(G, q, d, 1, d, 0)];
+      const double B = y[d][at3(G, q)] + y[d][off(G, q, c, 1, c, 0)];
+      ybar[c][at3(G, q)] += 0.25 * wq * B;
+      ybar[c][off(G, q, d, 1, d, 0)] += 0.25 * wq * B;
+      ybar[d][at3(G, q)] += 0.25 * wq * A;
+      ybar[d][off(G, q, c, 1, c, 0)] += 0.25 * wq * A;
+    }
+  }
+  return lap;
+}
+
 /* Scatter of w * dF_c(y)/dy into ybar at point p; returns sum_d second_d(y_c)
  * (the nu-derivative of F_c) for the viscosity gradient. */
 static double rhs_point_adj(const ora_grid* G, const double* const y[3], int c, const int p[3],
                             double w, double* const ybar[3]) {
+  if (G->form == ORA_FLUX) return rhs_point_adj_flux(G, y, c, p, w, ybar);
   const double* fc = y[c];
   const double f0 = fc[at3(G, p)];
   double lap = 0.0;

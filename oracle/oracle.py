@@ -300,12 +300,7 @@ class Oracle:
         self.lib.ora_ghost_fold(self._G(), _ptr(f), int(kind))
         return f
 
-    def _adjoint_form(self):
-        if self.form != "advective":
-            raise ValueError("the adjoint linearises the advective form only")
-
     def adj_stage(self, a, xbar, b, y, c, ybar, outbar):
-        self._adjoint_form()
         nb = ctypes.c_double(0.0)
         xs = _p3(xbar) if xbar is not None else (_D * 3)()
         self.lib.ora_adj_stage(self._G(), float(a), xs, float(b), _p3(y), float(c), _p3(ybar),
@@ -325,7 +320,6 @@ class Oracle:
 
     def adj_rk2_step(self, un, u1, dt, iters, ubar, pbar, scratch=None):
         """One adjoint step in place on ubar, pbar; returns dL/dnu of it."""
-        self._adjoint_form()
         if scratch is None:
             scratch = [self.zeros() for _ in range(11)]
         nb = ctypes.c_double(0.0)

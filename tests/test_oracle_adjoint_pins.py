@@ -37,12 +37,16 @@ def test_ghost_fold_is_transpose_of_fill(bc, g):
         assert lhs == pytest.approx(rhs, rel=1e-12, abs=1e-12)
 
 
-@pytest.mark.parametrize("order,g,bc", [(2, 1, "periodic"), (4, 2, "periodic"), (2, 1, "cavity")])
-def test_adj_stage_matches_central_difference(order, g, bc):
+@pytest.mark.parametrize("order,g,bc,form", [(2, 1, "periodic", "advective"),
+                                             (4, 2, "periodic", "advective"),
+                                             (2, 1, "cavity", "advective"),
+                                             (2, 1, "periodic", "flux"), (2, 2, "periodic", "flux"),
+                                             (2, 1, "cavity", "flux")])
+def test_adj_stage_matches_central_difference(order, g, bc, form):
     """Stage map out(y) = a x + b y + c F(y): its tangent by central
     differences (exact: F is quadratic) against the adjoint."""
     rng = np.random.default_rng(2)
-    o = Oracle((7, 6, 5), ghost=g, h=H3, bc=bc, nu=0.07, order=order, lid=0.0)
+    o = Oracle((7, 6, 5), ghost=g, h=H3, bc=bc, nu=0.07, order=order, lid=0.0, form=form)
     y = [rng.standard_normal(o.shape) for _ in range(3)]
     v = [rng.standard_normal(o.shape) for _ in range(3)]
     w = [o.embed(rng.standard_normal(o.dims[::-1])) for _ in range(3)]
@@ -57,15 +61,19 @@ def test_adj_stage_matches_central_difference(order, g, bc):
     assert lhs == pytest.approx(rhs, rel=1e-9)
 
 
-@pytest.mark.parametrize("order,g,bc,iters", [(2, 1, "periodic", 6), (2, 1, "periodic", 5),
-                                              (4, 2, "periodic", 4), (2, 1, "cavity", 6)])
-def test_adj_step_dot_product(order, g, bc, iters):
+@pytest.mark.parametrize("order,g,bc,iters,form", [(2, 1, "periodic", 6, "advective"),
+                                                   (2, 1, "periodic", 5, "advective"),
+                                                   (4, 2, "periodic", 4, "advective"),
+                                                   (2, 1, "cavity", 6, "advective"),
+                                                   (2, 2, "periodic", 5, "flux"),
+                                                   (2, 1, "cavity", 6, "flux")])
+def test_adj_step_dot_product(order, g, bc, iters, form):
     """Full RK2 step S(u, p) -> (u', p'): <dS (v, q), (w, s)> by central
     differences equals <(v, q), dS^T (w, s)> from the adjoint step."""
     rng = np.random.default_rng(3)
     n = (8, 7, 6)
     h = (0.35, 0.3, 0.25)
-    o = Oracle(n, ghost=g, h=h, bc=bc, nu=0.05, order=order, lid=0.7)
+    o = Oracle(n, ghost=g, h=h, bc=bc, nu=0.05, order=order, lid=0.7, form=form)
     dt = 0.02
     base = {c: 0.5 * rng.standard_normal(n[::-1]) for c in "uvwp"}
     if bc == "cavity":

@@ -278,12 +278,9 @@ def test_flux_form_converges_at_second_order():
     assert 3.2 < r2 < 5.0 and 2.8 < r1 < 5.2, (e, r1, r2)
 
 
-def test_flux_form_rejects_order4_and_adjoint():
+def test_flux_form_is_order2_only():
     with pytest.raises(ValueError):
         Oracle((4, 4, 4), ghost=2, order=4, form="flux")
-    o = Oracle((4, 4, 4), form="flux")
-    with pytest.raises(ValueError):
-        o.adj_rk2_step(None, None, 0.1, 1, None, None)
 
 
 # --------------------------------------------------------- pressure solve
