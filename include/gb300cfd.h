@@ -159,8 +159,8 @@ cfd_status cfd_set_params(cfd_grid* g, double nu, int jacobi_iters, double omega
  * every field (momentum conservation) and, for a discretely divergence-free
  * field, so does the work sum u_c A_c (energy conservation).  CFD_FLUX is
  * order 2 only (CFD_EINVAL with order 4, here or in cfd_set_params later);
- * the adjoint linearises CFD_ADVECTIVE only (CFD_EUNSUPPORTED).  Invalidates
- * captured step graphs. */
+ * the adjoint (cfd_adjoint_step, cfd_rollout_*) linearises either form.
+ * Invalidates captured step graphs. */
 cfd_status cfd_set_advection(cfd_grid* g, int form);
 
 /* ------------------------------------------------------ steps of the path */

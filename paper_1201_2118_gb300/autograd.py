@@ -16,12 +16,15 @@ class Rollout:
 
     rollout(u0, v0, w0, nu) -> (uT, vT, wT); u0.. are (nz, ny, nx) float32
     CUDA tensors, nu a 0-d tensor.  Gradients flow to u0, v0, w0 and nu.
-    p starts at zero (the Jacobi warm start)."""
+    p starts at zero (the Jacobi warm start).  form: the advection term,
+    'advective' or 'flux'."""
 
-    def __init__(self, dims, h, nsteps, dt, jacobi_iters=50, omega=1.0, seg=None, stream=None):
+    def __init__(self, dims, h, nsteps, dt, jacobi_iters=50, omega=1.0, seg=None, stream=None,
+                 form="advective"):
         import torch
         self.torch = torch
         self.grid = Grid(dims, ghost=2, h=h, dtype="f32", stream=stream)
+        self.grid.set_advection(form)
         self.nsteps, self.dt = int(nsteps), float(dt)
         self.iters, self.omega = int(jacobi_iters), float(omega)
         self.seg = int(seg) if seg else max(1, int(math.ceil(math.sqrt(self.nsteps))))

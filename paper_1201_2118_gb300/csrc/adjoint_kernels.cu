@@ -153,6 +153,48 @@ __device__ __forceinline__ float adj_rhs_comp(const F3 (&lam)[3], const F3 (&y)[
   return adj;
 }
 
+// The same for the conservative (flux) form.  On the periodic grid,
+// summation by parts turns sum_p lam_c(p) F_c(p) (advective part) into
+// sum_{c,d,q} E_cd(q) g_cd(q) with E_cd(q) = A B / 4,
+// A = y_c(q) + y_c(q + e_c') (c' = d), B = y_d(q) + y_d(q + e_c) and
+// g_cd(q) = (lam_c(q + e_d) - lam_c(q)) / h_d; its derivative by y_T(x) is
+//   1/4 sum_d [B_Td(x) g_Td(x) + B_Td(x - e_d) g_Td(x - e_d)]   (through A)
+// + 1/4 sum_c [A_cT(x) g_cT(x) + A_cT(x - e_c) g_cT(x - e_c)]   (through B),
+// B_Td(q) = y_d(q) + y_d(q + e_T), A_cT(q) = y_c(q) + y_c(q + e_T).
+template <int TT>
+__device__ __forceinline__ float adj_rhs_comp_flux(const F3 (&lam)[3], const F3 (&y)[3], int i,
+                                                   int j, int k, const float (&ih)[3],
+                                                   const float (&ih2)[3], float nu,
+                                                   double& lap_dot) {
+  auto at = [&](const F3& f, int d1, int o1, int d2, int o2) -> float {
+    int q[3] = {i, j, k};
+    q[d1] += o1;
+    q[d2] += o2;
+    return f(q[0], q[1], q[2]);
+  };
+  const float l0 = lam[TT](i, j, k);
+  const float y0 = y[TT](i, j, k);
+  float adj = 0.f, lapy = 0.f;
+#pragma unroll
+  for (int d = 0; d < 3; ++d) {
+    const float lp = at(lam[TT], d, 1, d, 0), lm = at(lam[TT], d, -1, d, 0);
+    adj += nu * (lp - 2.f * l0 + lm) * ih2[d];
+    lapy += (at(y[TT], d, 1, d, 0) - 2.f * y0 + at(y[TT], d, -1, d, 0)) * ih2[d];
+    // through A (c = T): q = x and q = x - e_d
+    const float bx = at(y[d], d, 0, TT, 0) + at(y[d], TT, 1, d, 0);
+    const float bm = at(y[d], d, -1, TT, 0) + at(y[d], d, -1, TT, 1);
+    adj += 0.25f * (bx * (lp - l0) + bm * (l0 - lm)) * ih[d];
+    // through B (d = T, here c = d): q = x and q = x - e_c
+    const float ax = at(y[d], d, 0, TT, 0) + at(y[d], TT, 1, d, 0);
+    const float am = at(y[d], d, -1, TT, 0) + at(y[d], d, -1, TT, 1);
+    const float gx = at(lam[d], TT, 1, d, 0) - at(lam[d], TT, 0, d, 0);
+    const float gm = at(lam[d], d, -1, TT, 1) - at(lam[d], d, -1, TT, 0);
+    adj += 0.25f * (ax * gx + am * gm) * ih[TT];
+  }
+  lap_dot += (double)l0 * (double)lapy;
+  return adj;
+}
+
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
   for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
@@ -161,6 +203,7 @@ __device__ __forceinline__ double warp_sum(double v) {
 
 // out_T = [acc ? out_T : 0] + b lam_T + c adj_T;  x_T = a lam_T (if x set);
 // per-CTA FP64 partial of <lam, lap y> into partials[blockIdx.x].
+template <bool FLUX>
 __global__ void __launch_bounds__(32 * kTY) k_adj_stage(Launch L, AdjSet lam_set, Ptr3 ys,
                                                         AdjSet out_set, int acc, float b, float c,
                                                         int has_x, AdjSet x_set, float a,
@@ -186,9 +229,15 @@ __global__ void __launch_bounds__(32 * kTY) k_adj_stage(Launch L, AdjSet lam_set
     for (int k = k0; k < k1; ++k) {
       const long long o = (long long)k * B.pz + (long long)j * B.py + i;
       float adj[3];
-      adj[0] = adj_rhs_comp<0>(lam, y, i, j, k, ih, ih2, nu, dot);
-      adj[1] = adj_rhs_comp<1>(lam, y, i, j, k, ih, ih2, nu, dot);
-      adj[2] = adj_rhs_comp<2>(lam, y, i, j, k, ih, ih2, nu, dot);
+      if constexpr (FLUX) {
+        adj[0] = adj_rhs_comp_flux<0>(lam, y, i, j, k, ih, ih2, nu, dot);
+        adj[1] = adj_rhs_comp_flux<1>(lam, y, i, j, k, ih, ih2, nu, dot);
+        adj[2] = adj_rhs_comp_flux<2>(lam, y, i, j, k, ih, ih2, nu, dot);
+      } else {
+        adj[0] = adj_rhs_comp<0>(lam, y, i, j, k, ih, ih2, nu, dot);
+        adj[1] = adj_rhs_comp<1>(lam, y, i, j, k, ih, ih2, nu, dot);
+        adj[2] = adj_rhs_comp<2>(lam, y, i, j, k, ih, ih2, nu, dot);
+      }
 #pragma unroll
       for (int m = 0; m < 3; ++m) {
         float* op = reinterpret_cast<float*>(L.base) + B.org[out_set.a[m]] + o;
@@ -250,11 +299,11 @@ cudaError_t launch_adj_wp(const Launch& L, const AdjSet& lam, int bk, int bk1, f
 cudaError_t launch_adj_stage(const Launch& L, const AdjSet& lam, const Ptr3& y, const AdjSet& out,
                              int acc, float b, float c, int has_x, const AdjSet& x, float a,
                              float nu, double* partials, int nparts, double* nu_acc,
-                             double nu_coef) {
+                             double nu_coef, bool flux) {
   const long long tiles = count_tiles(L, 32, kTY, kZC);
-  const unsigned grid = grid_size(L, k_adj_stage, 32 * kTY, tiles, nparts);
-  k_adj_stage<<<grid, dim3(32, kTY), 0, L.stream>>>(L, lam, y, out, acc, b, c, has_x, x, a, nu,
-                                                     partials);
+  auto kern = flux ? k_adj_stage<true> : k_adj_stage<false>;
+  const unsigned grid = grid_size(L, kern, 32 * kTY, tiles, nparts);
+  kern<<<grid, dim3(32, kTY), 0, L.stream>>>(L, lam, y, out, acc, b, c, has_x, x, a, nu, partials);
   k_nu_final<<<1, 32, 0, L.stream>>>(partials, (int)grid, nu_coef, nu_acc);
   return cudaGetLastError();
 }

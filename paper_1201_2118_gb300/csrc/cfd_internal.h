@@ -103,7 +103,8 @@ cudaError_t launch_jacobi2_ws(const Launch& L, const JacobiCfg& c, const void* m
 
 long long count_tiles(const Launch& L, int tx, int ty, int tz);
 
-// Adjoint kernels (FP32 storage, single periodic block, order 2).
+// Adjoint kernels (FP32 storage, single periodic block, order 2, either
+// advection form).
 struct AdjSet { int a[3]; };
 struct Ptr3 { const float* p[3]; };  // interior origins of stored forward states
 cudaError_t launch_adj_proj(const Launch& L, const AdjSet& lam, int lp, float c_dt, float r_scale,
@@ -113,7 +114,7 @@ cudaError_t launch_adj_wp(const Launch& L, const AdjSet& lam, int bk, int bk1, f
 cudaError_t launch_adj_stage(const Launch& L, const AdjSet& lam, const Ptr3& y, const AdjSet& out,
                              int acc, float b, float c, int has_x, const AdjSet& x, float a,
                              float nu, double* partials, int nparts, double* nu_acc,
-                             double nu_coef);
+                             double nu_coef, bool flux);
 
 cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr,
                          const long long* d_prefix, long long total);

@@ -784,8 +784,6 @@ cfd_status adjoint_supported(cfd_grid* g) {
   if (g->nblocks != 1 || g->dtype != CFD_F32 || g->order != 2 || g->g < 2)
     return fail(CFD_EUNSUPPORTED,
                 "the adjoint needs one FP32 block, order 2 and ghost width 2");
-  if (g->form != CFD_ADVECTIVE)
-    return fail(CFD_EUNSUPPORTED, "the adjoint linearises the advective form only");
   if (g->solver != CFD_SOLVER_JACOBI)
     return fail(CFD_EUNSUPPORTED, "the adjoint transposes the Jacobi pressure solve only");
   for (int f = 0; f < 6; ++f)
@@ -828,10 +826,10 @@ cfd_status enq_adjoint_step(cfd_grid* g, double dt, const Ptr3& un, const Ptr3& 
     if ((s = enq_ghost(g, set_mask(CFD_SET_W))) != CFD_OK) return s;
     if (stage == 2)
       CK(g, launch_adj_stage(L, ws, u1, u1s, 0, 0.5f, (float)(0.5 * dt), 1, lu, 0.5f, (float)g->nu,
-                             partials, g->nparts, nu_acc, 0.5 * dt));
+                             partials, g->nparts, nu_acc, 0.5 * dt, g->form == CFD_FLUX));
     else
       CK(g, launch_adj_stage(L, ws, un, lu, 1, 1.0f, (float)dt, 0, lu, 0.0f, (float)g->nu,
-                             partials, g->nparts, nu_acc, dt));
+                             partials, g->nparts, nu_acc, dt, g->form == CFD_FLUX));
     g->launches += 5 + g->iters;
   }
   return CFD_OK;

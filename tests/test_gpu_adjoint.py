@@ -22,7 +22,7 @@ def norm_rel(a, b):
     return np.linalg.norm(a - b) / np.linalg.norm(b)
 
 
-def run_case(dims, h, nsteps, seg, iters, nu, seed=4, tseed=5):
+def run_case(dims, h, nsteps, seg, iters, nu, seed=4, tseed=5, form="advective"):
     import torch
     from oracle import Oracle
     from paper_1201_2118_gb300 import Rollout
@@ -30,7 +30,7 @@ def run_case(dims, h, nsteps, seg, iters, nu, seed=4, tseed=5):
     u0 = rounded(workloads.random_div_free(dims, h, seed=seed))
     tgt = workloads.random_div_free(dims, h, seed=tseed)
     target = [0.5 * tgt[c] for c in "uvw"]
-    ro = Rollout(dims, h, nsteps, dt, jacobi_iters=iters, seg=seg)
+    ro = Rollout(dims, h, nsteps, dt, jacobi_iters=iters, seg=seg, form=form)
     t = [torch.tensor(u0[c], dtype=torch.float32, device="cuda", requires_grad=True) for c in "uvw"]
     nut = torch.tensor(nu, dtype=torch.float64, requires_grad=True)
     out = ro(t[0], t[1], t[2], nut)
@@ -39,7 +39,7 @@ def run_case(dims, h, nsteps, seg, iters, nu, seed=4, tseed=5):
     loss.backward()
     gpu_grad = [x.grad.double().cpu().numpy() for x in t]
     gpu_gnu = nut.grad.item()
-    o = Oracle(dims, ghost=2, h=h, nu=nu)
+    o = Oracle(dims, ghost=2, h=h, nu=nu, form=form)
     u, p = o.state(u0)
 
     def lg(ui):
@@ -49,12 +49,14 @@ def run_case(dims, h, nsteps, seg, iters, nu, seed=4, tseed=5):
     return loss.item(), gpu_grad, gpu_gnu, L, gu, gnu
 
 
-@pytest.mark.parametrize("dims,nsteps,seg,iters", [((32, 32, 32), 1, 1, 50),
-                                                   ((36, 28, 20), 6, 2, 10),
-                                                   ((32, 32, 32), 5, 3, 50)])
-def test_gpu_adjoint_matches_oracle_adjoint(dims, nsteps, seg, iters):
+@pytest.mark.parametrize("dims,nsteps,seg,iters,form", [((32, 32, 32), 1, 1, 50, "advective"),
+                                                        ((36, 28, 20), 6, 2, 10, "advective"),
+                                                        ((32, 32, 32), 5, 3, 50, "advective"),
+                                                        ((32, 32, 32), 1, 1, 50, "flux"),
+                                                        ((36, 28, 20), 6, 2, 10, "flux")])
+def test_gpu_adjoint_matches_oracle_adjoint(dims, nsteps, seg, iters, form):
     h = tuple(2 * math.pi / d for d in dims)
-    L, gg, ggnu, Lo, go, gonu = run_case(dims, h, nsteps, seg, iters, 0.01)
+    L, gg, ggnu, Lo, go, gonu = run_case(dims, h, nsteps, seg, iters, 0.01, form=form)
     assert L == pytest.approx(Lo, rel=1e-5)
     assert norm_rel(gg, go) < 1e-4
     assert ggnu == pytest.approx(gonu, rel=1e-4)

@@ -136,7 +136,7 @@ def test_flux_blockset_step_equals_global_oracle():
         assert rel_err(got, ref, remove_mean=(k == 3)) < 1e-5, k
 
 
-def test_flux_form_rejects_order4_and_adjoint():
+def test_flux_form_rejects_order4():
     from paper_1201_2118_gb300 import CfdError, Grid
     g = Grid((16, 16, 16), ghost=2, h=(0.1, 0.1, 0.1))
     g.set_params(0.01, 10, 1.0, 4)
