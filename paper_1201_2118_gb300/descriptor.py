@@ -151,7 +151,9 @@ def generate(d: Descriptor) -> str:
     w("#define YM %d" % ym)
     w("#define ZM %d" % zm)
     w("#define ZP %d" % zp)
-    w("extern \"C\" __global__ void __launch_bounds__(32 * TY) gen_%s(GenArgs ga) {" % d.name)
+    # at least 4 CTAs per SM: the register budget that leaves keeps enough
+    # warps resident to hide the loads' latency
+    w("extern \"C\" __global__ void __launch_bounds__(32 * TY, 4) gen_%s(GenArgs ga) {" % d.name)
     if cached:
         w("  __shared__ float ring[NC][RING][PL];")
     w("  const int nx = ga.n[0], ny = ga.n[1], nz = ga.n[2];")
@@ -181,6 +183,9 @@ def generate(d: Descriptor) -> str:
         w("  };")
         w("  for (int kk = k0 - ZM; kk <= k0 + ZP; ++kk) load_plane(kk);")
     w("  const bool mine = i < nx && j < ny;")
+    if not cached:
+        # no plane ring: an unrolled z loop would only hold more addresses
+        w("#pragma unroll 1")
     w("  for (int k = k0; k < k1; ++k) {")
     if cached:
         w("    __syncthreads();")
