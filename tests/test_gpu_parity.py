@@ -369,3 +369,37 @@ def test_cavity_256_first_steps():
         assert ew < max(1e-5, floor), (step, ew, floor)
         assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < tol_p
         print("ldc256 step", step, errs, "w", ew, "w floor", floor)
+
+
+@pytest.mark.parametrize("solver,jacobi,stencil", [("jacobi", (9, 4, 16, 64, 6), (8, 64, 1)),
+                                                   ("jacobi", (7, 4, 16, 64, 8), (4, 32, 3)),
+                                                   ("mg", (9, 4, 16, 64, 6), (8, 32, 1))])
+def test_steps_are_deterministic(solver, jacobi, stencil):
+    """The same steps on two grids give the same bits: no kernel of the step
+    (mbarrier rings, persistent tile walks, the one-CTA multigrid bottom,
+    fixed-order reductions) depends on timing."""
+    from paper_1201_2118_gb300 import Grid, U, V, W, P
+    n = 192
+    h = (1.0 / n,) * 3
+    dt = workloads.cfl_dt(h)
+    res = []
+    for _ in range(2):
+        g = Grid((n, n, n), ghost=1, h=h)
+        g.set_cavity(1.0)
+        g.set_params(1e-3, 30, 1.0, 2)
+        g.set_kernel_config(jacobi=jacobi, stencil=stencil)
+        if solver == "mg":
+            g.set_pressure_solver("mg", 2)
+        g.upload(workloads.ldc_noise(n, seed=1))
+        g.step(dt, 5)
+        ke = g.reduce(0)
+        res.append(([g.interior(a).clone() for a in (U, V, W, P)], ke))
+        g.check()
+    for a, b in zip(res[0][0], res[1][0]):
+        assert grid_equal(a, b)
+    assert res[0][1] == res[1][1]
+
+
+def grid_equal(a, b):
+    import torch
+    return bool(torch.equal(a, b))
