@@ -79,13 +79,17 @@ def test_mg_cycle_parameters(dims, levels, nu1, nu2):
     assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
 
 
-def test_mg_ghost_width_2():
+@pytest.mark.parametrize("jacobi", [(0, 4, 4, 32, 4), (9, 4, 16, 16, 6)])
+def test_mg_ghost_width_2(jacobi):
+    """Periodic grid with two ghost layers; the fine level smoothed by the
+    register sweep or by the periodic two-sweep launches."""
     from oracle import Oracle
     from paper_1201_2118_gb300 import Grid, P, R, mask
     dims = (64, 32, 32)
     h = (0.03, 0.03, 0.03)
     o = Oracle(dims, ghost=2, h=h)
     grid = Grid(dims, ghost=2, h=h)
+    grid.set_kernel_config(jacobi=jacobi)
     grid.fill(float("nan"))
     r = np.random.default_rng(9).uniform(-1, 1, dims[::-1])
     r = rounded({"r": r - r.mean()})["r"]
