@@ -16,11 +16,13 @@
  *   MAC placement, cell (i,j,k) of size h = (hx,hy,hz):
  *     p at ((i+1/2)hx,(j+1/2)hy,(k+1/2)hz); u, v, w on the +x, +y, +z faces.
  *   F(u) = -(u . grad) u + nu lap u, advective form, central differences;
- *     order 2 (ghost >= 1) or order 4 (ghost = 2).
+ *     order 2 (ghost >= 1) or order 4 (ghost = 2); or (cfd_set_advection)
+ *     the conservative form -div(u u) + nu lap u, order 2.
  *   Heun RK2, each stage projected:
  *     stage 1: w = u^n + dt F(u^n),              c = 1
  *     stage 2: w = 1/2 u^n + 1/2 u1 + 1/2 dt F(u1), c = 1/2
- *     r = (D w)/(c dt);  p <- K weighted Jacobi sweeps of L p = r (warm start);
+ *     r = (D w)/(c dt);  p <- K weighted Jacobi sweeps of L p = r (warm start),
+ *     or V-cycles of a geometric multigrid (cfd_set_pressure_solver);
  *     u_next = w - c dt G p.
  *
  * Conventions for every entry point:
@@ -120,7 +122,8 @@ cfd_status cfd_blockset_create(int nblocks, const int* dims, const int* origin,
 cfd_status cfd_grid_destroy(cfd_grid* g);
 
 /* Device bytes needed for all arrays of all blocks plus the library's
- * tables and reduction scratch. */
+ * tables and reduction scratch (and, on single FP32 blocks whose dims
+ * halve at least once, the multigrid levels: 1/7 of one field). */
 cfd_status cfd_memory_bytes(const cfd_grid* g, size_t* bytes);
 
 /* Binds caller-owned device memory (>= cfd_memory_bytes, 256-byte aligned).
