@@ -1345,9 +1345,6 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
     for (const JacobiCfg& d : {JacobiCfg{9, 4, 16, zc, 7}, JacobiCfg{9, 4, 16, zc, 6},
                                JacobiCfg{9, 4, 8, zc, 5}, JacobiCfg{9, 4, 8, zc, 6}})
       cands.push_back(d);
-  // chunk lengths between and past those: on a 512^3 grid, how the chunks
-  // fall over the SMs' last round moves the sweep by a few percent
-  for (int zc : {40, 72}) cands.push_back({9, 4, 16, zc, 6});
   const int avx = g->dtype == CFD_F32 ? 4 : 8;
   for (int zc : {16, 32, 64})
     for (const JacobiCfg& d : {JacobiCfg{3, avx, 4, zc, 5}, JacobiCfg{3, avx, 4, zc, 6},
