@@ -57,6 +57,8 @@ def parse():
     ap.add_argument("--dtype", default="f32", choices=["f32", "bf16", "f16"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--e2e-in-flight", type=int, default=3,
+                    help="independent problems in flight in the end-to-end measurement")
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the reduced-precision, block-set and adjoint comparisons")
     ap.add_argument("--precision-steps", type=int, default=20)
@@ -608,33 +610,103 @@ def run_gpu(a):
     if not a.no_e2e:
         tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
         host_in = [torch.empty((n, n, n), dtype=tdt, pin_memory=True) for _ in range(4)]
-        host_out = [torch.empty((n, n, n), dtype=tdt, pin_memory=True) for _ in range(4)]
+        nf = max(2, a.e2e_in_flight)
+        host_out = [[torch.empty((n, n, n), dtype=tdt, pin_memory=True) for _ in range(4)]
+                    for _ in range(nf)]
         for k, arr in enumerate((U, V, W, P)):
-            g.copy_interior(arr, host_out[k].data_ptr(), to_device=False)
+            g.copy_interior(arr, host_out[0][k].data_ptr(), to_device=False)
         torch.cuda.synchronize()
         for k in range(4):
-            host_in[k].copy_(host_out[k])
+            host_in[k].copy_(host_out[0][k])
         k_e2e = max(3, a.steps // 2)
+
+        def host_step(grid, out):
+            for k, arr in enumerate((U, V, W, P)):
+                grid.copy_interior(arr, host_in[k].data_ptr(), to_device=True)
+            grid.step(dt, 1)
+            for k, arr in enumerate((U, V, W, P)):
+                grid.copy_interior(arr, out[k].data_ptr(), to_device=False)
+
+        # one problem: copy in, step, copy out, one after the other
         x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
         x0.record(stream)
         for _ in range(k_e2e):
-            for k, arr in enumerate((U, V, W, P)):
-                g.copy_interior(arr, host_in[k].data_ptr(), to_device=True)
-            g.step(dt, 1)
-            for k, arr in enumerate((U, V, W, P)):
-                g.copy_interior(arr, host_out[k].data_ptr(), to_device=False)
+            host_step(g, host_out[0])
         x1.record(stream)
         torch.cuda.synchronize()
-        ems = x0.elapsed_time(x1) / k_e2e
-        ems, e2e_value = aggregate(ems, cells, dist, "cuda")
+        serial_ms, serial_value = aggregate(x0.elapsed_time(x1) / k_e2e, cells, dist, "cuda")
+
+        # nf independent problems in flight, one stream each, copies by the
+        # copy engines.  Events chain the input copies and the steps of the
+        # problems in turn, so they stay a fraction of a period apart: the
+        # others' host transfers run while one problem's step has the SMs.
+        def piped_step(grid, out, after):
+            in_done, step_done = torch.cuda.Event(), torch.cuda.Event()
+            if after[0] is not None:
+                grid.stream.wait_event(after[0])
+            for k, arr in enumerate((U, V, W, P)):
+                grid.copy_interior(arr, host_in[k].data_ptr(), to_device=True)
+            in_done.record(grid.stream)
+            if after[1] is not None:
+                grid.stream.wait_event(after[1])
+            grid.step(dt, 1)
+            step_done.record(grid.stream)
+            for k, arr in enumerate((U, V, W, P)):
+                grid.copy_interior(arr, out[k].data_ptr(), to_device=False)
+            return in_done, step_done
+
+        grids = [g]
+        for _ in range(nf - 1):
+            gx = Grid(dims, ghost=cfg["ghost"], h=h, dtype=a.dtype, stream=torch.cuda.Stream())
+            gx.set_cavity(1.0)
+            gx.set_params(cfg["nu"], cfg["jacobi_iters"], 1.0, cfg["order"])
+            gx.set_kernel_config(jacobi=jcfg[0], stencil=jcfg[1])
+            grids.append(gx)
+        for grid in grids:
+            grid.set_host_copy("engine")
+        for grid, out in zip(grids, host_out):  # warm-up: captures the step graphs
+            host_step(grid, out)
+        torch.cuda.synchronize()
+        x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        barrier()
+        torch.cuda.synchronize()
+        x0.record(stream)
+        for grid in grids[1:]:
+            grid.stream.wait_event(x0)
+        after = (None, None)
+        for _ in range(k_e2e):
+            for grid, out in zip(grids, host_out):
+                after = piped_step(grid, out, after)
+        for grid in grids[1:]:
+            y = torch.cuda.Event()
+            y.record(grid.stream)
+            stream.wait_event(y)
+        x1.record(stream)
+        torch.cuda.synchronize()
+        for grid in grids:
+            grid.check()
+        # every problem took the same step from the same input
+        same = all(torch.equal(host_out[0][k], host_out[j][k])
+                   for j in range(1, nf) for k in range(4))
+        g.set_host_copy("kernel")
+        del grids, gx
+        torch.cuda.empty_cache()
+        ems, e2e_value = aggregate(x0.elapsed_time(x1) / (nf * k_e2e), cells, dist, "cuda")
         es = host_in[0].element_size()
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * cells * es, "d2h_bytes_per_step": 4 * cells * es,
-               "ms_per_step": ems, "steps": k_e2e,
-               "api": "cfd_copy_interior (pinned host -> device, u,v,w,p) + cfd_step + "
-                      "cfd_copy_interior (device -> pinned host, u,v,w,p)"}
+               "ms_per_step": ems, "steps": nf * k_e2e, "in_flight": nf,
+               "outputs_equal": same,
+               "api": "per step: cfd_copy_interior (pinned host -> device, u,v,w,p; copy engine) "
+                      "+ cfd_step + cfd_copy_interior (device -> pinned host, u,v,w,p); %d "
+                      "independent %d^3 problems, one stream each, their input copies and steps "
+                      "chained by events in turn" % (nf, n),
+               "serial": {"value": serial_value, "ms_per_step": serial_ms, "steps": k_e2e,
+                          "in_flight": 1,
+                          "api": "the same calls on one problem, pack kernel over the host "
+                                 "link, each step's copies and step one after the other"}}
 
     cpu = None
     if rank == 0 and world == 1 and not a.no_cpu_baseline:

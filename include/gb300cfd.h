@@ -316,6 +316,17 @@ cfd_status cfd_set_state(cfd_grid* g, double t, long long step);
  * in the grid's memory (one interior of the largest block). */
 cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int to_device);
 
+/* How cfd_copy_interior moves page-locked host memory.  CFD_HOST_COPY_KERNEL
+ * (default): the pack kernel reads or writes it over the host link, one
+ * pass, but its CTAs hold SMs for the whole transfer.  CFD_HOST_COPY_ENGINE:
+ * a copy engine moves it to or from the staging region and the pack kernel
+ * runs device to device, so a transfer on this grid's stream overlaps
+ * kernels of another stream (another grid's step) with the SMs left to
+ * them.  Memory that is not page-locked always takes the staging route.
+ * CFD_EINVAL for another mode. */
+typedef enum { CFD_HOST_COPY_KERNEL = 0, CFD_HOST_COPY_ENGINE = 1 } cfd_host_copy;
+cfd_status cfd_set_host_copy(cfd_grid* g, int mode);
+
 /* Kernel variants.  jacobi = {kind, vx, ty, zc, stages}: kind 0 is the
  * register/shuffle sweep (vx in {1,2,4} cells per thread along x, ty rows per
  * CTA in {4,8,16}), kind 1 the TMA-staged sweep (vx 4 with ty in {4,8,16}, or

@@ -62,6 +62,7 @@ SIGNATURES = {
     "cfd_get_state": [c_void_p, P(c_double), P(c_ll)],
     "cfd_set_state": [c_void_p, c_double, c_ll],
     "cfd_copy_interior": [c_void_p, c_int, c_int, c_void_p, c_int],
+    "cfd_set_host_copy": [c_void_p, c_int],
     "cfd_check": [c_void_p],
     "cfd_last_error": [],
     "cfd_reduce_velocity_noalloc": [c_void_p, c_void_p, c_void_p, c_int, P(c_int), c_ll, c_ll,

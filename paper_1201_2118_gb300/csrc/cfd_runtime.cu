@@ -72,6 +72,7 @@ struct cfd_grid {
   bool maps_ready = false;        // maps encoded for the current Jacobi config
   size_t arrays_off = 0;
   size_t staging_off = 0;         // contiguous interior of one array (host copies)
+  int host_copy = CFD_HOST_COPY_KERNEL;  // route of page-locked host copies
   int nparts = 0;
   long long ghost_total = 0;
   std::vector<long long> ghost_prefix;
@@ -1734,11 +1735,12 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
   L.nblocks = 1;
   cudaPointerAttributes pa{};
   void* direct = nullptr;
-  if (cudaPointerGetAttributes(&pa, host) == cudaSuccess && pa.type == cudaMemoryTypeHost &&
-      pa.devicePointer)
-    direct = pa.devicePointer;
-  else
+  if (cudaPointerGetAttributes(&pa, host) == cudaSuccess) {
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer && g->host_copy == CFD_HOST_COPY_KERNEL)
+      direct = pa.devicePointer;
+  } else {
     cudaGetLastError();  // clear the query's error for plain host memory
+  }
   if ((s = join_in(g)) != CFD_OK) return s;
   if (direct) {
     CK(g, launch_pack(L, array, direct, to_device ? 0 : 1));
@@ -1754,6 +1756,14 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
   }
   g->launches += 1;
   return join_out(g);
+}
+
+cfd_status cfd_set_host_copy(cfd_grid* g, int mode) {
+  if (!g) return fail(CFD_EINVAL, "null grid");
+  if (mode != CFD_HOST_COPY_KERNEL && mode != CFD_HOST_COPY_ENGINE)
+    return fail(CFD_EINVAL, "mode must be CFD_HOST_COPY_KERNEL or CFD_HOST_COPY_ENGINE");
+  g->host_copy = mode;
+  return CFD_OK;
 }
 
 cfd_status cfd_check(cfd_grid* g) {

@@ -264,6 +264,15 @@ class Grid:
         call("cfd_copy_interior", self.handle, int(block), int(array_id), c_void_p(host_ptr),
              1 if to_device else 0)
 
+    def set_host_copy(self, mode: str = "kernel"):
+        """Route of copy_interior for page-locked host memory: 'kernel' (the
+        pack kernel over the host link) or 'engine' (a copy engine through
+        the staging region, leaving the SMs to other streams)."""
+        modes = {"kernel": 0, "engine": 1}
+        if mode not in modes:
+            raise ValueError("mode must be 'kernel' or 'engine'")
+        call("cfd_set_host_copy", self.handle, modes[mode])
+
     def adjoint_step(self, dt: float, un_ptrs, u1_ptrs, dnu_dev_ptr: int):
         call("cfd_adjoint_step", self.handle, float(dt), (c_void_p * 3)(*un_ptrs),
              (c_void_p * 3)(*u1_ptrs), ctypes.cast(c_void_p(dnu_dev_ptr), ctypes.POINTER(c_double)))

@@ -1,8 +1,10 @@
 """cfd_copy_interior: compact host arrays <-> the padded device layout,
-through the staging region and the pack kernel.  Bitwise checks against
-the torch view of the same interior, on a full-vector row width, a row
-width that is not a multiple of the 16-byte vector, 16-bit storage and a
-block set (per-block copies)."""
+by the pack kernel over the host link or through the staging region (a
+copy engine and the pack kernel).  Bitwise checks against the torch view
+of the same interior, on a full-vector row width, a row width that is not
+a multiple of the 16-byte vector, 16-bit storage and a block set
+(per-block copies); and two grids on two streams whose engine copies and
+steps interleave, against the same steps taken one grid at a time."""
 import numpy as np
 import pytest
 
@@ -11,12 +13,14 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 
+@pytest.mark.parametrize("mode", ["kernel", "engine"])
 @pytest.mark.parametrize("dims,dtype", [((64, 20, 7), "f32"), ((45, 37, 21), "f32"),
                                         ((70, 9, 5), "bf16"), ((33, 16, 4), "f16")])
-def test_copy_interior_round_trip(dims, dtype):
+def test_copy_interior_round_trip(dims, dtype, mode):
     import torch
     from paper_1201_2118_gb300 import Grid, U, P, R
     g = Grid(dims, ghost=1, h=(0.1, 0.1, 0.1), dtype=dtype)
+    g.set_host_copy(mode)
     g.fill(float("nan"))
     td = g.tdtype
     rng = np.random.default_rng(3)
@@ -72,3 +76,61 @@ def test_copy_interior_block_set():
         torch.cuda.synchronize()
         assert torch.equal(back, src)
     g.check()
+
+
+def test_set_host_copy_rejects_unknown_mode():
+    from paper_1201_2118_gb300 import CfdError, Grid
+    from paper_1201_2118_gb300._lib import call
+    g = Grid((16, 16, 16), ghost=1, h=(0.1, 0.1, 0.1))
+    with pytest.raises(CfdError) as e:
+        call("cfd_set_host_copy", g.handle, 2)
+    assert e.value.status == 1
+    with pytest.raises(ValueError):
+        g.set_host_copy("dma")
+    g.check()
+
+
+def test_two_grids_pipelined_engine_copies_equal_serial_steps():
+    """Two independent cavity problems on two streams: each step copies its
+    inputs in (engine route), steps and copies u, v, w, p out, with the
+    other grid's copies and step in flight.  Results are bitwise those of
+    the same steps taken one grid after the other with the kernel route."""
+    import torch
+    from paper_1201_2118_gb300 import Grid, U, V, W, P
+    n = 48
+    h = (1.0 / n,) * 3
+    dt = workloads.cfl_dt(h)
+    init = [workloads.ldc_noise(n, seed=s) for s in (1, 2)]
+    src = [[torch.from_numpy(f[c]).float().pin_memory() for c in "uvwp"] for f in init]
+
+    def run(mode, streams):
+        grids = []
+        for k in range(2):
+            with torch.cuda.stream(streams[k]):
+                g = Grid((n, n, n), ghost=1, h=h, stream=streams[k])
+                g.set_cavity()
+                g.set_params(1e-3, 30, 1.0, 2)
+                g.set_host_copy(mode)
+                grids.append(g)
+        out = [[torch.empty((n, n, n)).pin_memory() for _ in range(4)] for _ in range(2)]
+        torch.cuda.synchronize()
+        for step in range(3):
+            for k in range(2):
+                g = grids[k]
+                for c, arr in enumerate((U, V, W, P)):
+                    g.copy_interior(arr, src[k][c].data_ptr(), to_device=True)
+                g.step(dt, 1)
+                for c, arr in enumerate((U, V, W, P)):
+                    g.copy_interior(arr, out[k][c].data_ptr(), to_device=False)
+            torch.cuda.synchronize()
+        for g in grids:
+            g.check()
+        return out
+
+    cur = torch.cuda.current_stream()
+    serial = run("kernel", [cur, cur])
+    piped = run("engine", [torch.cuda.Stream(), torch.cuda.Stream()])
+    for k in range(2):
+        for c in range(4):
+            assert torch.equal(piped[k][c], serial[k][c]), (k, c)
+        assert not torch.equal(serial[k][0], src[k][0])
