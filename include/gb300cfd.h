@@ -312,8 +312,10 @@ cfd_status cfd_set_state(cfd_grid* g, double t, long long step);
  * and the device.  to_device != 0: host -> device.  Asynchronous: the host
  * buffer must stay valid and untouched until the grid's stream has reached
  * this point.  Page-locked buffers are read or written directly by a
- * kernel over the host link; others go through a contiguous staging copy
- * in the grid's memory (one interior of the largest block). */
+ * kernel over the host link (or, after cfd_set_host_copy with
+ * CFD_HOST_COPY_ENGINE, by a copy engine through the staging region);
+ * others go through a contiguous staging copy in the grid's memory (one
+ * interior of the largest block). */
 cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int to_device);
 
 /* How cfd_copy_interior moves page-locked host memory.  CFD_HOST_COPY_KERNEL
