@@ -74,3 +74,25 @@ def test_library_has_no_unresolved_internal_symbols():
     out = subprocess.run([nm, "-D", "-C", path], capture_output=True, text=True).stdout
     undefined = [l for l in out.splitlines() if " U " in l and "cfd::" in l]
     assert not undefined, undefined
+
+
+def test_every_grid_entry_point_rejects_a_null_grid():
+    """Each call that takes a grid returns CFD_EINVAL for a null one (other
+    arguments zero or null) before any device call; destroying a null grid
+    is a no-op that succeeds."""
+    import ctypes
+    from paper_1201_2118_gb300 import _lib
+    L = _lib.lib()
+    ints = (ctypes.c_int, ctypes.c_uint, ctypes.c_longlong, ctypes.c_size_t, ctypes.c_long)
+    checked = []
+    for name, args in sorted(_lib.SIGNATURES.items()):
+        if not args or args[0] is not ctypes.c_void_p or name.endswith("_create"):
+            continue
+        if "noalloc" in name:  # takes device pointers, not a grid
+            continue
+        vals = [None] + [0 if t in ints else 0.0 if t in (ctypes.c_double, ctypes.c_float)
+                         else None for t in args[1:]]
+        st = getattr(L, name)(*vals)
+        assert st == (0 if name == "cfd_grid_destroy" else 1), (name, st)
+        checked.append(name)
+    assert "cfd_set_host_copy" in checked and "cfd_step" in checked and len(checked) > 30
