@@ -96,3 +96,45 @@ def test_every_grid_entry_point_rejects_a_null_grid():
         assert st == (0 if name == "cfd_grid_destroy" else 1), (name, st)
         checked.append(name)
     assert "cfd_set_host_copy" in checked and "cfd_step" in checked and len(checked) > 30
+
+
+@pytest.mark.parametrize("case,blocks,gd,ghost,msg", [
+    ("no blocks", [], (8, 4, 4), 1, b"nblocks"),
+    ("thin block", [((1, 4, 4), (0, 0, 0))], (1, 4, 4), 1, b"2*ghost"),
+    ("thin for g=2", [((3, 4, 4), (0, 0, 0))], (3, 4, 4), 2, b"2*ghost"),
+    ("outside", [((4, 4, 4), (6, 0, 0))], (8, 4, 4), 1, b"outside"),
+    ("negative origin", [((4, 4, 4), (-1, 0, 0))], (8, 4, 4), 1, b"outside"),
+    ("gap", [((4, 4, 4), (0, 0, 0)), ((3, 4, 4), (5, 0, 0))], (8, 4, 4), 1, b"rectilinear"),
+    ("short", [((4, 4, 4), (0, 0, 0)), ((3, 4, 4), (4, 0, 0))], (8, 4, 4), 1, b"cover"),
+    ("missing combination", [((4, 4, 4), (0, 0, 0)), ((4, 4, 4), (4, 0, 0)),
+                             ((4, 4, 4), (0, 4, 0))], (8, 8, 4), 1, b"slab combination"),
+    ("coincide", [((4, 4, 4), (0, 0, 0)), ((4, 4, 4), (0, 0, 0)), ((4, 4, 4), (4, 4, 0)),
+                  ((4, 4, 4), (0, 4, 0))], (8, 8, 4), 1, b"coincide"),
+    ("ghost 0", [((4, 4, 4), (0, 0, 0))], (4, 4, 4), 0, b"ghost width"),
+])
+def test_blockset_tiling_errors_on_the_host(case, blocks, gd, ghost, msg):
+    """cfd_blockset_create checks the tiling (every block inside the domain
+    and at least 2*ghost wide, per axis slabs that partition [0, G), one
+    block per slab combination) before any device call."""
+    import ctypes
+    from paper_1201_2118_gb300 import _lib
+    L = _lib.lib()
+    out = ctypes.c_void_p()
+    dims = [x for b in blocks for x in b[0]] or [4, 4, 4]
+    origin = [x for b in blocks for x in b[1]] or [0, 0, 0]
+    st = L.cfd_blockset_create(len(blocks), _lib.ints(*dims), _lib.ints(*origin), _lib.ints(*gd),
+                               ghost, _lib.doubles(1, 1, 1), 0, None, ctypes.byref(out))
+    assert st == 1 and out.value is None, case
+    assert msg in L.cfd_last_error(), (case, L.cfd_last_error())
+
+
+@pytest.mark.parametrize("h,storage,msg", [((1, 0, 1), 0, b"h[1]"), ((1, 1, float("inf")), 0, b"h[2]"),
+                                           ((1, 1, 1), 3, b"storage")])
+def test_grid_argument_errors_on_the_host(h, storage, msg):
+    import ctypes
+    from paper_1201_2118_gb300 import _lib
+    L = _lib.lib()
+    out = ctypes.c_void_p()
+    st = L.cfd_grid_create(_lib.ints(8, 8, 8), 1, _lib.doubles(*h), storage, None, ctypes.byref(out))
+    assert st == 1 and out.value is None
+    assert msg in L.cfd_last_error()
