@@ -2,7 +2,8 @@
 cross-compile of the generated source for sm_103a (no GPU needed)."""
 import pytest
 
-from paper_1201_2118_gb300.descriptor import Descriptor, compile_source, generate
+from paper_1201_2118_gb300.descriptor import (MAX_ARRAYS, MAX_PARAMS, Descriptor,
+                                              compile_source, generate)
 
 
 def _uv(**kw):
@@ -49,6 +50,22 @@ def test_declaration_errors():
         _uv(stencil=(0, 3, 0, 1, 0, 1)).validate()
     with pytest.raises(ValueError, match="shared memory"):
         _uv(stencil=(2, 2, 2, 2, 2, 2), ty=16).validate()
+    with pytest.raises(ValueError, match="identifier"):
+        _uv(name="update-velocity").validate()
+    with pytest.raises(ValueError, match="at least one output"):
+        _uv(outputs=[], body="const float x = at(p, 0, 0, 0);").validate()
+    with pytest.raises(ValueError, match="at most"):
+        _uv(params=["c%d" % k for k in range(MAX_PARAMS + 1)]).validate()
+    with pytest.raises(ValueError, match="at most"):
+        _uv(inputs={"in%d" % k: "direct" for k in range(MAX_ARRAYS)}).validate()
+    for ty, zc in ((3, 32), (32, 32), (8, 0), (8, 1025)):
+        with pytest.raises(ValueError, match="ty must be"):
+            _uv(ty=ty, zc=zc).validate()
+    with pytest.raises(ValueError, match="stencil"):
+        _uv(stencil=(0, 1, 0, 1, 0)).validate()
+    # the limits themselves are accepted
+    _uv(ty=16, zc=1024).validate()
+    _uv(ty=1, zc=1).validate()
 
 
 def test_generated_source_cross_compiles_for_sm103a():
