@@ -118,7 +118,8 @@ cfd_status cfd_blockset_create(int nblocks, const int* dims, const int* origin,
                                int storage, void* stream, cfd_grid** out);
 
 /* Releases the grid (and memory from cfd_alloc_memory).  Waits for the
- * grid's queued work. */
+ * grid's queued work.  A null grid is a no-op (CFD_OK); every other call
+ * returns CFD_EINVAL for a null grid. */
 cfd_status cfd_grid_destroy(cfd_grid* g);
 
 /* Device bytes needed for all arrays of all blocks plus the library's
