@@ -295,6 +295,30 @@ def test_divergence_of_linear_field_is_trace():
     np.testing.assert_allclose(o.interior(r), np.trace(A) / 0.5, atol=1e-12)
 
 
+@pytest.mark.parametrize("bc", ["periodic", "cavity"])
+def test_divergence_is_minus_gradient_transpose(bc):
+    """Summation by parts on the MAC grid: <D w, p> = -<w, G p> over the
+    interior unknowns for any w and p (periodic; or walls, where the
+    wall-normal velocity is zero).  G p is read off the projection of a
+    zero field, w - G p with w = 0."""
+    dims = (7, 6, 5)
+    rng = np.random.default_rng(41)
+    o = Oracle(dims, ghost=1, h=H3, bc=bc)
+    w_int = [rng.uniform(-1, 1, dims[::-1]) for _ in range(3)]
+    if bc == "cavity":  # no flow through the walls
+        w_int[0][:, :, -1] = 0.0
+        w_int[1][:, -1, :] = 0.0
+        w_int[2][-1, :, :] = 0.0
+    w = [o.ghost_fill(o.embed(w_int[c]), c) for c in range(3)]
+    p = o.ghost_fill(o.embed(rng.uniform(-1, 1, dims[::-1])), 3)
+    dw = o.interior(o.divergence(w, c_dt=1.0))
+    minus_gp = o.project([o.zeros() for _ in range(3)], p, 1.0)
+    lhs = float((dw * o.interior(p)).sum())
+    rhs = sum(float((w_int[c] * o.interior(minus_gp[c])).sum()) for c in range(3))
+    assert abs(lhs) > 1.0
+    assert abs(lhs - rhs) < 1e-12 * sum(float(np.abs(w_int[c]).sum()) for c in range(3)) / min(H3)
+
+
 def test_random_div_free_field_has_zero_discrete_divergence():
     dims, h = (12, 10, 8), H3
     fl = workloads.random_div_free(dims, h, seed=3)
