@@ -47,3 +47,50 @@ def test_single_process_aggregate_is_identity():
     import bench
     ms, value = bench.aggregate(20.0, 2_000_000)
     assert ms == 20.0 and value == pytest.approx(2_000_000 / 20e-3 / 1e9)
+
+
+def _ref_args(steps=3):
+    import argparse
+    return argparse.Namespace(steps=steps, warmup=3, workload="ldc512")
+
+
+def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
+    """Under torchrun only rank 0 times the oracle and prints; the other
+    ranks return at once."""
+    import bench
+    monkeypatch.setenv("RANK", "1")
+    monkeypatch.setenv("WORLD_SIZE", "2")
+    monkeypatch.setenv("LOCAL_RANK", "1")
+
+    def no_call(*a, **k):
+        raise AssertionError("rank 1 ran the oracle")
+    monkeypatch.setattr(bench, "oracle_sample", no_call)
+    bench.run_reference(_ref_args())
+    assert capsys.readouterr().out == ""
+
+
+def test_reference_arm_line(monkeypatch, capsys):
+    """Rank 0 prints one JSON line: the median of the per-step oracle
+    samples as value, the same figure as cpu_baseline and e2e (no host
+    transfers), and the time of one 512^3 step at that rate."""
+    import json
+    import bench
+    monkeypatch.setenv("RANK", "0")
+    monkeypatch.setenv("WORLD_SIZE", "1")
+    rates = iter([0.010, 0.014, 0.012])
+
+    def fake_sample(detail=True, seconds_hint=False):
+        return {"value": next(rates), "unit": bench.UNIT, "cores": 4, "kind": "oracle",
+                "sample": "fake"}
+    monkeypatch.setattr(bench, "oracle_sample", fake_sample)
+    bench.run_reference(_ref_args(3))
+    lines = capsys.readouterr().out.strip().splitlines()
+    assert len(lines) == 1
+    d = json.loads(lines[0])
+    assert d["impl"] == "reference" and d["steps"] == 3
+    assert d["value"] == pytest.approx(0.012)
+    assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
+    assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+    assert d["ms_per_step"] == pytest.approx(512 ** 3 / 0.012e9 * 1e3)
+    assert d["config"]["workload"] == "ldc512" and d["higher_is_better"] is True
