@@ -3,7 +3,8 @@ reflection of each axis and with the exchange of x and y (equal cell
 sizes), for both advection forms and both orders, on periodic grids; and
 with the reflection of z on the lid-driven cavity (lid in the x-z plane at
 y = 1, moving along x), and with the reflection of x there when the lid's
-velocity is reversed.
+velocity is reversed; and a step with multigrid solves on power-of-two
+grids.
 
 On the staggered grid a reflection of axis a maps a cell-centred index i to
 n - 1 - i, and the a-face index i (at (i + 1) h_a) to n - 2 - i (mod n on a
@@ -119,6 +120,28 @@ def test_cavity_x_reflection_reverses_the_lid(form):
     a = step(dims, h, reflect_wall(f, "x"), "cavity", form, 1, 2, lid=1.0)
     b = reflect_wall(step(dims, h, f, "cavity", form, 1, 2, lid=1.0), "x")
     assert np.abs(a["u"] - b["u"]).max() > 1e-3 * np.abs(b["u"]).max()
+
+
+@pytest.mark.parametrize("bc,ax", [("periodic", "x"), ("periodic", "y"), ("periodic", "z"),
+                                   ("cavity", "z")])
+def test_multigrid_step_commutes_with_reflection(bc, ax):
+    """With power-of-two dims a reflection maps the children of each coarse
+    cell onto the children of another, so the V-cycle (averaging
+    restriction, trilinear prolongation, every level) commutes with it."""
+    dims, h = (16, 8, 8), (0.07, 0.11, 0.13)
+    f = rand_fields(dims, 10)
+    refl = reflect if bc == "periodic" else reflect_wall
+    if bc == "cavity":
+        f["u"][:, :, -1] = 0.0
+        f["v"][:, -1, :] = 0.0
+        f["w"][-1, :, :] = 0.0
+
+    def mg_step(fl):
+        o = Oracle(dims, ghost=1, h=h, bc=bc, nu=0.03)
+        u, p = o.state(fl)
+        o.rk2_step_mg(u, p, 0.04 * min(h), 2)
+        return {c: o.interior(a).copy() for c, a in zip("uvwp", u + [p])}
+    close(mg_step(refl(f, ax)), refl(mg_step(f), ax))
 
 
 def test_reflection_is_an_involution_and_breaks_a_shifted_index():
