@@ -3,8 +3,8 @@ reflection of each axis and with the exchange of x and y (equal cell
 sizes), for both advection forms and both orders, on periodic grids; and
 with the reflection of z on the lid-driven cavity (lid in the x-z plane at
 y = 1, moving along x), and with the reflection of x there when the lid's
-velocity is reversed; and a step with multigrid solves on power-of-two
-grids.
+velocity is reversed; a step with multigrid solves on power-of-two
+grids; and the adjoint's gradients.
 
 On the staggered grid a reflection of axis a maps a cell-centred index i to
 n - 1 - i, and the a-face index i (at (i + 1) h_a) to n - 2 - i (mod n on a
@@ -142,6 +142,30 @@ def test_multigrid_step_commutes_with_reflection(bc, ax):
         o.rk2_step_mg(u, p, 0.04 * min(h), 2)
         return {c: o.interior(a).copy() for c, a in zip("uvwp", u + [p])}
     close(mg_step(refl(f, ax)), refl(mg_step(f), ax))
+
+
+@pytest.mark.parametrize("form", ["advective", "flux"])
+@pytest.mark.parametrize("ax", ["x", "z"])
+def test_adjoint_gradient_commutes_with_reflection(form, ax):
+    """A reflection R is a signed permutation (orthogonal), so for the loss
+    L = 1/2 |u_T - t|^2 the gradient at (R u_0, R t) is R applied to the
+    gradient at (u_0, t), and dL/dnu is the same."""
+    dims, h = (9, 8, 7), (0.21, 0.17, 0.13)
+    f = rand_fields(dims, 11)
+    t = rand_fields(dims, 12)
+
+    def grad(fl, target):
+        o = Oracle(dims, ghost=1, h=h, bc="periodic", nu=0.03, form=form)
+        u, p = o.state(fl)
+        tt = [target[c] for c in "uvw"]
+        loss = lambda ut: (0.5 * sum(float(((a - b) ** 2).sum()) for a, b in zip(ut, tt)),
+                           [a - b for a, b in zip(ut, tt)])
+        _, du, dp, dnu = o.gradient(u, p, 0.04 * min(h), 6, 2, loss)
+        return {"u": du[0], "v": du[1], "w": du[2], "p": dp}, dnu
+    ga, na = grad(reflect(f, ax), reflect(t, ax))
+    gb, nb = grad(f, t)
+    close(ga, reflect(gb, ax))
+    assert abs(na - nb) <= 1e-12 * abs(nb)
 
 
 def test_reflection_is_an_involution_and_breaks_a_shifted_index():
