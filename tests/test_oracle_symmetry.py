@@ -4,7 +4,9 @@ sizes), for both advection forms and both orders, on periodic grids; and
 with the reflection of z on the lid-driven cavity (lid in the x-z plane at
 y = 1, moving along x), and with the reflection of x there when the lid's
 velocity is reversed; a step with multigrid solves on power-of-two
-grids; and the adjoint's gradients.
+grids; and the adjoint's gradients.  Whole-cell translations of a
+periodic grid commute with the step bitwise (for the V-cycle step, shifts
+by whole coarsest-level cells, 2^levels fine cells).
 
 On the staggered grid a reflection of axis a maps a cell-centred index i to
 n - 1 - i, and the a-face index i (at (i + 1) h_a) to n - 2 - i (mod n on a
@@ -166,6 +168,50 @@ def test_adjoint_gradient_commutes_with_reflection(form, ax):
     gb, nb = grad(f, t)
     close(ga, reflect(gb, ax))
     assert abs(na - nb) <= 1e-12 * abs(nb)
+
+
+def shift(f, d):
+    """Periodic translation by d = (dx, dy, dz) whole cells."""
+    return {c: np.roll(a, (d[2], d[1], d[0]), axis=(0, 1, 2)) for c, a in f.items()}
+
+
+@pytest.mark.parametrize("form,ghost,order", [("advective", 1, 2), ("flux", 1, 2),
+                                              ("advective", 2, 4)])
+def test_periodic_step_commutes_with_translation_bitwise(form, ghost, order):
+    """Every cell does the same arithmetic in the same order, so a shift by
+    whole cells commutes with the step exactly."""
+    dims, h = (9, 8, 7), (0.21, 0.17, 0.13)
+    f = rand_fields(dims, 13)
+    d = (3, 5, 1)
+    a = step(dims, h, shift(f, d), "periodic", form, ghost, order)
+    b = shift(step(dims, h, f, "periodic", form, ghost, order), d)
+    for c in "uvwp":
+        assert np.array_equal(a[c], b[c]), c
+
+
+def test_multigrid_step_commutes_with_coarse_aligned_translation_bitwise():
+    """A shift by a multiple of the coarsest level's cell (2^levels fine
+    cells, levels = the number of halvings) maps every level's cells onto
+    cells of the same level."""
+    dims, h = (32, 16, 16), (0.05, 0.07, 0.09)
+    f = rand_fields(dims, 14)
+
+    def mg_step(fl):
+        o = Oracle(dims, ghost=1, h=h, bc="periodic", nu=0.03)
+        u, p = o.state(fl)
+        o.rk2_step_mg(u, p, 0.04 * min(h), 2)
+        return {c: o.interior(a).copy() for c, a in zip("uvwp", u + [p])}, o.mg_max_levels()
+    b, levels = mg_step(f)
+    unit = 2 ** levels
+    assert levels == 3 and unit == 8
+    d = (3 * unit, unit, unit)
+    a, _ = mg_step(shift(f, d))
+    for c in "uvwp":
+        assert np.array_equal(a[c], shift(b, d)[c]), c
+    # half a coarsest cell moves the coarse grids against the fine one
+    half = (unit // 2,) * 3
+    a, _ = mg_step(shift(f, half))
+    assert np.abs(a["u"] - shift(b, half)["u"]).max() > 1e-6
 
 
 def test_reflection_is_an_involution_and_breaks_a_shifted_index():
