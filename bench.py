@@ -9,7 +9,9 @@ in the CUDA library, replayed from one CUDA graph per step.
 
 Prints one JSON line: GLUP/s (interior cells x steps / s / 1e9), the Jacobi
 sweep against the measured HBM roofline, an end-to-end figure through the C
-ABI with host buffers, and the FP64 oracle timed on the host cores.
+ABI with page-locked host buffers (u, v, w, p copied in and out every step;
+three independent problems in flight, and one problem alone as
+e2e.serial), and the FP64 oracle timed on the host cores.
 N > 1 (torchrun): N independent replicas, one per GPU ("replicas only": the
 single-GPU path has no data exchange between GPUs); value = cells of all
 ranks / slowest rank's time.
