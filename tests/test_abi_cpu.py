@@ -1,5 +1,8 @@
 """CPU-side checks of the C ABI: the library builds, loads, and exports every
-entry point the public header declares (no compute calls without a GPU)."""
+entry point the public header declares; argument errors (a null grid, bad
+sizes, cell sizes or storage types, block sets that are not rectilinear
+tilings) come back as status codes before any device call (no compute
+calls without a GPU)."""
 import os
 import re
 
