@@ -69,6 +69,8 @@ def parse():
     a = ap.parse_args()
     if a.warmup < 3:
         ap.error("--warmup must be >= 3")
+    if a.e2e_in_flight < 2:
+        ap.error("--e2e-in-flight must be >= 2 (e2e.serial is the one-problem figure)")
     return a
 
 
@@ -612,7 +614,7 @@ def run_gpu(a):
     if not a.no_e2e:
         tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
         host_in = [torch.empty((n, n, n), dtype=tdt, pin_memory=True) for _ in range(4)]
-        nf = max(2, a.e2e_in_flight)
+        nf = a.e2e_in_flight
         host_out = [[torch.empty((n, n, n), dtype=tdt, pin_memory=True) for _ in range(4)]
                     for _ in range(nf)]
         for k, arr in enumerate((U, V, W, P)):

@@ -94,3 +94,14 @@ def test_reference_arm_line(monkeypatch, capsys):
                         "d2h_bytes_per_step": 0}
     assert d["ms_per_step"] == pytest.approx(512 ** 3 / 0.012e9 * 1e3)
     assert d["config"]["workload"] == "ldc512" and d["higher_is_better"] is True
+
+
+def test_bench_arguments(monkeypatch):
+    import bench
+    monkeypatch.setattr("sys.argv", ["bench.py"])
+    a = bench.parse()
+    assert (a.gpus, a.warmup, a.e2e_in_flight, a.impl) == (1, 5, 3, "gb300")
+    for bad in (["--warmup", "2"], ["--e2e-in-flight", "1"]):
+        monkeypatch.setattr("sys.argv", ["bench.py"] + bad)
+        with pytest.raises(SystemExit):
+            bench.parse()
