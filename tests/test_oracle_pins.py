@@ -376,12 +376,15 @@ def test_jacobi_neumann_eigenmode_closed_form():
     np.testing.assert_allclose(o.interior(o.laplace_p(q)), lam * e, atol=1e-10)
 
 
-def test_exact_solve_projection_is_divergence_free_and_idempotent():
+@pytest.mark.parametrize("g,order", [(1, 2), (2, 2), (2, 4)])
+def test_exact_solve_projection_is_divergence_free_and_idempotent(g, order):
     """With the exact (FFT) Poisson solve, D G = L, so u = w - G p has D u = 0
-    to rounding and projecting u again leaves it unchanged."""
+    to rounding and projecting u again leaves it unchanged.  The projection
+    is the compact second-order one for either order of the right-hand side
+    and either ghost width."""
     rng = np.random.default_rng(41)
     n, h = (12, 10, 8), H3
-    o = Oracle(n, ghost=1, h=h)
+    o = Oracle(n, ghost=g, h=h, order=order)
     w = [o.ghost_fill(o.embed(rng.standard_normal(n[::-1])), c) for c in range(3)]
     r = o.divergence(w)
     p = o.ghost_fill(o.embed(exact_poisson_periodic(o.interior(r), h)), 3)
