@@ -328,8 +328,9 @@ def test_random_div_free_field_has_zero_discrete_divergence():
     assert max(np.abs(fl[c]).max() for c in "uvw") == pytest.approx(1.0)
 
 
+@pytest.mark.parametrize("g", [1, 2])
 @pytest.mark.parametrize("omega", [1.0, 0.8])
-def test_jacobi_periodic_eigenmode_closed_form(omega):
+def test_jacobi_periodic_eigenmode_closed_form(omega, g):
     """For r an eigenmode e of the periodic operator (L e = lam e) and p0 = 0,
     K weighted Jacobi sweeps give p_K = (1 - rho^K) e / lam with
     rho = 1 - omega (1 - s / diag), s = sum_d 2 cos(theta_d) / h_d^2."""
@@ -337,7 +338,7 @@ def test_jacobi_periodic_eigenmode_closed_form(omega):
     h = H3
     kw = (1, 2, 3)
     th = [2 * math.pi * kw[a] / n[a] for a in range(3)]
-    o = Oracle(n, ghost=1, h=h, omega=omega)
+    o = Oracle(n, ghost=g, h=h, omega=omega)
     k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
     e = np.cos(th[0] * i + th[1] * j + th[2] * k + 0.3)
     s = sum(2 * math.cos(th[a]) / h[a] ** 2 for a in range(3))
@@ -351,13 +352,14 @@ def test_jacobi_periodic_eigenmode_closed_form(omega):
     np.testing.assert_allclose(o.interior(p), (1 - rho ** K) * e / lam, rtol=0, atol=1e-12)
 
 
-def test_jacobi_neumann_eigenmode_closed_form():
+@pytest.mark.parametrize("g", [1, 2])
+def test_jacobi_neumann_eigenmode_closed_form(g):
     """Zero-gradient ghosts make cos(pi m (i+1/2)/N) eigenvectors with
     eigenvalue (2 cos(pi m / N) - 2) / h^2 per axis (the DCT-II basis)."""
     n = (7, 6, 5)
     h = H3
     mm = (2, 1, 3)
-    o = Oracle(n, ghost=1, h=h, bc="cavity")
+    o = Oracle(n, ghost=g, h=h, bc="cavity")
     k, j, i = np.meshgrid(np.arange(n[2]), np.arange(n[1]), np.arange(n[0]), indexing="ij")
     idx = (i, j, k)
     e = np.ones(i.shape)
