@@ -52,6 +52,37 @@ def test_cavity_pressure_ghosts_equal_numpy_symmetric():
     np.testing.assert_array_equal(f, np.pad(a, 1, mode="symmetric"))
 
 
+@pytest.mark.parametrize("g", [1, 2])
+def test_cavity_ghost_layers(g):
+    """Every ghost layer: pressure mirrors evenly (np.pad 'symmetric'); a
+    tangential component mirrors oddly about the wall velocity (the mean of
+    a ghost and its mirror image is U_wall); the wall-normal component is
+    zero on every ghost layer (at the low wall the first of them, index -1,
+    is the wall face itself)."""
+    rng = np.random.default_rng(14)
+    n = (6, 7, 5)
+    o = Oracle(n, ghost=g, h=H3, bc="cavity", lid=1.0)
+    a = rng.standard_normal(n[::-1])
+    np.testing.assert_array_equal(o.ghost_fill(o.embed(a, fill=np.nan), 3),
+                                  np.pad(a, g, mode="symmetric"))
+    u, v, w = [o.ghost_fill(o.embed(rng.standard_normal(n[::-1]), fill=np.nan), c)
+               for c in range(3)]
+    I = slice(g, -g)
+    for m in range(1, g + 1):
+        lo, hi = g - m, -g - 1 + m       # ghost m below / above the interior
+        mlo, mhi = g + m - 1, -g - m     # its mirror image
+        np.testing.assert_allclose(0.5 * (u[I, hi, I] + u[I, mhi, I]), 1.0, atol=1e-15)  # lid
+        np.testing.assert_allclose(0.5 * (u[I, lo, I] + u[I, mlo, I]), 0.0, atol=1e-15)
+        np.testing.assert_allclose(0.5 * (v[I, I, lo] + v[I, I, mlo]), 0.0, atol=1e-15)
+        np.testing.assert_allclose(0.5 * (w[I, hi, I] + w[I, mhi, I]), 0.0, atol=1e-15)
+        np.testing.assert_array_equal(u[I, I, lo], 0.0)
+        np.testing.assert_array_equal(u[I, I, hi], 0.0)
+        np.testing.assert_array_equal(v[I, lo, I], 0.0)
+        np.testing.assert_array_equal(v[I, hi, I], 0.0)
+        np.testing.assert_array_equal(w[lo, I, I], 0.0)
+        np.testing.assert_array_equal(w[hi, I, I], 0.0)
+
+
 def test_cavity_velocity_ghosts_no_slip_and_lid():
     rng = np.random.default_rng(13)
     n = (6, 7, 5)
