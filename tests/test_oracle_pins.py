@@ -83,6 +83,48 @@ def test_cavity_ghost_layers(g):
         np.testing.assert_array_equal(w[hi, I, I], 0.0)
 
 
+def _wall_fill_numpy(a, comp, g, lid, order=(0, 1, 2)):
+    """The cavity ghost fill written with numpy slices: passes over x, then
+    y, then z (or the given axis order), each over the whole extent of the
+    other two axes, so on edges and corners the later pass wins."""
+    f = a.copy()
+    for ax in order:
+        arr_ax = 2 - ax
+        n = f.shape[arr_ax] - 2 * g
+        at = lambda i: tuple(i if d == arr_ax else slice(None) for d in range(3))
+        u_hi = lid if (comp == 0 and ax == 1) else 0.0
+        for m in range(1, g + 1):
+            lo, hi = g - m, n + g - 1 + m
+            mlo, mhi = g + m - 1, n + g - m
+            if comp == 3:
+                f[at(lo)], f[at(hi)] = f[at(mlo)], f[at(mhi)]
+            elif comp == ax:
+                f[at(lo)], f[at(hi)] = 0.0, 0.0
+            else:
+                f[at(lo)] = 2.0 * 0.0 - f[at(mlo)]
+                f[at(hi)] = 2.0 * u_hi - f[at(mhi)]
+    return f
+
+
+@pytest.mark.parametrize("g", [1, 2])
+@pytest.mark.parametrize("comp", [0, 1, 2, 3])
+def test_cavity_ghost_fill_edges_and_corners(g, comp):
+    """The whole padded array after the oracle's cavity fill, edges and
+    corners included, equals the numpy passes x -> y -> z bitwise."""
+    rng = np.random.default_rng(15 + comp)
+    n = (6, 7, 5)
+    o = Oracle(n, ghost=g, h=H3, bc="cavity", lid=1.0)
+    e = o.embed(rng.standard_normal(n[::-1]), fill=np.nan)
+    got = o.ghost_fill(e.copy(), comp)
+    ref = _wall_fill_numpy(e, comp, g, 1.0)
+    assert np.isfinite(got).all()
+    np.testing.assert_array_equal(got, ref)
+    if comp == 0:  # the pass order shows where the lid meets a still wall
+        rev = _wall_fill_numpy(e, 0, g, 1.0, order=(2, 1, 0))
+        edge = (g - 1, -g, slice(g, -g))  # z ghost -1, first y ghost above the lid
+        np.testing.assert_allclose(np.abs(got[edge] - rev[edge]), 4.0, rtol=1e-12)
+
+
 def test_cavity_velocity_ghosts_no_slip_and_lid():
     rng = np.random.default_rng(13)
     n = (6, 7, 5)
