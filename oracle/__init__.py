@@ -3,5 +3,5 @@
 TEST INFRASTRUCTURE ONLY: used by tests/, the smoke check and the CPU-baseline
 leg of bench.py.  It shares no code with the CUDA library.
 """
-from .oracle import (Oracle, bc_faces, build, exact_poisson_periodic, set_threads,  # noqa: F401
-                     PERIODIC, WALL)
+from .oracle import (Oracle, bc_faces, build, compile_sources, exact_poisson_periodic,  # noqa: F401
+                     load_library, set_threads, source_paths, PERIODIC, WALL)

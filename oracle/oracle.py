@@ -35,8 +35,7 @@ def build(force: bool = False) -> str:
         return _LIB_PATH
     os.makedirs(_BUILD, exist_ok=True)
     tmp = _LIB_PATH + ".%d.tmp" % os.getpid()
-    cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-fopenmp", "-o", tmp] + srcs + ["-lm"]
-    subprocess.run(cmd, check=True)
+    compile_sources(srcs, tmp)
     os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -56,57 +55,80 @@ class _Mg(ctypes.Structure):
 _D = ctypes.POINTER(ctypes.c_double)
 
 
+def _configure(lib):
+    """Argument and result types of every oracle entry point on a loaded
+    library."""
+    G = ctypes.POINTER(_Grid)
+    P3 = _D * 3
+    sig = {
+        "ora_ghost_fill": [G, _D, ctypes.c_int],
+        "ora_rhs": [G, _D, _D, _D, _D, _D, _D],
+        "ora_stage": [G, ctypes.c_double, P3, ctypes.c_double, P3, ctypes.c_double, P3],
+        "ora_divergence": [G, P3, ctypes.c_double, _D],
+        "ora_jacobi_sweep": [G, _D, _D, _D],
+        "ora_jacobi": [G, _D, _D, _D, ctypes.c_int],
+        "ora_project": [G, P3, _D, ctypes.c_double, P3],
+        "ora_rk2_step": [G, P3, _D, ctypes.c_double, ctypes.c_int, _D * 8],
+        "ora_reduce": [G, P3, _D, _D, _D],
+        "ora_residual": [G, _D, _D],
+        "ora_laplace_p": [G, _D, _D],
+    }
+    for name, args in sig.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = ctypes.c_double if name == "ora_residual" else None
+    adj = {
+        "ora_ghost_fold": [G, _D, ctypes.c_int],
+        "ora_adj_stage": [G, ctypes.c_double, P3, ctypes.c_double, P3, ctypes.c_double,
+                          P3, P3, _D],
+        "ora_adj_rk2_step": [G, P3, P3, ctypes.c_double, ctypes.c_int, P3, _D, _D,
+                             _D * 11],
+    }
+    for name, args in adj.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = None
+    mg = {
+        "ora_mg_restrict_residual": [G, _D, _D, _D],
+        "ora_mg_prolong_add": [G, _D, _D],
+        "ora_mg_vcycle": [G, ctypes.POINTER(_Mg), _D, _D],
+        "ora_rk2_step_mg": [G, P3, _D, ctypes.c_double, ctypes.POINTER(_Mg), ctypes.c_int,
+                            _D * 8],
+    }
+    for name, args in mg.items():
+        fn = getattr(lib, name)
+        fn.argtypes = args
+        fn.restype = None
+    lib.ora_mg_max_levels.argtypes = [G]
+    lib.ora_mg_max_levels.restype = ctypes.c_int
+    lib.ora_set_threads.argtypes = [ctypes.c_int]
+    lib.ora_set_threads.restype = ctypes.c_int
+    return lib
+
+
+def load_library(path: str):
+    """A configured ctypes handle of an oracle build at `path` (the tests'
+    planted-error checks load altered builds of the same sources this way)."""
+    return _configure(ctypes.CDLL(path))
+
+
+def compile_sources(sources, out_path: str) -> str:
+    """gcc the given C files (plain C99, -O2, OpenMP) into a shared library."""
+    cmd = ["gcc", "-std=c99", "-O2", "-fPIC", "-shared", "-fopenmp", "-I", _HERE, "-o",
+           out_path] + list(sources) + ["-lm"]
+    subprocess.run(cmd, check=True)
+    return out_path
+
+
+def source_paths():
+    return [os.path.join(_HERE, s) for s in _SOURCES]
+
+
 def _load():
     global _lib
     with _lock:
         if _lib is None:
-            lib = ctypes.CDLL(build())
-            G = ctypes.POINTER(_Grid)
-            P3 = _D * 3
-            sig = {
-                "ora_ghost_fill": [G, _D, ctypes.c_int],
-                "ora_rhs": [G, _D, _D, _D, _D, _D, _D],
-                "ora_stage": [G, ctypes.c_double, P3, ctypes.c_double, P3, ctypes.c_double, P3],
-                "ora_divergence": [G, P3, ctypes.c_double, _D],
-                "ora_jacobi_sweep": [G, _D, _D, _D],
-                "ora_jacobi": [G, _D, _D, _D, ctypes.c_int],
-                "ora_project": [G, P3, _D, ctypes.c_double, P3],
-                "ora_rk2_step": [G, P3, _D, ctypes.c_double, ctypes.c_int, _D * 8],
-                "ora_reduce": [G, P3, _D, _D, _D],
-                "ora_residual": [G, _D, _D],
-                "ora_laplace_p": [G, _D, _D],
-            }
-            for name, args in sig.items():
-                fn = getattr(lib, name)
-                fn.argtypes = args
-                fn.restype = ctypes.c_double if name == "ora_residual" else None
-            adj = {
-                "ora_ghost_fold": [G, _D, ctypes.c_int],
-                "ora_adj_stage": [G, ctypes.c_double, P3, ctypes.c_double, P3, ctypes.c_double,
-                                  P3, P3, _D],
-                "ora_adj_rk2_step": [G, P3, P3, ctypes.c_double, ctypes.c_int, P3, _D, _D,
-                                     _D * 11],
-            }
-            for name, args in adj.items():
-                fn = getattr(lib, name)
-                fn.argtypes = args
-                fn.restype = None
-            mg = {
-                "ora_mg_restrict_residual": [G, _D, _D, _D],
-                "ora_mg_prolong_add": [G, _D, _D],
-                "ora_mg_vcycle": [G, ctypes.POINTER(_Mg), _D, _D],
-                "ora_rk2_step_mg": [G, P3, _D, ctypes.c_double, ctypes.POINTER(_Mg), ctypes.c_int,
-                                    _D * 8],
-            }
-            for name, args in mg.items():
-                fn = getattr(lib, name)
-                fn.argtypes = args
-                fn.restype = None
-            lib.ora_mg_max_levels.argtypes = [G]
-            lib.ora_mg_max_levels.restype = ctypes.c_int
-            lib.ora_set_threads.argtypes = [ctypes.c_int]
-            lib.ora_set_threads.restype = ctypes.c_int
-            _lib = lib
+            _lib = load_library(build())
     return _lib
 
 
@@ -135,12 +157,12 @@ class Oracle:
     """One block of the FP64 scheme with its boundary table and parameters."""
 
     def __init__(self, dims, ghost=1, h=(1.0, 1.0, 1.0), bc="periodic", nu=0.0, omega=1.0,
-                 order=2, lid=1.0, form="advective"):
+                 order=2, lid=1.0, form="advective", lib=None):
         if form not in FORMS:
             raise ValueError(f"form must be one of {sorted(FORMS)}")
         if form == "flux" and int(order) != 2:
             raise ValueError("the flux form is order 2")
-        self.lib = _load()
+        self.lib = _load() if lib is None else lib
         self.form = form
         self.dims = tuple(int(d) for d in dims)
         self.g = int(ghost)
