@@ -1,7 +1,8 @@
 /* FP64 CPU oracle: forward time step.  TEST INFRASTRUCTURE ONLY (see the
  * header).  Plain loops over (k, j, i); OpenMP, when enabled, only splits the
- * k loop of point-wise updates, and every sum is taken in a fixed order, so
- * results do not depend on the thread count.
+ * rows (k, j) of point-wise updates, each of which writes its own outputs
+ * (so a grid of a single plane still uses every core), and every sum is
+ * taken in a fixed order, so results do not depend on the thread count.
  *
  * Scheme (readings of Sec. 4.1, Eq. 1-2 and the Method of Lines of Sec. 1):
  *  - MAC grid: p at cell centres, u/v/w on the +x/+y/+z faces of cell (i,j,k).
@@ -65,6 +66,9 @@ void ora_ghost_fill(const ora_grid* G, double* f, int kind) {
   const int g = G->g;
   for (int a = 0; a < 3; ++a) {
     const int b = (a + 1) % 3, c = (a + 2) % 3;
+    /* within the pass along a, every write is a ghost layer of a and every
+     * read an interior index of a (dims >= 2g), so the rows are independent */
+#pragma omp parallel for collapse(2) schedule(static)
     for (int qc = -g; qc < G->n[c] + g; ++qc)
       for (int qb = -g; qb < G->n[b] + g; ++qb)
         for (int m = 1; m <= g; ++m) {
@@ -157,7 +161,7 @@ void ora_rhs(const ora_grid* G, const double* u, const double* v, const double* 
              double* fv, double* fw) {
   const double* f[3] = {u, v, w};
   double* out[3] = {fu, fv, fw};
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {
@@ -174,7 +178,7 @@ static inline int wall_face(const ora_grid* G, int c, const int p[3]) {
 
 void ora_stage(const ora_grid* G, double a, const double* const x[3], double b,
                const double* const y[3], double c, double* const out[3]) {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {
@@ -195,7 +199,7 @@ void ora_stage(const ora_grid* G, double a, const double* const x[3], double b,
 /* ------------------------------------------------------------- pressure */
 
 void ora_divergence(const ora_grid* G, const double* const w[3], double c_dt, double* r) {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {
@@ -210,7 +214,7 @@ void ora_divergence(const ora_grid* G, const double* const w[3], double c_dt, do
 void ora_jacobi_sweep(const ora_grid* G, const double* p, const double* r, double* p_out) {
   double diag = 0.0;
   for (int d = 0; d < 3; ++d) diag += 2.0 / (G->h[d] * G->h[d]);
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {
@@ -238,7 +242,7 @@ void ora_jacobi(const ora_grid* G, double* p, const double* r, double* tmp, int 
 
 void ora_project(const ora_grid* G, const double* const w[3], const double* p, double c_dt,
                  double* const u_out[3]) {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {
@@ -326,7 +330,7 @@ void ora_reduce(const ora_grid* G, const double* const u[3], double* ke, double*
 }
 
 void ora_laplace_p(const ora_grid* G, const double* p, double* lp) {
-#pragma omp parallel for schedule(static)
+#pragma omp parallel for collapse(2) schedule(static)
   for (int k = 0; k < G->n[2]; ++k)
     for (int j = 0; j < G->n[1]; ++j)
       for (int i = 0; i < G->n[0]; ++i) {

@@ -49,9 +49,13 @@ def test_single_process_aggregate_is_identity():
     assert ms == 20.0 and value == pytest.approx(2_000_000 / 20e-3 / 1e9)
 
 
-def _ref_args(steps=3):
+SMALL = dict(desc="test cavity", dims=(12, 10, 8), ghost=1, nu=1e-3, steps=10, order=2,
+             jacobi_iters=6, bc="cavity", ic="ldc_noise", seed=1)
+
+
+def _ref_args(steps=3, workload="ldc_small"):
     import argparse
-    return argparse.Namespace(steps=steps, warmup=3, workload="ldc512")
+    return argparse.Namespace(steps=steps, warmup=3, workload=workload)
 
 
 def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
@@ -64,36 +68,60 @@ def test_reference_arm_other_ranks_do_no_work(monkeypatch, capsys):
 
     def no_call(*a, **k):
         raise AssertionError("rank 1 ran the oracle")
-    monkeypatch.setattr(bench, "oracle_sample", no_call)
-    bench.run_reference(_ref_args())
+    monkeypatch.setattr(bench.workloads, "ldc_noise", no_call)
+    bench.run_reference(_ref_args(workload="ldc512"))
     assert capsys.readouterr().out == ""
 
 
-def test_reference_arm_line(monkeypatch, capsys):
-    """Rank 0 prints one JSON line: the median of the per-step oracle
-    samples as value, the same figure as cpu_baseline and e2e (no host
-    transfers), and the time of one 512^3 step at that rate."""
+def _line(monkeypatch, capsys, steps):
     import json
     import bench
     monkeypatch.setenv("RANK", "0")
     monkeypatch.setenv("WORLD_SIZE", "1")
-    rates = iter([0.010, 0.014, 0.012])
-
-    def fake_sample(detail=True, seconds_hint=False):
-        return {"value": next(rates), "unit": bench.UNIT, "cores": 4, "kind": "oracle",
-                "sample": "fake"}
-    monkeypatch.setattr(bench, "oracle_sample", fake_sample)
-    bench.run_reference(_ref_args(3))
+    monkeypatch.setitem(bench.workloads.WORKLOADS, "ldc_small", SMALL)
+    bench.run_reference(_ref_args(steps))
     lines = capsys.readouterr().out.strip().splitlines()
     assert len(lines) == 1
-    d = json.loads(lines[0])
-    assert d["impl"] == "reference" and d["steps"] == 3
-    assert d["value"] == pytest.approx(0.012)
+    return json.loads(lines[0])
+
+
+def test_reference_arm_times_the_steps_it_reports(monkeypatch, capsys):
+    """Rank 0 prints one JSON line for the configured workload: steps timed,
+    their mean time, value = cells x steps / timed seconds; cpu_baseline and
+    e2e carry the same figure (no host transfers).  The oracle's state after
+    the line's steps equals a direct run of the same steps."""
+    import math
+    import pytest
+    import workloads
+    from oracle import Oracle
+    d = _line(monkeypatch, capsys, 3)
+    nx, ny, nz = SMALL["dims"]
+    assert d["impl"] == "reference" and d["steps"] == 3 and d["steps_requested"] == 3
+    assert d["config"]["workload"] == "ldc_small" and d["config"]["dims"] == [nx, ny, nz]
+    total = sum(d["step_seconds"])
+    assert len(d["step_seconds"]) == 3
+    assert d["ms_per_step"] * d["steps"] == pytest.approx(total * 1e3)
+    assert d["value"] == pytest.approx(nx * ny * nz * 3 / total / 1e9)
     assert d["cpu_baseline"]["value"] == d["value"] and d["cpu_baseline"]["kind"] == "oracle"
     assert d["e2e"] == {"value": d["value"], "unit": d["unit"], "h2d_bytes_per_step": 0,
                         "d2h_bytes_per_step": 0}
-    assert d["ms_per_step"] == pytest.approx(512 ** 3 / 0.012e9 * 1e3)
-    assert d["config"]["workload"] == "ldc512" and d["higher_is_better"] is True
+    assert d["higher_is_better"] is True
+    h = tuple(1.0 / n for n in SMALL["dims"])
+    o = Oracle(SMALL["dims"], ghost=1, h=h, bc="cavity", nu=SMALL["nu"])
+    u, p = o.state(workloads.ldc_noise(SMALL["dims"], seed=1))
+    o.run(u, p, workloads.cfl_dt(h), SMALL["jacobi_iters"], 3)
+    ke, umax, divmax = o.reduce(u)
+    assert d["check"] == {"kinetic_energy": ke, "max_abs_u": umax, "max_abs_div": divmax}
+    assert math.isfinite(ke) and ke > 0
+
+
+def test_reference_arm_stops_at_its_budget(monkeypatch, capsys):
+    import bench
+    monkeypatch.setattr(bench, "REF_BUDGET_S", 0.0)
+    d = _line(monkeypatch, capsys, 4)
+    assert d["steps"] == 1 and d["steps_requested"] == 4
+    assert "stopped after 1 of 4 requested steps" in d["cpu_baseline"]["sample"]
+    assert d["ms_per_step"] == sum(d["step_seconds"]) * 1e3
 
 
 def test_bench_arguments(monkeypatch):
