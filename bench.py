@@ -310,10 +310,53 @@ def _time_steps(torch, g, dt, warm, steps):
     return a.elapsed_time(b) / steps
 
 
+TG512_STEPS = 500     # run length of the reduced-precision workload
+
+
+def oracle_tg_plane(n, nu, steps, out_path):
+    """FP64 oracle run of the n^3 periodic Taylor-Green workload as its
+    n x n x 1 plane: the flow has no z dependence and the scheme keeps it so
+    bit for bit, so the plane's arithmetic is that of every z-plane of the
+    3-D run.  Saves the interiors of u, v, w, p after `steps` RK2 steps (50
+    Jacobi sweeps per solve) with the seconds taken and the threads used."""
+    import numpy as np
+    from oracle import Oracle, set_threads
+    threads = set_threads(0)
+    h = (2 * math.pi / n,) * 3
+    o = Oracle((n, n, 1), ghost=1, h=h, nu=nu)
+    u, p = o.state(workloads.taylor_green((n, n, 1), h=h))
+    t0 = time.perf_counter()
+    o.run(u, p, workloads.cfl_dt(h), 50, steps)
+    el = time.perf_counter() - t0
+    np.savez(out_path, u=o.interior(u[0])[0], v=o.interior(u[1])[0], w=o.interior(u[2])[0],
+             p=o.interior(p)[0], seconds=el, threads=threads)
+
+
+def start_oracle_tg_plane(n, nu, steps):
+    """Starts oracle_tg_plane in a child process (a new interpreter, so no
+    CUDA state is inherited); returns (process, output path)."""
+    fd, path = tempfile.mkstemp(suffix=".npz")
+    os.close(fd)
+    code = "import bench; bench.oracle_tg_plane(%d, %r, %d, %r)" % (n, nu, steps, path)
+    proc = subprocess.Popen([sys.executable, "-c", code], cwd=ROOT, stdout=subprocess.DEVNULL,
+                            stderr=subprocess.PIPE)
+    return proc, path
+
+
+def _rel_err(got, ref, field):
+    import numpy as np
+    if field == "p":
+        got, ref = got - got.mean(), ref - ref.mean()
+    return float(np.abs(got - ref).max() / np.abs(ref).max())
+
+
 def measure_precision(torch, steps):
-    """512^3 periodic Taylor-Green (nu = 0.005): step time with FP32, BF16
-    and FP16 storage, and each run's max error per field against the FP32
-    run and against the exact solution after warm-up + timed steps."""
+    """512^3 periodic Taylor-Green (nu = 0.005), two ghost layers (the
+    fastest FP32 form: two Jacobi sweeps per launch) with FP32, BF16 and
+    FP16 storage: step time over `steps` timed steps after 3 warm-up steps,
+    then the run continued to TG512_STEPS steps; plane z = n/3 of every
+    field is kept for the error against the FP64 oracle (finish_precision),
+    the FP32 run and the exact solution."""
     import numpy as np
     from paper_1201_2118_gb300 import Grid, U, V, W, P
     n = 512
@@ -322,10 +365,10 @@ def measure_precision(torch, steps):
     nu = workloads.WORKLOADS["tg512"]["nu"]
     plane = workloads.taylor_green((n, n, 1), h=h)
     warm = 3
-    out, fields = {}, {}
+    out, planes = {}, {}
     for dt_name in ("f32", "bf16", "f16"):
         s = torch.cuda.Stream()
-        g = Grid((n, n, n), ghost=1, h=h, dtype=dt_name, stream=s)
+        g = Grid((n, n, n), ghost=2, h=h, dtype=dt_name, stream=s)
         g.set_params(nu, 50, 1.0, 2)
         with torch.cuda.stream(s):
             for arr, c in ((U, "u"), (V, "v"), (W, "w"), (P, "p")):
@@ -334,31 +377,59 @@ def measure_precision(torch, steps):
         g.ghost_fill(0b1111)
         g.autotune(None)
         ms = _time_steps(torch, g, dt, warm, steps)
-        T = (warm + steps) * dt
-        ex = workloads.taylor_green((n, n, 1), h=h, t=T, nu=nu)
+        g.step(dt, TG512_STEPS - warm - steps)
+        torch.cuda.synchronize()
+        g.check()
         with torch.cuda.stream(s):
-            fields[dt_name] = [g.interior(a)[n // 3].double().cpu().numpy() for a in (U, V, P)]
-        err_exact = {}
-        for k, c in enumerate("uvp"):
-            got, ref = fields[dt_name][k], ex[c][0]
-            if c == "p":
-                got, ref = got - got.mean(), ref - ref.mean()
-            err_exact[c] = float(np.abs(got - ref).max() / np.abs(ref).max())
+            planes[dt_name] = {c: g.interior(a)[n // 3].double().cpu().numpy()
+                               for a, c in ((U, "u"), (V, "v"), (W, "w"), (P, "p"))}
+            z_same = all(torch.equal(g.interior(a)[0], g.interior(a)[n // 3]) for a in (U, V, P))
+        T = TG512_STEPS * dt
+        ex = workloads.taylor_green((n, n, 1), h=h, t=T, nu=nu)
         out[dt_name] = {"ms_per_step": ms, "glups": n ** 3 / (ms * 1e-3) / 1e9,
-                        "err_vs_exact": err_exact, "jacobi_config": g.kernel_config()[0]}
+                        "err_vs_exact": {c: _rel_err(planes[dt_name][c], ex[c][0], c)
+                                         for c in "uvp"},
+                        "max_abs_w": float(np.abs(planes[dt_name]["w"]).max()),
+                        "planes_z_independent": bool(z_same),
+                        "jacobi_config": g.kernel_config()[0]}
         del g
         torch.cuda.empty_cache()
     for dt_name in ("bf16", "f16"):
-        e = {}
-        for k, c in enumerate("uvp"):
-            a, b = fields[dt_name][k], fields["f32"][k]
-            if c == "p":
-                a, b = a - a.mean(), b - b.mean()
-            e[c] = float(np.abs(a - b).max() / np.abs(b).max())
-        out[dt_name]["err_vs_f32"] = e
+        out[dt_name]["err_vs_f32"] = {c: _rel_err(planes[dt_name][c], planes["f32"][c], c)
+                                      for c in "uvp"}
         out[dt_name]["speedup_vs_f32"] = out["f32"]["ms_per_step"] / out[dt_name]["ms_per_step"]
-    out["workload"] = "512^3 periodic Taylor-Green, nu=0.005, %d timed steps after %d warm-up; " \
-                      "errors on plane z = n/3 after the run" % (steps, warm)
+    out["workload"] = ("512^3 periodic Taylor-Green, nu=0.005, two ghost layers, %d RK2 steps "
+                       "(%d timed after %d warm-up); errors on plane z = n/3 after the %d steps"
+                       % (TG512_STEPS, steps, warm, TG512_STEPS))
+    return out, planes
+
+
+def finish_precision(out, planes, proc, path, timeout_s=1500):
+    """Adds each storage type's error against the FP64 oracle's plane run
+    (e = max |f - f_oracle| / max |f_oracle| per field, p without its mean;
+    w as max |w|, which is 0 in the oracle)."""
+    import numpy as np
+    try:
+        _, err = proc.communicate(timeout=timeout_s)
+    except subprocess.TimeoutExpired:
+        proc.kill()
+        out["oracle"] = {"error": "oracle run took longer than %d s" % timeout_s}
+        return out
+    if proc.returncode != 0:
+        out["oracle"] = {"error": err.decode(errors="replace")[-400:]}
+        return out
+    ref = np.load(path)
+    os.remove(path)
+    out["oracle"] = {"steps": TG512_STEPS, "seconds": float(ref["seconds"]),
+                     "threads": int(ref["threads"]),
+                     "run": "FP64 C oracle on the 512x512x1 plane of the same start, "
+                            "%d steps, host cores" % TG512_STEPS}
+    for dt_name, pl in planes.items():
+        e = {c: _rel_err(pl[c], ref[c], c) for c in "uvp"}
+        e["w_abs"] = float(np.abs(pl["w"] - ref["w"]).max())
+        out[dt_name]["err_vs_oracle"] = e
+    out["f32"]["within_1e-3_after_run"] = all(out["f32"]["err_vs_oracle"][c] <= 1e-3
+                                              for c in "uvp")
     return out
 
 
@@ -753,10 +824,15 @@ def run_gpu(a):
     if rank == 0 and world == 1 and not a.no_secondary:
         del g
         torch.cuda.empty_cache()
-        secondary = {"precision": measure_precision(torch, a.precision_steps),
-                     "blocks": measure_blocks(torch),
+        # the oracle's reference run for the precision errors starts after
+        # the CPU baseline has been timed and runs beside the GPU work
+        oproc, opath = start_oracle_tg_plane(512, workloads.WORKLOADS["tg512"]["nu"],
+                                             TG512_STEPS)
+        prec, planes = measure_precision(torch, a.precision_steps)
+        secondary = {"blocks": measure_blocks(torch),
                      "adjoint": measure_adjoint(torch),
                      "multigrid": measure_multigrid(torch)}
+        secondary["precision"] = finish_precision(prec, planes, oproc, opath)
 
     if rank == 0:
         line = {

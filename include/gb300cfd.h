@@ -235,8 +235,15 @@ cfd_status cfd_pressure_solve_mg(cfd_grid* g, double c_dt, double rtol, int max_
 typedef enum { CFD_SOLVER_JACOBI = 0, CFD_SOLVER_MG = 1 } cfd_solver;
 cfd_status cfd_set_pressure_solver(cfd_grid* g, int solver, int cycles);
 
-/* F(U) into WU, WV, WW (cfd_stage(g, 0, -, 0, U, 1, W)). */
-cfd_status cfd_rhs_eval(cfd_grid* g);
+/* F(U) = -(U . grad) U + nu lap U (Eq. 1 without the pressure term, f = 0;
+ * the form of cfd_set_advection), U's ghosts filled, wall-normal faces 0:
+ * always into WU, WV, WW (cfd_stage(g, 0, -, 0, U, 1, W)); with out_dev
+ * non-NULL also into three caller-owned device buffers, one per component,
+ * each the compact interiors (x fastest, then y, then z, storage dtype) of
+ * all blocks one after the other in block order.  Any alignment works;
+ * 16-byte aligned buffers move as vectors.  CFD_EINVAL if out_dev is
+ * non-NULL with a NULL entry.  Asynchronous. */
+cfd_status cfd_rhs_eval(cfd_grid* g, void* const out_dev[3]);
 
 /* R = (D W)/c_dt (W ghosts must be filled), then iters weighted Jacobi
  * sweeps on P (warm start, ghosts filled) with the pressure halo refreshed
@@ -380,8 +387,24 @@ cfd_status cfd_set_launch_mode(cfd_grid* g, int per_block);
  * count every kernel node once per replay). */
 cfd_status cfd_stats(const cfd_grid* g, long long* kernel_launches);
 
-/* Waits for the grid's work and reports device-side errors. */
+/* Waits for the grid's work and reports device-side errors: CFD_ETIMEOUT
+ * once any kernel has set the grid's device error flag (a bounded wait ran
+ * out, or a TMA destination was misaligned).  The flag stays set, so later
+ * calls keep reporting it, until memory is bound again (cfd_bind_memory /
+ * cfd_alloc_memory clear it); the CUDA context stays usable. */
 cfd_status cfd_check(cfd_grid* g);
+
+/* Failure-detection self-test (the paper has no counterpart: it checks the
+ * library's own device-wait bound).  Enqueues on the grid's stream one CTA
+ * whose single thread initialises an mbarrier expecting one arrival and
+ * waits for it through the same bounded wait the TMA-staged Jacobi kernels
+ * use (form 0: the inline wait, form 1: the wait with its polling loop out
+ * of line), 2 s of %globaltimer.  Nothing arrives, so the wait runs out,
+ * the kernel sets the device error flag and returns; cfd_check then returns
+ * CFD_ETIMEOUT.  No trap, no fault: the context and the grid's memory stay
+ * usable.  Needs bound memory (CFD_ESTATE otherwise); CFD_EINVAL for
+ * another form.  Asynchronous; takes about 2 s on the device. */
+cfd_status cfd_selftest_wait_timeout(cfd_grid* g, int form);
 
 /* Last error message of the calling thread (never NULL). */
 const char* cfd_last_error(void);

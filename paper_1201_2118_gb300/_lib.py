@@ -40,7 +40,7 @@ SIGNATURES = {
     "cfd_pressure_solve_mg": [c_void_p, c_double, c_double, c_int, P(c_int), P(c_double)],
     "cfd_ghost_fill": [c_void_p, c_uint],
     "cfd_stage": [c_void_p, c_double, c_int, c_double, c_int, c_double, c_int],
-    "cfd_rhs_eval": [c_void_p],
+    "cfd_rhs_eval": [c_void_p, P(c_void_p)],
     "cfd_pressure_solve": [c_void_p, c_double, c_int, P(c_double)],
     "cfd_pressure_solve_converged": [c_void_p, c_double, c_double, c_int, c_int, P(c_int),
                                      P(c_double)],
@@ -64,6 +64,7 @@ SIGNATURES = {
     "cfd_copy_interior": [c_void_p, c_int, c_int, c_void_p, c_int],
     "cfd_set_host_copy": [c_void_p, c_int],
     "cfd_check": [c_void_p],
+    "cfd_selftest_wait_timeout": [c_void_p, c_int],
     "cfd_last_error": [],
     "cfd_reduce_velocity_noalloc": [c_void_p, c_void_p, c_void_p, c_int, P(c_int), c_ll, c_ll,
                                     P(c_double), c_void_p, c_void_p],

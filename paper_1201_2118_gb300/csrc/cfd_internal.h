@@ -93,6 +93,9 @@ cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* m
 // (nz, ny, nx) buffer in device memory: to_compact 0 scatters the buffer
 // into the array, 1 gathers the array into the buffer.
 cudaError_t launch_pack(const Launch& L, int arr, void* compact, int to_compact);
+// One CTA waits (bounded) on an mbarrier that nothing completes; sets the
+// device error flag when the wait runs out (failure-detection self-test).
+cudaError_t launch_wait_probe(const Launch& L, int form);
 
 // Two sweeps per launch (kind 9), src -> dst; single block, walls on all
 // faces, or (periodic) all faces periodic with ghost width >= 2, src's two

@@ -1128,7 +1128,26 @@ cfd_status cfd_stage(cfd_grid* g, double a, int x_set, double b, int y_set, doub
   return join_out(g);
 }
 
-cfd_status cfd_rhs_eval(cfd_grid* g) { return cfd_stage(g, 0.0, 0, 0.0, CFD_SET_U, 1.0, CFD_SET_W); }
+cfd_status cfd_rhs_eval(cfd_grid* g, void* const out_dev[3]) {
+  if (out_dev && (!out_dev[0] || !out_dev[1] || !out_dev[2]))
+    return fail(CFD_EINVAL, "out_dev must be NULL or hold three device pointers");
+  cfd_status s = cfd_stage(g, 0.0, 0, 0.0, CFD_SET_U, 1.0, CFD_SET_W);
+  if (s != CFD_OK || !out_dev) return s;
+  if ((s = join_in(g)) != CFD_OK) return s;
+  for (int c = 0; c < 3; ++c) {
+    size_t off = 0;  // elements: the blocks' interiors one after the other
+    for (int b = 0; b < g->nblocks; ++b) {
+      Launch L = make_launch(g);
+      L.b0 = b;
+      L.nblocks = 1;
+      CK(g, launch_pack(L, A_WU + c, static_cast<char*>(out_dev[c]) + off * g->es, 1));
+      g->launches += 1;
+      const HostBlock& hb = g->hb[b];
+      off += (size_t)hb.n[0] * hb.n[1] * hb.n[2];
+    }
+  }
+  return join_out(g);
+}
 
 cfd_status cfd_pressure_solve(cfd_grid* g, double c_dt, int iters, double* residual) {
   cfd_status s = usable(g);
@@ -1764,6 +1783,16 @@ cfd_status cfd_set_host_copy(cfd_grid* g, int mode) {
     return fail(CFD_EINVAL, "mode must be CFD_HOST_COPY_KERNEL or CFD_HOST_COPY_ENGINE");
   g->host_copy = mode;
   return CFD_OK;
+}
+
+cfd_status cfd_selftest_wait_timeout(cfd_grid* g, int form) {
+  cfd_status s = usable(g);
+  if (s != CFD_OK) return s;
+  if (form != 0 && form != 1) return fail(CFD_EINVAL, "form must be 0 or 1");
+  if ((s = join_in(g)) != CFD_OK) return s;
+  CK(g, launch_wait_probe(make_launch(g), form));
+  g->launches += 1;
+  return join_out(g);
 }
 
 cfd_status cfd_check(cfd_grid* g) {

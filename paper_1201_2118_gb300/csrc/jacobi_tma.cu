@@ -103,6 +103,23 @@ __device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map
       : "memory");
 }
 
+// A wait that nothing completes: one thread initialises an mbarrier that
+// expects one arrival, never arrives, and waits for its first phase through
+// the bounded wait of the TMA-staged kernels (form 0: mbar_wait, form 1:
+// mbar_wait_split, the form with the polling loop out of line).  When the
+// limit runs out it sets bit 2 of the device error flag, as those kernels do
+// on a timeout, and returns; it has no copies in flight and holds no other
+// resource.
+__global__ void __launch_bounds__(32) k_wait_probe(int* err_flag, int form) {
+  __shared__ __align__(8) unsigned long long bar;
+  if (threadIdx.x != 0) return;
+  const uint32_t b = smem_u32(&bar);
+  mbar_init(b, 1);
+  mbar_fence_init();
+  const bool ok = form == 0 ? mbar_wait(b, 0u) : mbar_wait_split(b, 0u);
+  if (!ok) atomicOr(err_flag, 2);
+}
+
 template <typename T, int VX, int TY>
 struct TmaGeom {
   static constexpr int TX = 32 * VX;
@@ -867,6 +884,11 @@ PFN_cuTensorMapEncodeTiled_v12000 encoder() {
 }
 
 }  // namespace
+
+cudaError_t launch_wait_probe(const Launch& L, int form) {
+  k_wait_probe<<<1, 32, 0, L.stream>>>(L.err_flag, form);
+  return cudaGetLastError();
+}
 
 int tma_box_x(int dtype, int vx, int halo) {
   const int es = dtype == 0 ? 4 : 2;

@@ -63,8 +63,10 @@ __global__ void __launch_bounds__(256) k_plane_partials(const T* u, const T* v, 
   float umax = 0.f;
   cfd::FF dmax = {0.f, 0.f};
   int bad = 0;
-  for (int c = threadIdx.x; c < nx * ny; c += 256) {
-    const int i = c % nx, j = c / nx;
+  // 64-bit cell index: nx * ny may come within 256 of 2^31 - 1
+  const long long cells = (long long)nx * ny;
+  for (long long c = threadIdx.x; c < cells; c += 256) {
+    const int i = (int)(c % nx), j = (int)(c / nx);
     const long long o = (long long)k * pz + (long long)j * py + i;
     const float x[3] = {ld(u + o), ld(v + o), ld(w + o)};
     const float xm[3] = {ld(u + o - 1), ld(v + o - py), ld(w + o - pz)};

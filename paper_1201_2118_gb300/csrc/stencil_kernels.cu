@@ -1469,8 +1469,10 @@ __global__ void __launch_bounds__(32 * TY * TZ) k_jacobi_direct(Launch L, int sr
 // ---------------------------------------------------- compact <-> padded
 
 // One warp per interior row: the compact buffer holds rows of nx elements
-// back to back, the array rows start 128-byte aligned at x = 0.  Rows whose
-// compact start is 16-byte aligned move as 16-byte vectors.
+// back to back, the array rows start 128-byte aligned at x = 0.  When the
+// compact buffer starts 16-byte aligned and nx is a multiple of the vector
+// width (so every compact row starts aligned) rows move as 16-byte vectors;
+// otherwise element by element.
 template <typename T>
 __global__ void __launch_bounds__(256) k_pack(Launch L, int arr, T* compact, int to_compact) {
   constexpr int V = 16 / (int)sizeof(T);
@@ -1481,7 +1483,7 @@ __global__ void __launch_bounds__(256) k_pack(Launch L, int arr, T* compact, int
   T* a = reinterpret_cast<T*>(L.base) + B.org[arr];
   const long long rows = (long long)ny * nz;
   const int lane = threadIdx.x & 31;
-  const bool vec = (nx % V) == 0;
+  const bool vec = (nx % V) == 0 && (reinterpret_cast<uintptr_t>(compact) % 16) == 0;
   for (long long r = ((long long)blockIdx.x * blockDim.x + threadIdx.x) >> 5; r < rows;
        r += ((long long)gridDim.x * blockDim.x) >> 5) {
     const int j = (int)(r % ny), k = (int)(r / ny);

@@ -163,8 +163,11 @@ class Grid:
         call("cfd_stage", self.handle, float(a), int(x_set), float(b), int(y_set), float(c),
              int(out_set))
 
-    def rhs_eval(self):
-        call("cfd_rhs_eval", self.handle)
+    def rhs_eval(self, out=None):
+        """F(U) into WU, WV, WW; with out = three device tensors, also their
+        compact interiors (blocks in order) into those."""
+        ptrs = None if out is None else (c_void_p * 3)(*[c_void_p(t.data_ptr()) for t in out])
+        call("cfd_rhs_eval", self.handle, ptrs)
 
     def pressure_solve(self, c_dt: float, iters: int, residual: bool = False):
         r = c_double()
@@ -294,6 +297,11 @@ class Grid:
 
     def check(self):
         call("cfd_check", self.handle)
+
+    def selftest_wait_timeout(self, form: int = 0):
+        """Enqueues the library's bounded-wait self-test (cfd_check then
+        reports CFD_ETIMEOUT)."""
+        call("cfd_selftest_wait_timeout", self.handle, int(form))
 
     @property
     def time(self):

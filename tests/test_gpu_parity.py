@@ -74,6 +74,45 @@ def test_rhs_eval(order, g):
         assert rel_err(grid.download(a), o.interior(F[k])) < 1e-5
 
 
+@pytest.mark.parametrize("misalign", [0, 1])
+def test_rhs_eval_into_caller_buffers(misalign):
+    """cfd_rhs_eval with out_dev: the compact interiors equal WU, WV, WW bit
+    for bit, also into buffers that start 4 bytes past a 16-byte boundary
+    (element-wise path) and on a block set (blocks one after the other)."""
+    import torch
+    from paper_1201_2118_gb300 import Grid, WU, WV, WW
+    fl = rand_fields(RAGGED, 5)
+    o, grid, u, p = make_pair(RAGGED, nu=0.05, fields=fl)
+    nx, ny, nz = RAGGED
+    cells = nx * ny * nz
+    bufs = [torch.full((cells + 4,), float("nan"), device="cuda") for _ in range(3)]
+    outs = [b[misalign:misalign + cells] for b in bufs]
+    grid.rhs_eval(out=outs)
+    torch.cuda.synchronize()
+    for t, a in zip(outs, (WU, WV, WW)):
+        assert torch.equal(t.view(nz, ny, nx), grid.interior(a))
+    F = o.rhs(*u)
+    assert rel_err(outs[0].view(nz, ny, nx).double().cpu().numpy(), o.interior(F[0])) < 1e-5
+    blocks = [((20, 16, 12), (0, 0, 0)), ((13, 16, 12), (20, 0, 0))]
+    bs = Grid(ghost=1, h=(0.2, 0.2, 0.2), blocks=blocks, global_dims=(33, 16, 12))
+    bs.set_params(0.05, 10, 1.0, 2)
+    rng = np.random.default_rng(6)
+    for b, (d, _) in enumerate(blocks):
+        bs.upload({c: rng.uniform(-1, 1, d[::-1]) for c in "uvwp"}, block=b, fill_ghosts=False)
+    bs.ghost_fill(0b1111)
+    total = sum(d[0] * d[1] * d[2] for d, _ in blocks)
+    outs = [torch.full((total + 4,), float("nan"), device="cuda")[misalign:misalign + total]
+            for _ in range(3)]
+    bs.rhs_eval(out=outs)
+    torch.cuda.synchronize()
+    for t, a in zip(outs, (WU, WV, WW)):
+        off = 0
+        for b, (d, _) in enumerate(blocks):
+            n = d[0] * d[1] * d[2]
+            assert torch.equal(t[off:off + n].view(d[2], d[1], d[0]), bs.interior(a, b))
+            off += n
+
+
 def test_rhs_eval_cavity():
     from paper_1201_2118_gb300 import WU, WV, WW
     fl = rand_fields(RAGGED, 4)
@@ -369,6 +408,73 @@ def test_cavity_256_first_steps():
         assert ew < max(1e-5, floor), (step, ew, floor)
         assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < tol_p
         print("ldc256 step", step, errs, "w", ew, "w floor", floor)
+
+
+def test_cavity_512_first_step_bench_configuration():
+    """The bench's own workload and launch configuration: the 512^3 cavity
+    with the Jacobi sweeps two per launch (9, 4, 16, 64, 6) and the RHS ring
+    (8, 64, 1), one step against the oracle's 512^3 step, cell by cell, with
+    the bars of the 256^3 case (w's FP32 pressure floor as there)."""
+    from paper_1201_2118_gb300 import P, W
+    n = 512
+    h = (1.0 / n,) * 3
+    dt = workloads.cfl_dt(h)
+    o, grid, u, p = make_pair((n, n, n), bc="cavity", h=h, nu=1e-3,
+                              fields=workloads.ldc_noise(n, seed=1))
+    grid.set_kernel_config(jacobi=(9, 4, 16, 64, 6), stencil=(8, 64, 1))
+    grid.step(dt, 1)
+    o.rk2_step(u, p, dt, 50)
+    errs = {c: rel_err(grid.download(a), o.interior(u[k]))
+            for k, (c, a) in enumerate(zip("uv", (0, 1)))}
+    assert max(errs.values()) < 1e-5, errs
+    pmax = np.abs(o.interior(p)).max()
+    floor = 4 * np.spacing(np.float32(pmax)) * dt / h[2] / np.abs(o.interior(u[2])).max()
+    ew = rel_err(grid.download(W), o.interior(u[2]))
+    assert ew < max(1e-5, floor), (ew, floor)
+    assert rel_err(grid.download(P), o.interior(p), remove_mean=True) < 1e-5
+    print("ldc512 step 1", errs, "w", ew, "w floor", floor)
+
+
+def test_tg512_against_oracle_plane():
+    """The reduced-precision workload's FP32 run: 512^3 periodic
+    Taylor-Green, nu = 0.005, two ghost layers (two Jacobi sweeps per launch,
+    periodic form), against the oracle on the 512 x 512 x 1 plane, whose
+    arithmetic is that of every z-plane (the flow has no z dependence and the
+    scheme keeps it so bit for bit).  e <= 1e-5 after one step and after
+    five; w stays 0 and every z-plane of the device run is the same."""
+    import torch
+    from paper_1201_2118_gb300 import Grid, U, V, W, P
+    from oracle import Oracle
+    n = 512
+    h = (2 * math.pi / n,) * 3
+    dt = workloads.cfl_dt(h)
+    nu = workloads.WORKLOADS["tg512"]["nu"]
+    plane = rounded(workloads.taylor_green((n, n, 1), h=h))
+    o = Oracle((n, n, 1), ghost=1, h=h, nu=nu)
+    u, p = o.state(plane)
+    grid = Grid((n, n, n), ghost=2, h=h)
+    grid.set_params(nu, 50, 1.0, 2)
+    grid.set_kernel_config(jacobi=(9, 4, 16, 64, 6))
+    with torch.cuda.stream(grid.stream):
+        for arr, c in ((U, "u"), (V, "v"), (W, "w"), (P, "p")):
+            src = torch.from_numpy(plane[c][0]).float().cuda()
+            grid.interior(arr).copy_(src.expand(n, n, n))
+    grid.ghost_fill(0b1111)
+    done = 0
+    for upto in (1, 5):
+        grid.step(dt, upto - done)
+        o.run(u, p, dt, 50, upto - done)
+        done = upto
+        torch.cuda.synchronize()
+        for arr in (U, V, P):
+            full = grid.interior(arr)
+            assert torch.equal(full, full[:1].expand_as(full)), (upto, arr)
+        assert float(grid.interior(W).abs().max()) == 0.0
+        errs = {c: rel_err(grid.interior(a)[n // 3].double().cpu().numpy(),
+                           o.interior(f)[0], remove_mean=(c == "p"))
+                for c, a, f in (("u", U, u[0]), ("v", V, u[1]), ("p", P, p))}
+        assert max(errs.values()) <= 1e-5, (upto, errs)
+        print("tg512 step", upto, errs)
 
 
 @pytest.mark.parametrize("solver,jacobi,stencil", [("jacobi", (9, 4, 16, 64, 6), (8, 64, 1)),

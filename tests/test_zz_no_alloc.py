@@ -14,26 +14,34 @@ import pytest
 pytestmark = pytest.mark.gpu
 
 
-def _noalloc(lib, ints, doubles, g, dims, h, out, arrays):
+DTYPES = {"f32": 0, "bf16": 1, "f16": 2}
+
+
+def _noalloc(lib, ints, doubles, g, dims, h, out, arrays, dtype):
     ptrs = [ctypes.c_void_p(g.interior(a).data_ptr()) for a in arrays]
     sz, sy, _ = g.array(arrays[0]).stride()
-    return lib.cfd_reduce_velocity_noalloc(ptrs[0], ptrs[1], ptrs[2], 0, ints(*dims), sy, sz,
+    return lib.cfd_reduce_velocity_noalloc(ptrs[0], ptrs[1], ptrs[2], DTYPES[dtype], ints(*dims),
+                                           sy, sz,
                                            doubles(*h), ctypes.c_void_p(out.data_ptr()),
                                            ctypes.c_void_p(g.stream.cuda_stream))
 
 
-def test_noalloc_reduce_matches_grid_reduce_on_two_calls():
+@pytest.mark.parametrize("dtype", sorted(DTYPES))
+def test_noalloc_reduce_matches_grid_reduce_on_two_calls(dtype):
+    """Every storage type: the same three quantities as the grid's own
+    reduction, on two calls in a row (the second sees the first call's
+    partial sums left in the shared static array)."""
     import torch
     from paper_1201_2118_gb300 import Grid, U, V, W, SET_U, _lib
     L = _lib.lib()
     dims, h = (45, 37, 21), (0.3, 0.2, 0.1)
     rng = np.random.default_rng(21)
-    g = Grid(dims, ghost=1, h=h)
+    g = Grid(dims, ghost=1, h=h, dtype=dtype)
     out = torch.full((4,), float("nan"), dtype=torch.float64, device="cuda")
     for call in range(2):
         g.upload({c: rng.uniform(-1, 1, dims[::-1]) * (call + 1) for c in "uvwp"})
         ke, umax, divmax = g.reduce(SET_U)
-        st = _noalloc(L, _lib.ints, _lib.doubles, g, dims, h, out, (U, V, W))
+        st = _noalloc(L, _lib.ints, _lib.doubles, g, dims, h, out, (U, V, W), dtype)
         assert st == 0, L.cfd_noalloc_last_error()
         torch.cuda.synchronize()
         got = out.cpu().numpy()
