@@ -64,6 +64,9 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the reduced-precision, block-set and adjoint comparisons")
     ap.add_argument("--precision-steps", type=int, default=20)
+    ap.add_argument("--cuda-connections", type=int, default=0,
+                    help="CUDA_DEVICE_MAX_CONNECTIONS for this process (0: leave as is); "
+                         "hardware work queues shared by the streams")
     ap.add_argument("--tune-cache", default=None,
                     help="autotuner cache file (reused when it holds this GPU and grid)")
     a = ap.parse_args()
@@ -293,6 +296,31 @@ def aggregate(ms_local: float, cells: int, dist=None, device="cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     return ms, world * cells / (ms * 1e-3) / 1e9
+
+
+def pipeline_schedule(origin, marks):
+    """Summary of the end-to-end pipeline from its timing events (ms after
+    `origin`): per problem-step the input copies, the wait for the previous
+    problem's step, the step and the output copies; and the SMs' idle time
+    between consecutive steps (a step that waits for its own input copies,
+    or for nothing, shows up there)."""
+    rows = [[origin.elapsed_time(e) for e in ev] for ev in marks]
+    h2d = [r[1] - r[0] for r in rows]
+    wait = [r[2] - r[1] for r in rows]
+    step = [r[3] - r[2] for r in rows]
+    d2h = [r[4] - r[3] for r in rows]
+    starts = sorted((r[2], r[3]) for r in rows)
+    gaps = [max(0.0, b[0] - a[1]) for a, b in zip(starts, starts[1:])]
+    span = starts[-1][1] - starts[0][0] if starts else 0.0
+
+    def mean(x):
+        return sum(x) / len(x) if x else None
+    return {"h2d_ms": mean(h2d), "h2d_max_ms": max(h2d) if h2d else None,
+            "wait_ms": mean(wait), "step_ms": mean(step), "step_max_ms": max(step) if step else None,
+            "d2h_ms": mean(d2h), "d2h_max_ms": max(d2h) if d2h else None,
+            "gap_between_steps_ms": mean(gaps), "gap_max_ms": max(gaps) if gaps else None,
+            "steps_busy_frac": sum(step) / span if span > 0 else None,
+            "first_steps_ms": [round(r[2], 2) for r in rows[:6]]}
 
 
 # ------------------------------------------------------ secondary measures
@@ -750,20 +778,29 @@ def run_gpu(a):
         # copy engines.  Events chain the input copies and the steps of the
         # problems in turn, so they stay a fraction of a period apart: the
         # others' host transfers run while one problem's step has the SMs.
+        # each problem's copies and step are bracketed by timing events, so
+        # the pipeline's schedule can be read back: when each input copy,
+        # step and output copy ran, and how long the SMs waited between steps
+        marks = []
+
         def piped_step(grid, out, after):
-            in_done, step_done = torch.cuda.Event(), torch.cuda.Event()
+            ev = [torch.cuda.Event(enable_timing=True) for _ in range(5)]
             if after[0] is not None:
                 grid.stream.wait_event(after[0])
+            ev[0].record(grid.stream)
             for k, arr in enumerate((U, V, W, P)):
                 grid.copy_interior(arr, host_in[k].data_ptr(), to_device=True)
-            in_done.record(grid.stream)
+            ev[1].record(grid.stream)
             if after[1] is not None:
                 grid.stream.wait_event(after[1])
+            ev[2].record(grid.stream)
             grid.step(dt, 1)
-            step_done.record(grid.stream)
+            ev[3].record(grid.stream)
             for k, arr in enumerate((U, V, W, P)):
                 grid.copy_interior(arr, out[k].data_ptr(), to_device=False)
-            return in_done, step_done
+            ev[4].record(grid.stream)
+            marks.append(ev)
+            return ev[1], ev[3]
 
         grids = [g]
         for _ in range(nf - 1):
@@ -777,6 +814,7 @@ def run_gpu(a):
         for grid, out in zip(grids, host_out):  # warm-up: captures the step graphs
             host_step(grid, out)
         torch.cuda.synchronize()
+        marks.clear()
         x0, x1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         barrier()
         torch.cuda.synchronize()
@@ -802,11 +840,12 @@ def run_gpu(a):
         del grids, gx
         torch.cuda.empty_cache()
         ems, e2e_value = aggregate(x0.elapsed_time(x1) / (nf * k_e2e), cells, dist, "cuda")
+        schedule = pipeline_schedule(x0, marks)
         es = host_in[0].element_size()
         e2e = {"value": e2e_value, "unit": UNIT,
                "h2d_bytes_per_step": 4 * cells * es, "d2h_bytes_per_step": 4 * cells * es,
                "ms_per_step": ems, "steps": nf * k_e2e, "in_flight": nf,
-               "outputs_equal": same,
+               "outputs_equal": same, "schedule": schedule,
                "api": "per step: cfd_copy_interior (pinned host -> device, u,v,w,p; copy engine) "
                       "+ cfd_step + cfd_copy_interior (device -> pinned host, u,v,w,p); %d "
                       "independent %d^3 problems, one stream each, their input copies and steps "
@@ -862,6 +901,8 @@ def run_gpu(a):
 
 def main():
     a = parse()
+    if a.cuda_connections > 0:  # read when the CUDA context is created
+        os.environ["CUDA_DEVICE_MAX_CONNECTIONS"] = str(a.cuda_connections)
     if a.impl == "reference":
         run_reference(a)
     else:
