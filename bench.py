@@ -45,7 +45,8 @@ def kernel_sources(kind: int):
     """Source files of the Jacobi variant `kind` (the TMA variants live in
     jacobi_tma.cu, the others in stencil_kernels.cu)."""
     main = "jacobi_tma.cu" if kind in (1, 7, 9) else "stencil_kernels.cu"
-    return [os.path.join(CSRC, f) for f in (main, "dev_common.cuh", "tiles.cuh", "cfd_internal.h")]
+    return [os.path.join(CSRC, f) for f in (main, "dev_common.cuh", "tiles.cuh", "tma_ptx.cuh",
+                                            "cfd_internal.h")]
 TRAFFIC_FILE = os.path.join(ROOT, "profiles", "jacobi_dram_traffic.txt")
 
 

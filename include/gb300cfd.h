@@ -353,8 +353,9 @@ cfd_status cfd_set_host_copy(cfd_grid* g, int mode);
  * vx 2 (64-wide tiles, for narrow blocks) with ty in {8,16} and 6 stages),
  * kind 9 two sweeps per launch in the warp-specialised TMA form (temporal
  * blocking; vx 4 with (ty, stages) in {(16,6), (16,7), (8,5), (8,6)}; used on
- * single-block grids whose six faces are walls, odd sweep counts and other
- * grids take single sweeps of kind 0);
+ * single-block grids whose six faces are walls or, with two ghost layers,
+ * are all periodic; odd sweep counts and other grids take single sweeps of
+ * kind 0);
  * zc = z-planes per tile.
  * stencil = {ty in {4,8}, zc, tile_tz in {0..4}} for the point kernels:
  * rows per CTA, z chunk, and for the RHS + stage kernel either neighbour

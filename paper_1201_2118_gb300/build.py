@@ -34,7 +34,8 @@ def sources():
 
 
 def _newest_input() -> float:
-    files = sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(INCLUDE, "*.h"))
+    files = (sources() + glob.glob(os.path.join(CSRC, "*.h")) + glob.glob(os.path.join(CSRC, "*.cuh"))
+             + glob.glob(os.path.join(INCLUDE, "*.h")))
     files.append(os.path.abspath(__file__))
     return max(os.path.getmtime(f) for f in files)
 

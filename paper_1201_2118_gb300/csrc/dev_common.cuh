@@ -119,21 +119,24 @@ __device__ __forceinline__ unsigned long long fma2(unsigned long long a, unsigne
   return r;
 }
 
-// jacobi_update on two cells at once, the same operations in the same order
-// (so the same bits): nb = fma(zm+zp, cz, fma(ym+yp, cy, (xm+xp) cx)),
-// out = fma(omega, fma(nb - r, inv_diag, -c), c).
+// jacobi_update on two cells at once with the same roundings.  The x terms
+// arrive summed (xs = xm + xp, one scalar add per cell, written straight into
+// the pair).  nb = fma(zm+zp, cz, fma(ym+yp, cy, xs cx)); the update
+// fma(w, fma(nb - r, 1/diag, -c), c) is taken as fma(-w, fma(r - nb, 1/diag,
+// c), c): r - nb = -(nb - r) and fma(-a, b, c) = -fma(a, b, -c) exactly
+// (round-to-nearest is symmetric), and -w times -x is w times x, so this is
+// the same value without forming -c (an exact zero may change its sign).
 struct Jac2 {
-  unsigned long long cx, cy, cz, om, inv, m1;
+  unsigned long long cx, cy, cz, mom, inv;
   __device__ __forceinline__ Jac2(float cx_, float cy_, float cz_, float om_, float inv_)
-      : cx(pk2(cx_, cx_)), cy(pk2(cy_, cy_)), cz(pk2(cz_, cz_)), om(pk2(om_, om_)),
-        inv(pk2(inv_, inv_)), m1(pk2(-1.f, -1.f)) {}
+      : cx(pk2(cx_, cx_)), cy(pk2(cy_, cy_)), cz(pk2(cz_, cz_)), mom(pk2(-om_, -om_)),
+        inv(pk2(inv_, inv_)) {}
   __device__ __forceinline__ unsigned long long operator()(
-      unsigned long long c, unsigned long long xm, unsigned long long xp, unsigned long long ym,
-      unsigned long long yp, unsigned long long zm, unsigned long long zp,
-      unsigned long long r) const {
+      unsigned long long c, unsigned long long xs, unsigned long long ym, unsigned long long yp,
+      unsigned long long zm, unsigned long long zp, unsigned long long r) const {
     const unsigned long long nb =
-        fma2(add2(zm, zp), cz, fma2(add2(ym, yp), cy, mul2(add2(xm, xp), cx)));
-    return fma2(om, fma2(sub2(nb, r), inv, mul2(c, m1)), c);
+        fma2(add2(zm, zp), cz, fma2(add2(ym, yp), cy, mul2(xs, cx)));
+    return fma2(mom, fma2(sub2(r, nb), inv, c), c);
   }
 };
 
@@ -143,12 +146,12 @@ __device__ __forceinline__ void jac_row4(const Jac2& J, const float (&c)[4], flo
                                          const float (&zm)[4], const float (&zp)[4],
                                          const float (&r)[4], float (&out)[4]) {
   const unsigned long long c01 = pk2(c[0], c[1]), c23 = pk2(c[2], c[3]);
-  const unsigned long long o01 =
-      J(c01, pk2(left, c[0]), pk2(c[1], c[2]), pk2(ym[0], ym[1]), pk2(yp[0], yp[1]),
-        pk2(zm[0], zm[1]), pk2(zp[0], zp[1]), pk2(r[0], r[1]));
-  const unsigned long long o23 =
-      J(c23, pk2(c[1], c[2]), pk2(c[3], right), pk2(ym[2], ym[3]), pk2(yp[2], yp[3]),
-        pk2(zm[2], zm[3]), pk2(zp[2], zp[3]), pk2(r[2], r[3]));
+  const unsigned long long x01 = pk2(__fadd_rn(left, c[1]), __fadd_rn(c[0], c[2]));
+  const unsigned long long x23 = pk2(__fadd_rn(c[1], c[3]), __fadd_rn(c[2], right));
+  const unsigned long long o01 = J(c01, x01, pk2(ym[0], ym[1]), pk2(yp[0], yp[1]),
+                                   pk2(zm[0], zm[1]), pk2(zp[0], zp[1]), pk2(r[0], r[1]));
+  const unsigned long long o23 = J(c23, x23, pk2(ym[2], ym[3]), pk2(yp[2], yp[3]),
+                                   pk2(zm[2], zm[3]), pk2(zp[2], zp[3]), pk2(r[2], r[3]));
   unpk2(o01, out[0], out[1]);
   unpk2(o23, out[2], out[3]);
 }

@@ -25,83 +25,10 @@
 #include "cfd_internal.h"
 #include "dev_common.cuh"
 #include "tiles.cuh"
+#include "tma_ptx.cuh"
 
 namespace cfd {
 namespace {
-
-// ------------------------------------------------------------- PTX helpers
-
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
-}
-__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
-}
-__device__ __forceinline__ void mbar_fence_init() {
-  asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.b32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ unsigned long long gtimer() {
-  unsigned long long t;
-  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
-  return t;
-}
-constexpr unsigned long long kWaitLimitNs = 2000000000ull;
-
-// try_wait with a suspend-time hint: the waiting thread sleeps until the
-// phase completes or about 100 us have passed, instead of polling
-__device__ __forceinline__ bool mbar_try_wait_sleep(uint32_t bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
-      "selp.b32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(100000)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  if (mbar_try_wait(bar, parity)) return true;
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try_wait_sleep(bar, parity))
-    if (gtimer() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-__device__ __noinline__ bool mbar_wait_slow(uint32_t bar, uint32_t parity) {
-  const unsigned long long t0 = gtimer();
-  while (!mbar_try_wait_sleep(bar, parity))
-    if (gtimer() - t0 > kWaitLimitNs) return false;
-  return true;
-}
-// The same bounded wait with the polling loop out of line (less code in
-// kernels that wait several times per plane; the call raises the register
-// count of kernels that run two CTAs per SM, which use mbar_wait).
-__device__ __forceinline__ bool mbar_wait_split(uint32_t bar, uint32_t parity) {
-  return mbar_try_wait(bar, parity) || mbar_wait_slow(bar, parity);
-}
-__device__ __forceinline__ void tma_load_3d(uint32_t dst, const CUtensorMap* map, int x, int y,
-                                            int z, uint32_t bar) {
-  asm volatile(
-      "cp.async.bulk.tensor.3d.shared::cluster.global.tile.mbarrier::complete_tx::bytes"
-      " [%0], [%1, {%2, %3, %4}], [%5];" ::"r"(dst),
-      "l"(reinterpret_cast<unsigned long long>(map)), "r"(x), "r"(y), "r"(z), "r"(bar)
-      : "memory");
-}
 
 // A wait that nothing completes: one thread initialises an mbarrier that
 // expects one arrival, never arrives, and waits for its first phase through
@@ -307,24 +234,6 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
 // f % S, its full barrier completes phase f / S, and its empty barrier is
 // waited with the opposite parity so the first pass through the ring does
 // not wait.
-
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Position in the ring: stage index and phase parity of plane f.
-template <int S>
-struct Ring {
-  int s;
-  uint32_t ph;
-  __device__ __forceinline__ explicit Ring(unsigned f) : s((int)(f % S)), ph((f / S) & 1u) {}
-  __device__ __forceinline__ void next() {
-    if (++s == S) {
-      s = 0;
-      ph ^= 1u;
-    }
-  }
-};
 
 template <typename T, int VX, int TY, int S>
 __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUtensorMap* maps,
