@@ -66,7 +66,7 @@ struct cfd_grid {
   char* base = nullptr;
   size_t bytes = 0;
   bool owns = false;
-  size_t table_off = 0, prefix_off = 0, partial_off = 0, out_off = 0, flag_off = 0;
+  size_t table_off = 0, items_off = 0, partial_off = 0, out_off = 0, flag_off = 0;
   size_t maps_off = 0;            // TMA tensor maps: nblocks x {P, P2, R}
   size_t adj_off = 0;             // adjoint scalars: [0] dL/dnu accumulator
   bool maps_ready = false;        // maps encoded for the current Jacobi config
@@ -74,8 +74,10 @@ struct cfd_grid {
   size_t staging_off = 0;         // contiguous interior of one array (host copies)
   int host_copy = CFD_HOST_COPY_KERNEL;  // route of page-locked host copies
   int nparts = 0;
-  long long ghost_total = 0;
-  std::vector<long long> ghost_prefix;
+  // ghost-fill work items: the grid's blocks first, then each multigrid
+  // level's (gitem_first[l], gitem_count[l]; l = 0 the grid itself)
+  std::vector<GhostItem> gitems;
+  std::vector<int> gitem_first, gitem_count;
   std::vector<BlockDev> bdev;
   double* h_out = nullptr;  // pinned, 4 doubles
   int* h_flag = nullptr;    // pinned, 1 int
@@ -105,8 +107,7 @@ struct cfd_grid {
   std::vector<MgLevel> mgl;   // level l at index l - 1
   std::vector<BlockDev> mg_bdev;
   std::vector<int> mg_hn;     // 3 ints per level
-  std::vector<long long> mg_prefix;  // 2 per level: {0, ghost cells}
-  size_t mg_table_off = 0, mg_prefix_off = 0;
+  size_t mg_table_off = 0;
   int mg_levels = 0, mg_nu1 = 2, mg_nu2 = 2, mg_ncoarse = 30;  // mg_levels 0: all
   double mg_omega = 6.0 / 7.0;
   cudaGraphExec_t mg_exec = nullptr;  // one V-cycle, captured on first use
@@ -148,13 +149,95 @@ cfd_status usable(cfd_grid* g) {
 }
 
 // Device layout: [tables][arrays of block 0][arrays of block 1]...
+// The ghost-fill work items of blocks with dims n (3 ints each) and
+// neighbours nbr (6 each), faces bc, ghost width gw, appended to out: per
+// block the 26 boxes of its ghost shell with their sources (axis by axis,
+// x then y then z: across a periodic face into the neighbour, mirrored at a
+// wall), each cut into pieces of at most 16 rows.  False if a box has 2^31
+// or more rows.
+bool ghost_items(const int* n, const int* nbr, int nb, const int bc[6], int gw,
+                 std::vector<GhostItem>& out) {
+  constexpr int kRows = 16;
+  for (int b = 0; b < nb; ++b)
+    for (int dir = 0; dir < 27; ++dir) {
+      if (dir == 13) continue;
+      const int dv[3] = {dir % 3 - 1, (dir / 3) % 3 - 1, dir / 9 - 1};
+      int ext[3], d0[3], s0[3], st[3], wf[3] = {-1, -1, -1};
+      int sbk = b;
+      for (int a = 0; a < 3; ++a) {
+        const int N = n[3 * b + a];
+        if (dv[a] == 0) {
+          ext[a] = N;
+          d0[a] = 0;
+          s0[a] = 0;
+          st[a] = 1;
+          continue;
+        }
+        const int face = dv[a] < 0 ? 2 * a : 2 * a + 1;
+        ext[a] = gw;
+        d0[a] = dv[a] < 0 ? -gw : N;
+        if (bc[face] == CFD_BC_PERIODIC) {  // into the neighbour (itself for one block)
+          const int to = nbr[6 * sbk + face];
+          s0[a] = dv[a] < 0 ? n[3 * to + a] - gw : 0;
+          st[a] = 1;
+          sbk = to;
+        } else {  // mirror: ghost layer m takes the cell m - 1 from the wall
+          s0[a] = dv[a] < 0 ? gw - 1 : N - 1;
+          st[a] = -1;
+          wf[a] = face;
+        }
+      }
+      const int ia = ext[0] >= 16 ? 0 : (ext[1] >= ext[2] ? 1 : 2);
+      const int ax[3] = {ia, ia == 0 ? 1 : 0, ia == 2 ? 1 : 2};
+      const long long rows = (long long)ext[ax[1]] * ext[ax[2]];
+      if (rows >= (1LL << 31)) return false;
+      for (long long r = 0; r < rows; r += kRows) {
+        GhostItem it{};
+        it.dst = b;
+        it.src = sbk;
+        for (int k = 0; k < 3; ++k) {
+          it.ax[k] = ax[k];
+          it.e[k] = ext[ax[k]];
+          it.d0[k] = d0[ax[k]];
+          it.s0[k] = s0[ax[k]];
+          it.st[k] = st[ax[k]];
+          it.wface[k] = wf[k];
+        }
+        it.r0 = (int)r;
+        it.r1 = (int)std::min(rows, r + kRows);
+        out.push_back(it);
+      }
+    }
+  return true;
+}
+
+// All ghost items of the grid and of its multigrid levels (gitems empty if
+// a box is too large).  Depends on the faces' kinds: rebuilt with the tables.
+void build_ghost_items(cfd_grid* g) {
+  g->gitems.clear();
+  g->gitem_first.assign(g->mgl.size() + 1, 0);
+  g->gitem_count.assign(g->mgl.size() + 1, 0);
+  std::vector<int> n, nbr;
+  for (const auto& b : g->hb) {
+    n.insert(n.end(), b.n, b.n + 3);
+    nbr.insert(nbr.end(), b.nbr, b.nbr + 6);
+  }
+  bool ok = ghost_items(n.data(), nbr.data(), g->nblocks, g->bc, g->g, g->gitems);
+  g->gitem_count[0] = (int)g->gitems.size();
+  const int self[6] = {0, 0, 0, 0, 0, 0};
+  for (size_t l = 0; l < g->mgl.size() && ok; ++l) {
+    g->gitem_first[l + 1] = (int)g->gitems.size();
+    ok = ghost_items(g->mgl[l].n, self, 1, g->bc, g->g, g->gitems);
+    g->gitem_count[l + 1] = (int)g->gitems.size() - g->gitem_first[l + 1];
+  }
+  if (!ok) g->gitems.clear();
+}
+
 void plan_layout(cfd_grid* g) {
   const int align_e = kAlignBytes / g->es;
   size_t off = 0;
   g->table_off = off;
   off = round_up(off + sizeof(BlockDev) * g->nblocks, 256);
-  g->prefix_off = off;
-  off = round_up(off + sizeof(long long) * (g->nblocks + 1), 256);
   g->nparts = 8 * g->sms;  // reduction CTAs: 8 per SM of 256 threads (full occupancy)
   g->partial_off = off;
   off = round_up(off + sizeof(double) * 4 * g->nparts, 256);
@@ -180,8 +263,10 @@ void plan_layout(cfd_grid* g) {
   const size_t nl = g->mgl.size();
   g->mg_table_off = off;
   off = round_up(off + sizeof(BlockDev) * std::max<size_t>(nl, 1), 256);
-  g->mg_prefix_off = off;
-  off = round_up(off + sizeof(long long) * 2 * std::max<size_t>(nl, 1), 256);
+  // ghost items (their number depends on the dims and the ghost width only)
+  build_ghost_items(g);
+  g->items_off = off;
+  off = round_up(off + sizeof(GhostItem) * std::max<size_t>(g->gitems.size(), 1), 256);
   g->arrays_off = off;
   for (auto& b : g->hb) {
     b.py = (int)round_up((size_t)align_e + b.n[0] + g->g, align_e);
@@ -198,7 +283,6 @@ void plan_layout(cfd_grid* g) {
   g->staging_off = off;
   off += round_up(stage, 256);
   g->mg_hn.clear();
-  g->mg_prefix.clear();
   for (auto& m : g->mgl) {
     m.py = (int)round_up((size_t)align_e + m.n[0] + g->g, align_e);
     m.pz = (long long)m.py * (m.n[1] + 2 * g->g);
@@ -206,28 +290,14 @@ void plan_layout(cfd_grid* g) {
     m.first_byte = off;
     off += 3 * m.array_bytes;
     for (int a = 0; a < 3; ++a) g->mg_hn.push_back(m.n[a]);
-    const long long ex = m.n[0] + 2 * g->g, ey = m.n[1] + 2 * g->g;
-    g->mg_prefix.push_back(0);
-    g->mg_prefix.push_back(2LL * g->g * ey * ex + 2LL * g->g * m.n[2] * ex +
-                           2LL * g->g * m.n[2] * m.n[1]);
   }
   off += 256;  // tail pad: a 4-byte halo copy next to the very last row stays inside
   g->bytes = off;
-  // ghost-cell enumeration prefix (z-slabs, y-slabs, x-slabs per block)
-  g->ghost_prefix.assign(g->nblocks + 1, 0);
-  long long tot = 0;
-  for (int i = 0; i < g->nblocks; ++i) {
-    const int* n = g->hb[i].n;
-    const long long ex = n[0] + 2 * g->g, ey = n[1] + 2 * g->g;
-    g->ghost_prefix[i] = tot;
-    tot += 2LL * g->g * ey * ex + 2LL * g->g * n[2] * ex + 2LL * g->g * n[2] * n[1];
-  }
-  g->ghost_prefix[g->nblocks] = tot;
-  g->ghost_total = tot;
 }
 
 void build_tables(cfd_grid* g) {
   const int align_e = kAlignBytes / g->es;
+  build_ghost_items(g);  // same count as planned: the faces' kinds change only the sources
   g->bdev.resize(g->nblocks);
   for (int i = 0; i < g->nblocks; ++i) {
     const HostBlock& b = g->hb[i];
@@ -272,14 +342,13 @@ cfd_status upload_tables(cfd_grid* g) {
   build_tables(g);
   CK(g, cudaMemcpyAsync(g->base + g->table_off, g->bdev.data(), sizeof(BlockDev) * g->nblocks,
                         cudaMemcpyHostToDevice, g->own));
-  CK(g, cudaMemcpyAsync(g->base + g->prefix_off, g->ghost_prefix.data(),
-                        sizeof(long long) * (g->nblocks + 1), cudaMemcpyHostToDevice, g->own));
+  CK(g, cudaMemcpyAsync(g->base + g->items_off, g->gitems.data(),
+                        sizeof(GhostItem) * g->gitems.size(), cudaMemcpyHostToDevice, g->own));
   CK(g, cudaMemsetAsync(g->base + g->flag_off, 0, 256, g->own));
   if (!g->mgl.empty()) {
     CK(g, cudaMemcpyAsync(g->base + g->mg_table_off, g->mg_bdev.data(),
                           sizeof(BlockDev) * g->mg_bdev.size(), cudaMemcpyHostToDevice, g->own));
-    CK(g, cudaMemcpyAsync(g->base + g->mg_prefix_off, g->mg_prefix.data(),
-                          sizeof(long long) * g->mg_prefix.size(), cudaMemcpyHostToDevice, g->own));
+
   }
   CK(g, cudaStreamSynchronize(g->own));
   return refresh_maps(g);
@@ -354,9 +423,8 @@ cfd_status common_init(cfd_grid* g, int ghost, const double h[3], int storage, v
     for (int d = 0; d < 3; ++d) g->hn[3 * b + d] = g->hb[b].n[d];
   g->jcfg = JacobiCfg{0, 4, 8, 32, 4};
   plan_layout(g);
-  for (int b = 0; b < g->nblocks; ++b)  // the ghost kernel indexes a block's ghost cells in 32 bits
-    if (g->ghost_prefix[b + 1] - g->ghost_prefix[b] >= (1LL << 31))
-      return fail(CFD_EINVAL, "block %d has too many ghost cells (>= 2^31)", b);
+  if (g->gitems.empty())  // the ghost kernel counts a box's rows in 32 bits
+    return fail(CFD_EINVAL, "a block's ghost box has 2^31 or more rows");
   if (!g->mgl.empty() && (e = prepare_mg_bottom()) != cudaSuccess)
     return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
   return CFD_OK;
@@ -424,8 +492,8 @@ cfd_status enq_ghost(cfd_grid* g, unsigned mask) {
   for (int a = 0; a < kNumArrays; ++a)
     if (mask & (1u << a)) arrs[n++] = a;
   const Launch L = make_launch(g);
-  CK(g, launch_ghost(L, arrs, n, reinterpret_cast<const long long*>(g->base + g->prefix_off),
-                     g->ghost_total));
+  CK(g, launch_ghost(L, arrs, n, reinterpret_cast<const GhostItem*>(g->base + g->items_off),
+                     g->gitem_count[0]));
   g->launches += n > 0 ? 1 : 0;
   return CFD_OK;
 }
@@ -442,21 +510,27 @@ cfd_status enq_stage(cfd_grid* g, double a, int xs, double b, int ys, double c, 
   });
 }
 
-// The two-sweep kernel's periodic form: every face periodic and two ghost
-// layers (the first sweep is also taken on the first ghost layer).
+// The two-sweep kernel's periodic form: every face periodic (or, in a block
+// set, copied from the neighbouring block) and two ghost layers (the first
+// sweep is also taken on the first ghost layer, whose cells the ghost launch
+// before each two-sweep launch has copied from where they live).
 bool ws2_periodic(const cfd_grid* g) {
   for (int f = 0; f < 6; ++f)
     if (g->bc[f] != CFD_BC_PERIODIC) return false;
   return g->g >= 2;
 }
 
-// Fused two-sweep launches apply (single block, tiles dividing x and y).
+// Fused two-sweep launches apply: kind 9 on a single block whose six faces
+// are walls, or in the periodic form (single blocks and block sets); kind 5
+// on single blocks with tiles dividing x and y.
 bool fused_ok(const cfd_grid* g) {
   if (g->jcfg.kind == 9) {
-    if (g->nblocks != 1 || !g->maps_ready) return false;
+    if (!g->maps_ready) return false;
+    if (ws2_periodic(g)) return true;
+    if (g->nblocks != 1) return false;
     bool walls = true;
     for (int f = 0; f < 6; ++f) walls &= g->bdev[0].bc[f] == BC_WALL;
-    return walls || ws2_periodic(g);
+    return walls;
   }
   return g->jcfg.kind == 5 && g->nblocks == 1 && g->hb[0].n[0] % 128 == 0 &&
          g->hb[0].n[1] % g->jcfg.ty == 0 && g->hb[0].n[1] >= 2 && g->hb[0].n[2] >= 2;
@@ -656,8 +730,8 @@ cfd_status enq_level_sweeps(cfd_grid* g, int l, int n, int start, int* end) {
 // corners).
 cfd_status enq_level_ghost(cfd_grid* g, int l, int arr) {
   if (l == 0) return enq_ghost(g, 1u << arr);
-  const long long* prefix = reinterpret_cast<const long long*>(g->base + g->mg_prefix_off) + 2 * (l - 1);
-  CK(g, launch_ghost(level_launch(g, l), &arr, 1, prefix, g->mg_prefix[2 * (l - 1) + 1]));
+  const GhostItem* items = reinterpret_cast<const GhostItem*>(g->base + g->items_off) + g->gitem_first[l];
+  CK(g, launch_ghost(level_launch(g, l), &arr, 1, items, g->gitem_count[l]));
   g->launches += 1;
   return CFD_OK;
 }

@@ -7,6 +7,7 @@
 // addressed as base + org[array] + k*pz + j*py + i with i,j,k relative to the
 // interior origin, so ghost cells have negative or >= n indices.
 #include <cuda_bf16.h>
+#include <algorithm>
 #include <cuda_fp16.h>
 
 #include "cfd_internal.h"
@@ -27,111 +28,68 @@ namespace {
 
 struct GhostArrays { int arr[kNumArrays]; int n; };
 
+// Ghost fill of the arrays in ga.  A block's ghost shell is 26 disjoint
+// boxes, one per direction (dx, dy, dz) in {-1, 0, 1}^3 other than 0; each
+// is the image of one box of cells, found on the host axis by axis (x, then
+// y, then z): a periodic or block-to-block face moves the source into the
+// neighbouring block, a wall mirrors it within the block and composes the
+// wall rule v -> A + S v (zero normal velocity, tangential 2 U_wall - v,
+// pressure v).  The result is that of ghost passes x, y, z over the full
+// extent, each reading the previous pass's ghosts, with nothing but copies
+// between blocks.  The host cuts the boxes into items of at most 16 rows
+// (GhostItem); CTA i copies item i: its eight warps take rows, the lanes
+// run along the box's inner axis (x unless the box is thinner than 16
+// there), one array at a time, eight cells per lane loaded before any is
+// stored (the loads do not wait behind stores through the same base).
 template <typename T>
-__global__ void __launch_bounds__(256) k_ghost(Launch L, GhostArrays ga, const long long* prefix,
-                                               long long total) {
-  // the block table and the enumeration prefix, once per CTA, in shared
-  // memory: every ghost cell resolves its source through several of them
-  extern __shared__ __align__(16) unsigned char gsm[];
-  BlockDev* sb = reinterpret_cast<BlockDev*>(gsm);
-  long long* spre = reinterpret_cast<long long*>(gsm + (size_t)L.nblocks * sizeof(BlockDev));
-  {
-    const int words = L.nblocks * (int)(sizeof(BlockDev) / 4);
-    const int* src = reinterpret_cast<const int*>(L.blocks);
-    for (int w = threadIdx.x; w < words; w += blockDim.x) reinterpret_cast<int*>(sb)[w] = src[w];
-    for (int b = threadIdx.x; b <= L.nblocks; b += blockDim.x) spre[b] = prefix[b];
-  }
-  __syncthreads();
-  const int g = L.ghost;
-  // one thread per ghost cell of the block set; the cell's position and its
-  // source (block and cell, walls met on the way) are found once and serve
-  // every array of the launch.  A block's ghost cells number below 2^31
-  // (checked at grid creation), so the per-block index arithmetic is 32-bit.
-  for (long long t = (long long)blockIdx.x * blockDim.x + threadIdx.x; t < total;
-       t += (long long)gridDim.x * blockDim.x) {
-    // block of this ghost cell (binary search over the prefix sums)
-    int lo = 0, hi = L.nblocks - 1;
-    while (lo < hi) {
-      const int mid = (lo + hi + 1) >> 1;
-      if (spre[mid] <= t) lo = mid; else hi = mid - 1;
-    }
-    const int b = lo;
-    const BlockDev& B = sb[b];
-    const int nx = B.n[0], ny = B.n[1], nz = B.n[2];
-    const unsigned ex = nx + 2 * g, ey = ny + 2 * g;
-    unsigned l = (unsigned)(t - spre[b]);
-    int q[3];
-    const unsigned zc = 2u * g * ey * ex, yc = 2u * g * nz * ex;
-    if (l < zc) {
-      const int s2 = (int)(l / (ey * ex));
-      const unsigned rem = l % (ey * ex);
-      q[2] = s2 < g ? s2 - g : nz + s2 - g;
-      q[1] = (int)(rem / ex) - g;
-      q[0] = (int)(rem % ex) - g;
-    } else if ((l -= zc) < yc) {
-      const int s2 = (int)(l / (nz * ex));
-      const unsigned rem = l % (nz * ex);
-      q[1] = s2 < g ? s2 - g : ny + s2 - g;
-      q[2] = (int)(rem / ex);
-      q[0] = (int)(rem % ex) - g;
-    } else {
-      l -= yc;
-      const int s2 = (int)(l / ((unsigned)nz * ny));
-      const unsigned rem = l % ((unsigned)nz * ny);
-      q[0] = s2 < g ? s2 - g : nx + s2 - g;
-      q[2] = (int)(rem / ny);
-      q[1] = (int)(rem % ny);
-    }
-    const int dst[3] = {q[0], q[1], q[2]};
-    // source cell: axis by axis, across a periodic/neighbour face to the
-    // neighbouring block, or mirrored at a wall (recorded for the rules)
-    int sbk = b;
-    int wface[3] = {-1, -1, -1}, wblk[3] = {0, 0, 0};
-#pragma unroll
-    for (int d = 0; d < 3; ++d) {
-      const BlockDev& C = sb[sbk];
-      const int N = C.n[d];
-      int face;
-      if (q[d] < 0) face = 2 * d; else if (q[d] >= N) face = 2 * d + 1; else continue;
-      const bool low = (face == 2 * d);
-      if (C.bc[face] == BC_PERIODIC) {
-        const int nb = C.nbr[face];
-        q[d] = low ? q[d] + sb[nb].n[d] : q[d] - N;
-        sbk = nb;
-      } else {
-        q[d] = low ? -1 - q[d] : 2 * N - 1 - q[d];
-        wface[d] = face;
-        wblk[d] = sbk;
-      }
-    }
-    const BlockDev& Sd = sb[sbk];
-    const long long so = (long long)q[2] * Sd.pz + (long long)q[1] * Sd.py + q[0];
-    const long long dof = (long long)dst[2] * B.pz + (long long)dst[1] * B.py + dst[0];
-    // every array's source value first, then the stores: a load after a
-    // store through the same base pointer would wait behind it
-    float src[kNumArrays];
-#pragma unroll
-    for (int ai = 0; ai < kNumArrays; ++ai)
-      if (ai < ga.n) src[ai] = ldf<T>(reinterpret_cast<const T*>(L.base) + Sd.org[ga.arr[ai]] + so);
-#pragma unroll
-    for (int ai = 0; ai < kNumArrays; ++ai) {
-      if (ai >= ga.n) break;
+__global__ void __launch_bounds__(256) k_ghost(Launch L, const GhostItem* items,
+                                               const __grid_constant__ GhostArrays ga) {
+  const GhostItem it = items[blockIdx.x];
+  const BlockDev& B = L.blocks[it.dst];
+  const BlockDev& Sd = L.blocks[it.src];
+  auto pick3 = [](int i, long long v0, long long v1, long long v2) {
+    return i == 0 ? v0 : (i == 1 ? v1 : v2);
+  };
+  const long long dsi = pick3(it.ax[0], 1, B.py, B.pz), dsj = pick3(it.ax[1], 1, B.py, B.pz);
+  const long long dsk = pick3(it.ax[2], 1, B.py, B.pz);
+  const long long ssi = pick3(it.ax[0], 1, Sd.py, Sd.pz), ssj = pick3(it.ax[1], 1, Sd.py, Sd.pz);
+  const long long ssk = pick3(it.ax[2], 1, Sd.py, Sd.pz);
+  const int ei = it.e[0], ej = it.e[1];
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+  const long long dinc = dsi, sinc = (long long)it.st[0] * ssi;
+  constexpr int U = 8;  // cells per lane loaded before any is stored
+  for (int r = it.r0 + warp; r < it.r1; r += 8) {
+    const int rj = r % ej, rk = r / ej;
+    const long long dbase = (long long)(it.d0[1] + rj) * dsj + (long long)(it.d0[2] + rk) * dsk +
+                            (long long)it.d0[0] * dsi;
+    const long long sbase = (long long)(it.s0[1] + it.st[1] * rj) * ssj +
+                            (long long)(it.s0[2] + it.st[2] * rk) * ssk + (long long)it.s0[0] * ssi;
+    for (int ai = 0; ai < ga.n; ++ai) {
       const int arr = ga.arr[ai];
+      // the array's wall rule v -> A + S v, composed over the axes in order
       const int kind = array_kind(arr);
-      // the wall rules compose as affine maps v -> A + S v, axis by axis
       float A = 0.f, S = 1.f;
 #pragma unroll
       for (int d = 0; d < 3; ++d) {
-        if (wface[d] < 0) continue;
+        if (it.wface[d] < 0) continue;
         float a, s1;
         if (kind == 3) { a = 0.f; s1 = 1.f; }
         else if (kind == d) { a = 0.f; s1 = 0.f; }
-        else { a = 2.f * sb[wblk[d]].wall[wface[d]][kind]; s1 = -1.f; }
+        else { a = 2.f * B.wall[it.wface[d]][kind]; s1 = -1.f; }
         A = a + s1 * A;
         S = s1 * S;
       }
-      const float v = S != 0.f ? A + S * src[ai] : A;
-      reinterpret_cast<T*>(L.base)[B.org[arr] + dof] = cvt<T>(v);
+      const T* sp = reinterpret_cast<const T*>(L.base) + Sd.org[arr] + sbase;
+      T* dp = reinterpret_cast<T*>(L.base) + B.org[arr] + dbase;
+      for (int i0 = lane; i0 < ei; i0 += 32 * U) {
+        float v[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (i0 + 32 * u < ei) v[u] = ldf<T>(sp + (i0 + 32 * u) * sinc);
+#pragma unroll
+        for (int u = 0; u < U; ++u)
+          if (i0 + 32 * u < ei) dp[(i0 + 32 * u) * dinc] = cvt<T>(S != 0.f ? A + S * v[u] : A);
+      }
     }
   }
 }
@@ -1712,33 +1670,13 @@ long long count_tiles(const Launch& L, int tx, int ty, int tz) {
     default: { using T = __half; __VA_ARGS__; } break;     \
   }
 
-template <typename T>
-static cudaError_t run_ghost(const Launch& L, const GhostArrays& ga, const long long* d_prefix,
-                             long long total) {
-  const size_t smem = (size_t)L.nblocks * sizeof(BlockDev) + sizeof(long long) * (L.nblocks + 1);
-  static size_t set_for = 48 * 1024;
-  if (smem > set_for) {
-    cudaError_t e = cudaFuncSetAttribute(k_ghost<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                         (int)smem);
-    if (e != cudaSuccess) return e;
-    set_for = smem;
-  }
-  long long grid = (total + 255) / 256;
-  const long long cap = (long long)L.sms * 8;
-  if (grid > cap) grid = cap;
-  k_ghost<T><<<(unsigned)grid, 256, smem, L.stream>>>(L, ga, d_prefix, total);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr, const long long* d_prefix,
-                         long long total) {
-  if (total == 0 || narr == 0) return cudaSuccess;
+cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr, const GhostItem* items,
+                         int nitems) {
+  if (nitems == 0 || narr == 0) return cudaSuccess;
   GhostArrays ga{};
   ga.n = narr;
   for (int e = 0; e < narr; ++e) ga.arr[e] = arrays[e];
-  cudaError_t e = cudaSuccess;
-  CFD_DISPATCH_T(L.dtype, e = run_ghost<T>(L, ga, d_prefix, total));
-  if (e != cudaSuccess) return e;
+  CFD_DISPATCH_T(L.dtype, k_ghost<T><<<(unsigned)nitems, 256, 0, L.stream>>>(L, items, ga));
   return cudaGetLastError();
 }
 

@@ -326,6 +326,40 @@ def test_blockset_step_equals_global_oracle(order, g):
         assert rel_err(got, ref, remove_mean=(k == 3)) < 1e-5, k
 
 
+@pytest.mark.parametrize("order,g,jacobi", [(2, 1, (0, 4, 4, 32, 4)), (4, 2, (0, 4, 4, 32, 4)),
+                                             (4, 2, (9, 4, 16, 16, 6)), (4, 2, (9, 4, 8, 32, 6))])
+def test_blockset_workload_tiling_equals_global_oracle(order, g, jacobi):
+    """The block-set workload's own tiling: 64 blocks with per-axis widths
+    U{16..96} (seed 2), curl-noise start (seed 3), two RK2 steps with 20
+    Jacobi sweeps per solve, against the oracle on the global grid.  With
+    two ghost layers the two-sweep kernel runs in its periodic form over
+    all blocks at once, the ghost launch between its launches copying both
+    layers from the neighbouring blocks."""
+    from oracle import Oracle
+    from paper_1201_2118_gb300 import Grid, U, V, W, P
+    gd, blocks = workloads.block_tiling(seed=2)
+    h = workloads.workload_h("blocks64")
+    fl = rounded(workloads.random_div_free(gd, h, seed=3))
+    o = Oracle(gd, ghost=g, h=h, nu=0.01, order=order)
+    u, p = o.state(fl)
+    grid = Grid(ghost=g, h=h, blocks=[(b["dims"], b["origin"]) for b in blocks], global_dims=gd)
+    grid.fill(float("nan"))
+    grid.set_params(0.01, 20, 1.0, order)
+    grid.set_kernel_config(jacobi=jacobi)
+    grid.upload_blocks(workloads.split_blocks(fl, blocks))
+    dt = workloads.cfl_dt(h)
+    grid.step(dt, 2)
+    o.run(u, p, dt, 20, 2)
+    grid.check()
+    for k, a in enumerate((U, V, W, P)):
+        got = np.full(gd[::-1], np.nan)
+        for b, blk in enumerate(blocks):
+            (nx, ny, nz), (ox, oy, oz) = blk["dims"], blk["origin"]
+            got[oz:oz + nz, oy:oy + ny, ox:ox + nx] = grid.download(a, block=b)
+        ref = o.interior(u[k] if k < 3 else p)
+        assert rel_err(got, ref, remove_mean=(k == 3)) < 1e-5, k
+
+
 def test_nan_watchdog_and_errors():
     from paper_1201_2118_gb300 import CfdError, Grid, U, SET_U
     grid = Grid((16, 16, 16), ghost=1, h=(0.1, 0.1, 0.1))
