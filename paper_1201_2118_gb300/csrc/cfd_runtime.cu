@@ -10,12 +10,24 @@
 #include <string>
 #include <vector>
 
+#include <nvtx3/nvToolsExt.h>
+
 #include "cfd_internal.h"
 #include "gb300cfd.h"
 
 using namespace cfd;
 
 namespace {
+
+// An NVTX range around one entry point (shows the library's calls on a
+// profiler's timeline; a push and a pop are two inline checks when no tool
+// is attached).
+struct CallRange {
+  explicit CallRange(const char* name) { nvtxRangePushA(name); }
+  ~CallRange() { nvtxRangePop(); }
+  CallRange(const CallRange&) = delete;
+  CallRange& operator=(const CallRange&) = delete;
+};
 
 thread_local std::string t_err = "no error";
 
@@ -1182,6 +1194,7 @@ cfd_status cfd_set_advection(cfd_grid* g, int form) {
 }
 
 cfd_status cfd_ghost_fill(cfd_grid* g, unsigned mask) {
+  const CallRange range("cfd_ghost_fill");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (mask >> kNumArrays) return fail(CFD_EINVAL, "mask has bits beyond the array ids");
@@ -1191,6 +1204,7 @@ cfd_status cfd_ghost_fill(cfd_grid* g, unsigned mask) {
 }
 
 cfd_status cfd_stage(cfd_grid* g, double a, int x_set, double b, int y_set, double c, int out_set) {
+  const CallRange range("cfd_stage");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (y_set < 0 || y_set > 2 || out_set < 0 || out_set > 2 || (a != 0.0 && (x_set < 0 || x_set > 2)))
@@ -1203,6 +1217,7 @@ cfd_status cfd_stage(cfd_grid* g, double a, int x_set, double b, int y_set, doub
 }
 
 cfd_status cfd_rhs_eval(cfd_grid* g, void* const out_dev[3]) {
+  const CallRange range("cfd_rhs_eval");
   if (out_dev && (!out_dev[0] || !out_dev[1] || !out_dev[2]))
     return fail(CFD_EINVAL, "out_dev must be NULL or hold three device pointers");
   cfd_status s = cfd_stage(g, 0.0, 0, 0.0, CFD_SET_U, 1.0, CFD_SET_W);
@@ -1224,6 +1239,7 @@ cfd_status cfd_rhs_eval(cfd_grid* g, void* const out_dev[3]) {
 }
 
 cfd_status cfd_pressure_solve(cfd_grid* g, double c_dt, int iters, double* residual) {
+  const CallRange range("cfd_pressure_solve");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (!(c_dt > 0.0) || iters < 0) return fail(CFD_EINVAL, "need c_dt > 0 and iters >= 0");
@@ -1240,6 +1256,7 @@ cfd_status cfd_pressure_solve(cfd_grid* g, double c_dt, int iters, double* resid
 
 cfd_status cfd_pressure_solve_converged(cfd_grid* g, double c_dt, double rtol, int max_iters,
                                         int check_every, int* iters_done, double* residual) {
+  const CallRange range("cfd_pressure_solve_converged");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (!(c_dt > 0.0) || !(rtol >= 0.0) || max_iters < 0 || check_every < 1)
@@ -1305,6 +1322,7 @@ cfd_status cfd_set_pressure_solver(cfd_grid* g, int solver, int cycles) {
 }
 
 cfd_status cfd_mg_vcycles(cfd_grid* g, int cycles) {
+  const CallRange range("cfd_mg_vcycles");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if ((s = mg_supported(g)) != CFD_OK) return s;
@@ -1317,6 +1335,7 @@ cfd_status cfd_mg_vcycles(cfd_grid* g, int cycles) {
 
 cfd_status cfd_pressure_solve_mg(cfd_grid* g, double c_dt, double rtol, int max_cycles,
                                  int* cycles_done, double* residual) {
+  const CallRange range("cfd_pressure_solve_mg");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if ((s = mg_supported(g)) != CFD_OK) return s;
@@ -1344,6 +1363,7 @@ cfd_status cfd_pressure_solve_mg(cfd_grid* g, double c_dt, double rtol, int max_
 }
 
 cfd_status cfd_jacobi(cfd_grid* g, int iters) {
+  const CallRange range("cfd_jacobi");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (iters < 0) return fail(CFD_EINVAL, "iters must be >= 0");
@@ -1396,6 +1416,7 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
 }
 
 cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
+  const CallRange range("cfd_autotune");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   const std::string key = tune_key(g);
@@ -1536,6 +1557,7 @@ cfd_status cfd_stats(const cfd_grid* g, long long* kernel_launches) {
 }
 
 cfd_status cfd_project(cfd_grid* g, double c_dt, int out_set) {
+  const CallRange range("cfd_project");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (out_set < 0 || out_set > 2 || out_set == CFD_SET_W) return fail(CFD_EINVAL, "output set must be U or U1");
@@ -1545,6 +1567,7 @@ cfd_status cfd_project(cfd_grid* g, double c_dt, int out_set) {
 }
 
 cfd_status cfd_rk_step(cfd_grid* g, int stage, double dt) {
+  const CallRange range("cfd_rk_step");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (stage != 1 && stage != 2) return fail(CFD_EINVAL, "stage must be 1 or 2");
@@ -1559,6 +1582,7 @@ cfd_status cfd_rk_step(cfd_grid* g, int stage, double dt) {
 }
 
 cfd_status cfd_step(cfd_grid* g, double dt, int n) {
+  const CallRange range("cfd_step");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (!(dt > 0.0) || n < 0) return fail(CFD_EINVAL, "need dt > 0 and n >= 0");
@@ -1574,6 +1598,7 @@ cfd_status cfd_step(cfd_grid* g, double dt, int n) {
 
 cfd_status cfd_reduce(cfd_grid* g, int set, double* kinetic_energy, double* max_abs_u,
                       double* max_abs_div) {
+  const CallRange range("cfd_reduce");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (set < 0 || set > 2) return fail(CFD_EINVAL, "set must be 0..2");
@@ -1589,6 +1614,7 @@ cfd_status cfd_reduce(cfd_grid* g, int set, double* kinetic_energy, double* max_
 }
 
 cfd_status cfd_residual(cfd_grid* g, double* residual) {
+  const CallRange range("cfd_residual");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (!residual) return fail(CFD_EINVAL, "null argument");
@@ -1603,6 +1629,7 @@ cfd_status cfd_residual(cfd_grid* g, double* residual) {
 
 cfd_status cfd_adjoint_step(cfd_grid* g, double dt, const void* const un[3],
                             const void* const u1[3], double* dnu_accum_dev) {
+  const CallRange range("cfd_adjoint_step");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if ((s = adjoint_supported(g)) != CFD_OK) return s;
@@ -1740,6 +1767,7 @@ extern "C" {
 
 cfd_status cfd_rollout_forward(cfd_grid* g, double dt, int nsteps, int seg, void* store,
                                size_t bytes) {
+  const CallRange range("cfd_rollout_forward");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if ((s = adjoint_supported(g)) != CFD_OK) return s;
@@ -1765,6 +1793,7 @@ cfd_status cfd_rollout_forward(cfd_grid* g, double dt, int nsteps, int seg, void
 
 cfd_status cfd_rollout_backward(cfd_grid* g, double dt, int nsteps, int seg, void* store,
                                 size_t bytes, double* dnu) {
+  const CallRange range("cfd_rollout_backward");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if ((s = adjoint_supported(g)) != CFD_OK) return s;
@@ -1811,6 +1840,7 @@ cfd_status cfd_set_state(cfd_grid* g, double t, long long step) {
 }
 
 cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int to_device) {
+  const CallRange range("cfd_copy_interior");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (!host) return fail(CFD_EINVAL, "null host pointer");
@@ -1860,6 +1890,7 @@ cfd_status cfd_set_host_copy(cfd_grid* g, int mode) {
 }
 
 cfd_status cfd_selftest_wait_timeout(cfd_grid* g, int form) {
+  const CallRange range("cfd_selftest_wait_timeout");
   cfd_status s = usable(g);
   if (s != CFD_OK) return s;
   if (form != 0 && form != 1) return fail(CFD_EINVAL, "form must be 0 or 1");
@@ -1870,6 +1901,7 @@ cfd_status cfd_selftest_wait_timeout(cfd_grid* g, int form) {
 }
 
 cfd_status cfd_check(cfd_grid* g) {
+  const CallRange range("cfd_check");
   if (!g) return fail(CFD_EINVAL, "null grid");
   if (g->sticky) return fail(CFD_ECUDA, "grid is in a failed state after an earlier CUDA error");
   if (!g->base) return CFD_OK;
