@@ -10,8 +10,9 @@ in the CUDA library, replayed from one CUDA graph per step.
 Prints one JSON line: GLUP/s (interior cells x steps / s / 1e9), the Jacobi
 sweep against the measured HBM roofline, an end-to-end figure through the C
 ABI with page-locked host buffers (u, v, w, p copied in and out every step;
-three independent problems in flight, and one problem alone as
-e2e.serial), and the FP64 oracle timed on the host cores.
+three independent problems in flight, their copies by the pack kernel on
+one CTA per eight SMs, and one problem alone as e2e.serial), and the FP64
+oracle timed on the host cores.
 N > 1 (torchrun): N independent replicas, one per GPU ("replicas only": the
 single-GPU path has no data exchange between GPUs); value = cells of all
 ranks / slowest rank's time.
@@ -65,6 +66,14 @@ def parse():
     ap.add_argument("--no-secondary", action="store_true",
                     help="skip the reduced-precision, block-set and adjoint comparisons")
     ap.add_argument("--precision-steps", type=int, default=20)
+    ap.add_argument("--e2e-copy", default="narrow", choices=["narrow", "engine", "kernel"],
+                    help="route of the pipelined end-to-end leg's host copies: the pack kernel "
+                         "on one CTA per eight SMs over the host link (default), copy engines "
+                         "through the staging region, or the pack kernel on the whole GPU")
+    ap.add_argument("--e2e-host-mem", default="pinned", choices=["pinned", "hugepages"],
+                    help="host buffers of the end-to-end leg: torch's page-locked allocator, or "
+                         "anonymous memory advised for transparent huge pages and registered "
+                         "with CUDA")
     ap.add_argument("--cuda-connections", type=int, default=0,
                     help="CUDA_DEVICE_MAX_CONNECTIONS for this process (0: leave as is); "
                          "hardware work queues shared by the streams")
@@ -297,6 +306,50 @@ def aggregate(ms_local: float, cells: int, dist=None, device="cpu"):
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
     return ms, world * cells / (ms * 1e-3) / 1e9
+
+
+class HostBuffers:
+    """Page-locked host tensors for the end-to-end leg: torch's pinned
+    allocator, or (hugepages) anonymous mappings advised for transparent huge
+    pages, touched, then registered with cudaHostRegister, so that the host
+    side of the link translates 2 MB pages instead of 4 KB ones."""
+
+    def __init__(self, torch, hugepages):
+        self.torch, self.huge, self.keep = torch, hugepages, []
+
+    def empty(self, shape, dtype):
+        torch = self.torch
+        if not self.huge:
+            return torch.empty(shape, dtype=dtype, pin_memory=True)
+        import mmap
+        nbytes = math.prod(shape) * torch.empty((), dtype=dtype).element_size()
+        size = (nbytes + (2 << 20) - 1) // (2 << 20) * (2 << 20)
+        m = mmap.mmap(-1, size, flags=mmap.MAP_PRIVATE | mmap.MAP_ANONYMOUS)
+        m.madvise(mmap.MADV_HUGEPAGE)
+        raw = torch.frombuffer(m, dtype=torch.uint8)
+        raw[::4096].zero_()  # fault the pages in after the advice
+        err = torch.cuda.cudart().cudaHostRegister(raw.data_ptr(), size, 0)
+        if int(err) != 0:
+            raise RuntimeError("cudaHostRegister failed: %s" % err)
+        self.keep.append((m, raw))
+        return raw[:nbytes].view(dtype).view(shape)
+
+    def release(self):
+        for m, raw in self.keep:
+            self.torch.cuda.cudart().cudaHostUnregister(raw.data_ptr())
+        self.keep.clear()
+
+
+def anon_huge_kb():
+    """AnonHugePages of /proc/meminfo in kB (None where unreadable)."""
+    try:
+        with open("/proc/meminfo") as f:
+            for line in f:
+                if line.startswith("AnonHugePages:"):
+                    return int(line.split()[1])
+    except OSError:
+        pass
+    return None
 
 
 def pipeline_schedule(origin, marks):
@@ -746,10 +799,12 @@ def run_gpu(a):
     e2e = None
     if not a.no_e2e:
         tdt = {"f32": torch.float32, "bf16": torch.bfloat16, "f16": torch.float16}[a.dtype]
-        host_in = [torch.empty((n, n, n), dtype=tdt, pin_memory=True) for _ in range(4)]
+        hb = HostBuffers(torch, a.e2e_host_mem == "hugepages")
+        huge0 = anon_huge_kb()
+        host_in = [hb.empty((n, n, n), tdt) for _ in range(4)]
         nf = a.e2e_in_flight
-        host_out = [[torch.empty((n, n, n), dtype=tdt, pin_memory=True) for _ in range(4)]
-                    for _ in range(nf)]
+        host_out = [[hb.empty((n, n, n), tdt) for _ in range(4)] for _ in range(nf)]
+        huge1 = anon_huge_kb()
         for k, arr in enumerate((U, V, W, P)):
             g.copy_interior(arr, host_out[0][k].data_ptr(), to_device=False)
         torch.cuda.synchronize()
@@ -811,7 +866,7 @@ def run_gpu(a):
             gx.set_kernel_config(jacobi=jcfg[0], stencil=jcfg[1])
             grids.append(gx)
         for grid in grids:
-            grid.set_host_copy("engine")
+            grid.set_host_copy(a.e2e_copy)
         for grid, out in zip(grids, host_out):  # warm-up: captures the step graphs
             host_step(grid, out)
         torch.cuda.synchronize()
@@ -840,6 +895,7 @@ def run_gpu(a):
         g.set_host_copy("kernel")
         del grids, gx
         torch.cuda.empty_cache()
+        hb.release()
         ems, e2e_value = aggregate(x0.elapsed_time(x1) / (nf * k_e2e), cells, dist, "cuda")
         schedule = pipeline_schedule(x0, marks)
         es = host_in[0].element_size()
@@ -847,10 +903,16 @@ def run_gpu(a):
                "h2d_bytes_per_step": 4 * cells * es, "d2h_bytes_per_step": 4 * cells * es,
                "ms_per_step": ems, "steps": nf * k_e2e, "in_flight": nf,
                "outputs_equal": same, "schedule": schedule,
-               "api": "per step: cfd_copy_interior (pinned host -> device, u,v,w,p; copy engine) "
+               "host_mem": {"kind": a.e2e_host_mem,
+                            "anon_huge_pages_gb": None if huge0 is None or huge1 is None
+                            else (huge1 - huge0) / 2 ** 20},
+               "api": "per step: cfd_copy_interior (pinned host -> device, u,v,w,p; %s) "
                       "+ cfd_step + cfd_copy_interior (device -> pinned host, u,v,w,p); %d "
                       "independent %d^3 problems, one stream each, their input copies and steps "
-                      "chained by events in turn" % (nf, n),
+                      "chained by events in turn" % (
+                          {"engine": "copy engine", "kernel": "pack kernel over the host link",
+                           "narrow": "pack kernel on one CTA per eight SMs over the host link"}
+                          [a.e2e_copy], nf, n),
                "serial": {"value": serial_value, "ms_per_step": serial_ms, "steps": k_e2e,
                           "in_flight": 1,
                           "api": "the same calls on one problem, pack kernel over the host "

@@ -332,9 +332,18 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
  * a copy engine moves it to or from the staging region and the pack kernel
  * runs device to device, so a transfer on this grid's stream overlaps
  * kernels of another stream (another grid's step) with the SMs left to
- * them.  Memory that is not page-locked always takes the staging route.
- * CFD_EINVAL for another mode. */
-typedef enum { CFD_HOST_COPY_KERNEL = 0, CFD_HOST_COPY_ENGINE = 1 } cfd_host_copy;
+ * them.  CFD_HOST_COPY_NARROW: the pack kernel reads or writes the
+ * page-locked memory itself, but on one CTA per eight SMs with sixteen
+ * 16-byte transfers in flight per thread, so the link stays busy while
+ * another grid's step keeps the rest of the GPU (needs the block's nx a
+ * multiple of 16 bytes' worth of elements and a 16-byte aligned buffer,
+ * else it takes the CFD_HOST_COPY_KERNEL form).  Memory that is not
+ * page-locked always takes the staging route.  CFD_EINVAL for another mode. */
+typedef enum {
+  CFD_HOST_COPY_KERNEL = 0,
+  CFD_HOST_COPY_ENGINE = 1,
+  CFD_HOST_COPY_NARROW = 2
+} cfd_host_copy;
 cfd_status cfd_set_host_copy(cfd_grid* g, int mode);
 
 /* Kernel variants.  jacobi = {kind, vx, ty, zc, stages}: kind 0 is the

@@ -69,8 +69,10 @@ struct Launch {
 //           no CTA barrier per plane)
 //   kind 5: two fused sweeps per launch (temporal blocking, single block,
 //           nx % 128 == 0, ny % ty == 0); odd counts end with one kind-0 sweep
-//   kind 9: two sweeps per launch, warp-specialised TMA (single block with
-//           walls on all six faces); odd counts end with one kind-0 sweep
+//   kind 9: two sweeps per launch, warp-specialised TMA, tiles claimed from a
+//           counter (single block with walls on all six faces, or the
+//           periodic form with two ghost layers, block sets included); odd
+//           counts end with one kind-0 sweep
 struct JacobiCfg { int kind, vx, ty, zc, stages; };
 // Point kernels: rows per CTA (32 x ty threads) and z chunk; the RHS + stage
 // kernel either reads neighbours through L1 (tile_tz = 0) or from a
@@ -93,6 +95,12 @@ cudaError_t launch_jacobi_tma(const Launch& L, const JacobiCfg& c, const void* m
 // (nz, ny, nx) buffer in device memory: to_compact 0 scatters the buffer
 // into the array, 1 gathers the array into the buffer.
 cudaError_t launch_pack(const Launch& L, int arr, void* compact, int to_compact);
+// The same copy on a few CTAs (one per eight SMs) with sixteen 16-byte
+// transfers in flight per thread: for page-locked host buffers, so that a
+// transfer keeps the host link busy without taking the SMs from other work.
+// Needs nx a multiple of the 16-byte vector and a 16-byte aligned buffer
+// (returns cudaErrorInvalidValue otherwise; the caller falls back).
+cudaError_t launch_pack_narrow(const Launch& L, int arr, void* compact, int to_compact);
 // One CTA waits (bounded) on an mbarrier that nothing completes; sets the
 // device error flag when the wait runs out (failure-detection self-test).
 cudaError_t launch_wait_probe(const Launch& L, int form);

@@ -1859,13 +1859,16 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
   cudaPointerAttributes pa{};
   void* direct = nullptr;
   if (cudaPointerGetAttributes(&pa, host) == cudaSuccess) {
-    if (pa.type == cudaMemoryTypeHost && pa.devicePointer && g->host_copy == CFD_HOST_COPY_KERNEL)
+    if (pa.type == cudaMemoryTypeHost && pa.devicePointer && g->host_copy != CFD_HOST_COPY_ENGINE)
       direct = pa.devicePointer;
   } else {
     cudaGetLastError();  // clear the query's error for plain host memory
   }
   if ((s = join_in(g)) != CFD_OK) return s;
-  if (direct) {
+  if (direct && g->host_copy == CFD_HOST_COPY_NARROW &&
+      launch_pack_narrow(L, array, direct, to_device ? 0 : 1) == cudaSuccess) {
+    // transferred by the narrow pack kernel
+  } else if (direct) {
     CK(g, launch_pack(L, array, direct, to_device ? 0 : 1));
   } else {
     char* stage = g->base + g->staging_off;
@@ -1883,8 +1886,9 @@ cfd_status cfd_copy_interior(cfd_grid* g, int block, int array, void* host, int 
 
 cfd_status cfd_set_host_copy(cfd_grid* g, int mode) {
   if (!g) return fail(CFD_EINVAL, "null grid");
-  if (mode != CFD_HOST_COPY_KERNEL && mode != CFD_HOST_COPY_ENGINE)
-    return fail(CFD_EINVAL, "mode must be CFD_HOST_COPY_KERNEL or CFD_HOST_COPY_ENGINE");
+  if (mode != CFD_HOST_COPY_KERNEL && mode != CFD_HOST_COPY_ENGINE && mode != CFD_HOST_COPY_NARROW)
+    return fail(CFD_EINVAL,
+                "mode must be CFD_HOST_COPY_KERNEL, CFD_HOST_COPY_ENGINE or CFD_HOST_COPY_NARROW");
   g->host_copy = mode;
   return CFD_OK;
 }

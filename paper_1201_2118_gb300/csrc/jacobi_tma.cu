@@ -453,6 +453,8 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
   unsigned long long* full = reinterpret_cast<unsigned long long*>(s1 + NS1 * G::SPLANE);
   unsigned long long* empty = full + S;
   unsigned long long* s1bar = empty + S;
+  unsigned long long* tbar = s1bar + NS1;                          // tile numbers handed out
+  unsigned* tile_q = reinterpret_cast<unsigned*>(tbar + 4);        // ... in four slots
   const int lane = threadIdx.x, w = threadIdx.y;
   if (smem_u32(smem) & 127u) {
     if (w == 0 && lane == 0) atomicOr(L.err_flag, 4);
@@ -466,6 +468,8 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     }
 #pragma unroll
     for (int s = 0; s < NS1; ++s) mbar_init(smem_u32(&s1bar[s]), NW + 1);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) mbar_init(smem_u32(&tbar[s]), 1);
     mbar_fence_init();
   }
   __shared__ TileTable tt;
@@ -480,7 +484,31 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
   unsigned issued = 0;  // planes the producer has issued
   bool bad = false;
   int blk = L.b0;
-  for (long long t = blockIdx.x;; t += gridDim.x) {
+  // Tiles are claimed from a counter in the grid's flag area, so an SM that
+  // shares its issue slots with other work (another grid's host copies)
+  // takes fewer tiles instead of holding up the launch.  Each CTA ends on
+  // one claim past the last tile; atomicInc wraps the counter to 0 on the
+  // final one, ready for the next launch.  The producer claims and hands
+  // the number to the CTA's other warps through a four-slot queue.
+  unsigned* const ctr = reinterpret_cast<unsigned*>(L.err_flag) + 32;
+  const unsigned ctr_wrap = (unsigned)tt.start[L.nblocks] + gridDim.x - 1;
+  for (unsigned k = 0;; ++k) {
+    long long t;
+    if (w == PWARP) {
+      unsigned v = 0;
+      if (lane == 0) {
+        v = atomicInc(ctr, ctr_wrap);
+        tile_q[k & 3] = v;
+        mbar_arrive(smem_u32(&tbar[k & 3]));
+      }
+      t = __shfl_sync(0xffffffffu, v, 0);
+    } else {
+      if (!mbar_wait_split(smem_u32(&tbar[k & 3]), (k >> 2) & 1u)) {
+        bad = true;
+        break;
+      }
+      t = tile_q[k & 3];
+    }
     int i0, j0, k0;
     if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
@@ -719,7 +747,7 @@ cudaError_t run_ws2(const Launch& L, const JacobiCfg& c, const void* maps, int s
                     float omega, float inv_diag) {
   using G = Ws2Geom<T, TY>;
   auto kern = k_jacobi2_ws<T, TY, S, PER>;
-  const int smem = S * G::STAGE + G::NS1 * G::SPLANE * 4 + 8 * (2 * S + G::NS1);
+  const int smem = S * G::STAGE + G::NS1 * G::SPLANE * 4 + 8 * (2 * S + G::NS1 + 4) + 16;
   static int occ = -1;
   if (occ < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

@@ -1463,6 +1463,47 @@ __global__ void __launch_bounds__(256) k_pack(Launch L, int arr, T* compact, int
   }
 }
 
+// The pack copy on a few CTAs: thread t of T moves 16-byte vectors
+// t + u T of each batch (u < 16), all sixteen loads before the stores, so
+// every thread keeps sixteen transfers over the host link in flight;
+// consecutive threads take consecutive vectors of a row.
+template <typename T>
+__global__ void __launch_bounds__(256) k_pack_narrow(Launch L, int arr, T* compact, int to_compact) {
+  constexpr int V = 16 / (int)sizeof(T), U = 16;
+  const BlockDev& B = L.blocks[L.b0];
+  const int nx = B.n[0], ny = B.n[1];
+  const long long vpr = nx / V;                                 // vectors per row
+  const long long total = vpr * ny * B.n[2];
+  const long long py = B.py, pz = B.pz;
+  T* a = reinterpret_cast<T*>(L.base) + B.org[arr];
+  uint4* cv = reinterpret_cast<uint4*>(compact);
+  const long long nthr = (long long)gridDim.x * blockDim.x;
+  const long long tid = (long long)blockIdx.x * blockDim.x + threadIdx.x;
+  auto at = [&](long long k) {  // vector k of the compact order -> the array
+    const long long r = k / vpr, v = k - r * vpr;
+    const long long j = r % ny, kz = r / ny;
+    return reinterpret_cast<uint4*>(a + kz * pz + j * py) + v;
+  };
+  for (long long base = tid; base < total; base += U * nthr) {
+    uint4 x[U];
+    if (to_compact) {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + u * nthr < total) x[u] = *at(base + u * nthr);
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + u * nthr < total) cv[base + u * nthr] = x[u];
+    } else {
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + u * nthr < total) x[u] = cv[base + u * nthr];
+#pragma unroll
+      for (int u = 0; u < U; ++u)
+        if (base + u * nthr < total) *at(base + u * nthr) = x[u];
+    }
+  }
+}
+
 // --------------------------------------------------------------- reductions
 
 __device__ __forceinline__ double warp_sum(double v) {
@@ -1783,6 +1824,16 @@ cudaError_t launch_pack(const Launch& L, int arr, void* compact, int to_compact)
     kern<<<(unsigned)(L.sms * occ), 256, 0, L.stream>>>(L, arr, static_cast<T*>(compact),
                                                        to_compact);
   });
+  return cudaGetLastError();
+}
+
+cudaError_t launch_pack_narrow(const Launch& L, int arr, void* compact, int to_compact) {
+  const int es = L.dtype == 0 ? 4 : 2;
+  if (L.hn[L.b0][0] % (16 / es) != 0 || reinterpret_cast<uintptr_t>(compact) % 16 != 0)
+    return cudaErrorInvalidValue;
+  const unsigned grid = (unsigned)std::max(1, L.sms / 8);
+  CFD_DISPATCH_T(L.dtype, k_pack_narrow<T><<<grid, 256, 0, L.stream>>>(L, arr, static_cast<T*>(compact),
+                                                                        to_compact));
   return cudaGetLastError();
 }
 

@@ -269,11 +269,13 @@ class Grid:
 
     def set_host_copy(self, mode: str = "kernel"):
         """Route of copy_interior for page-locked host memory: 'kernel' (the
-        pack kernel over the host link) or 'engine' (a copy engine through
-        the staging region, leaving the SMs to other streams)."""
-        modes = {"kernel": 0, "engine": 1}
+        pack kernel over the host link), 'engine' (a copy engine through
+        the staging region, leaving the SMs to other streams) or 'narrow'
+        (the pack kernel on one CTA per eight SMs, many transfers in flight
+        per thread)."""
+        modes = {"kernel": 0, "engine": 1, "narrow": 2}
         if mode not in modes:
-            raise ValueError("mode must be 'kernel' or 'engine'")
+            raise ValueError("mode must be 'kernel', 'engine' or 'narrow'")
         call("cfd_set_host_copy", self.handle, modes[mode])
 
     def adjoint_step(self, dt: float, un_ptrs, u1_ptrs, dnu_dev_ptr: int):

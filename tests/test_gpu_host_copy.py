@@ -13,10 +13,13 @@ import workloads
 pytestmark = pytest.mark.gpu
 
 
-@pytest.mark.parametrize("mode", ["kernel", "engine"])
-@pytest.mark.parametrize("dims,dtype", [((64, 20, 7), "f32"), ((45, 37, 21), "f32"),
-                                        ((70, 9, 5), "bf16"), ((33, 16, 4), "f16")])
-def test_copy_interior_round_trip(dims, dtype, mode):
+@pytest.mark.parametrize("mode", ["kernel", "engine", "narrow"])
+@pytest.mark.parametrize("dims,dtype,shift", [((64, 20, 7), "f32", 0), ((64, 20, 7), "f32", 1),
+                                              ((45, 37, 21), "f32", 0), ((70, 9, 5), "bf16", 0),
+                                              ((64, 9, 5), "bf16", 0), ((33, 16, 4), "f16", 0)])
+def test_copy_interior_round_trip(dims, dtype, shift, mode):
+    """shift 1: the host buffer starts one element past a 16-byte boundary
+    (the pack kernels then move elements one by one)."""
     import torch
     from paper_1201_2118_gb300 import Grid, U, P, R
     g = Grid(dims, ghost=1, h=(0.1, 0.1, 0.1), dtype=dtype)
@@ -24,7 +27,9 @@ def test_copy_interior_round_trip(dims, dtype, mode):
     g.fill(float("nan"))
     td = g.tdtype
     rng = np.random.default_rng(3)
-    src = torch.from_numpy(rng.uniform(-1, 1, dims[::-1])).to(td).pin_memory()
+    cells = dims[0] * dims[1] * dims[2]
+    big = torch.from_numpy(rng.uniform(-1, 1, cells + shift)).to(td).pin_memory()
+    src = big[shift:].view(dims[::-1])
     for arr in (U, P):
         g.copy_interior(arr, src.data_ptr(), to_device=True)
         torch.cuda.synchronize()
@@ -34,7 +39,7 @@ def test_copy_interior_round_trip(dims, dtype, mode):
     assert torch.isnan(full[0]).all() and torch.isnan(full[:, 0]).all()
     # device -> host of a different array
     g.interior(R).copy_(torch.from_numpy(rng.uniform(-2, 2, dims[::-1])).to(td).cuda())
-    dst = torch.empty(dims[::-1], dtype=td).pin_memory()
+    dst = torch.empty(cells + shift, dtype=td).pin_memory()[shift:].view(dims[::-1])
     g.copy_interior(R, dst.data_ptr(), to_device=False)
     torch.cuda.synchronize()
     assert torch.equal(dst, g.interior(R).cpu())
@@ -83,16 +88,17 @@ def test_set_host_copy_rejects_unknown_mode():
     from paper_1201_2118_gb300._lib import call
     g = Grid((16, 16, 16), ghost=1, h=(0.1, 0.1, 0.1))
     with pytest.raises(CfdError) as e:
-        call("cfd_set_host_copy", g.handle, 2)
+        call("cfd_set_host_copy", g.handle, 3)
     assert e.value.status == 1
     with pytest.raises(ValueError):
         g.set_host_copy("dma")
     g.check()
 
 
-def test_two_grids_pipelined_engine_copies_equal_serial_steps():
+@pytest.mark.parametrize("route", ["engine", "narrow"])
+def test_two_grids_pipelined_copies_equal_serial_steps(route):
     """Two independent cavity problems on two streams: each step copies its
-    inputs in (engine route), steps and copies u, v, w, p out, with the
+    inputs in (engine or narrow route), steps and copies u, v, w, p out, with the
     other grid's copies and step in flight.  Results are bitwise those of
     the same steps taken one grid after the other with the kernel route."""
     import torch
@@ -129,7 +135,7 @@ def test_two_grids_pipelined_engine_copies_equal_serial_steps():
 
     cur = torch.cuda.current_stream()
     serial = run("kernel", [cur, cur])
-    piped = run("engine", [torch.cuda.Stream(), torch.cuda.Stream()])
+    piped = run(route, [torch.cuda.Stream(), torch.cuda.Stream()])
     for k in range(2):
         for c in range(4):
             assert torch.equal(piped[k][c], serial[k][c]), (k, c)
