@@ -91,7 +91,16 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
   __shared__ TileTable tt;
   tile_table_build(tt, L, TX, TY, zc);
   int blk = L.b0;
-  for (long long t = blockIdx.x;; t += gridDim.x) {
+  // tiles claimed at run time from the counter in the grid's flag area:
+  // thread 0 claims, the CTA barrier hands the number out (two slots: a
+  // slot is rewritten two tiles later, after the planes' barriers between)
+  __shared__ unsigned tile_no[2];
+  unsigned* const ctr = tile_counter(L);
+  const unsigned ctr_wrap = (unsigned)tt.start[L.nblocks] + gridDim.x - 1;
+  for (unsigned kq = 0;; ++kq) {
+    if (tid == 0) tile_no[kq & 1] = atomicInc(ctr, ctr_wrap);
+    __syncthreads();
+    const long long t = tile_no[kq & 1];
     int i0, j0, k0;
     if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
@@ -245,6 +254,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
   extern __shared__ __align__(128) unsigned char smem[];
   unsigned long long* full = reinterpret_cast<unsigned long long*>(smem + S * Gm::STAGE);
   unsigned long long* empty = full + S;
+  const TileQueue tq{empty + S, reinterpret_cast<unsigned*>(empty + S + 4)};
   __shared__ RowImage<T> rimg[TY][4];
   const int lane = threadIdx.x, w = threadIdx.y;
   if (smem_u32(smem) & 127u) {
@@ -257,6 +267,7 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
       mbar_init(smem_u32(&full[s]), 1);
       mbar_init(smem_u32(&empty[s]), TY);
     }
+    tq.init();
     mbar_fence_init();
   }
   __shared__ TileTable tt;
@@ -269,7 +280,17 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
   unsigned issued = 0;  // planes the producer has issued
   bool bad = false;
   int blk = L.b0;
-  for (long long t = blockIdx.x;; t += gridDim.x) {
+  // tiles claimed at run time from the counter in the grid's flag area
+  unsigned* const ctr = tile_counter(L);
+  const unsigned ctr_wrap = (unsigned)tt.start[L.nblocks] + gridDim.x - 1;
+  for (unsigned kq = 0;; ++kq) {
+    long long t;
+    if (w == TY) {
+      t = tq.claim(kq, ctr, ctr_wrap, lane);
+    } else if (!tq.take(kq, t)) {
+      bad = true;
+      break;
+    }
     int i0, j0, k0;
     if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
     const BlockDev& B = L.blocks[blk];
@@ -453,8 +474,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
   unsigned long long* full = reinterpret_cast<unsigned long long*>(s1 + NS1 * G::SPLANE);
   unsigned long long* empty = full + S;
   unsigned long long* s1bar = empty + S;
-  unsigned long long* tbar = s1bar + NS1;                          // tile numbers handed out
-  unsigned* tile_q = reinterpret_cast<unsigned*>(tbar + 4);        // ... in four slots
+  const TileQueue tq{s1bar + NS1, reinterpret_cast<unsigned*>(s1bar + NS1 + 4)};
   const int lane = threadIdx.x, w = threadIdx.y;
   if (smem_u32(smem) & 127u) {
     if (w == 0 && lane == 0) atomicOr(L.err_flag, 4);
@@ -468,8 +488,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     }
 #pragma unroll
     for (int s = 0; s < NS1; ++s) mbar_init(smem_u32(&s1bar[s]), NW + 1);
-#pragma unroll
-    for (int s = 0; s < 4; ++s) mbar_init(smem_u32(&tbar[s]), 1);
+    tq.init();
     mbar_fence_init();
   }
   __shared__ TileTable tt;
@@ -484,30 +503,16 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
   unsigned issued = 0;  // planes the producer has issued
   bool bad = false;
   int blk = L.b0;
-  // Tiles are claimed from a counter in the grid's flag area, so an SM that
-  // shares its issue slots with other work (another grid's host copies)
-  // takes fewer tiles instead of holding up the launch.  Each CTA ends on
-  // one claim past the last tile; atomicInc wraps the counter to 0 on the
-  // final one, ready for the next launch.  The producer claims and hands
-  // the number to the CTA's other warps through a four-slot queue.
-  unsigned* const ctr = reinterpret_cast<unsigned*>(L.err_flag) + 32;
+  // tiles claimed at run time from the counter in the grid's flag area
+  unsigned* const ctr = tile_counter(L);
   const unsigned ctr_wrap = (unsigned)tt.start[L.nblocks] + gridDim.x - 1;
   for (unsigned k = 0;; ++k) {
     long long t;
     if (w == PWARP) {
-      unsigned v = 0;
-      if (lane == 0) {
-        v = atomicInc(ctr, ctr_wrap);
-        tile_q[k & 3] = v;
-        mbar_arrive(smem_u32(&tbar[k & 3]));
-      }
-      t = __shfl_sync(0xffffffffu, v, 0);
-    } else {
-      if (!mbar_wait_split(smem_u32(&tbar[k & 3]), (k >> 2) & 1u)) {
-        bad = true;
-        break;
-      }
-      t = tile_q[k & 3];
+      t = tq.claim(k, ctr, ctr_wrap, lane);
+    } else if (!tq.take(k, t)) {
+      bad = true;
+      break;
     }
     int i0, j0, k0;
     if (!tile_locate(tt, L, t, TX, TY, zc, blk, i0, j0, k0)) break;
@@ -769,7 +774,7 @@ cudaError_t run_ws(const Launch& L, const JacobiCfg& c, const void* maps, int sr
                    float omega, float inv_diag) {
   using Gm = TmaGeom<T, VX, TY>;
   auto kern = k_jacobi_ws<T, VX, TY, S>;
-  const int smem = S * Gm::STAGE + 16 * S;
+  const int smem = S * Gm::STAGE + 16 * S + 8 * 4 + 16;  // stages, full/empty, tile queue
   static int occ = -1;
   if (occ < 0) {
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, smem);

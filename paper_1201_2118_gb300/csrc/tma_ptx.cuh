@@ -6,6 +6,8 @@
 #include <cuda.h>
 #include <cstdint>
 
+#include "cfd_internal.h"
+
 namespace cfd {
 namespace {
 
@@ -96,6 +98,45 @@ struct Ring {
       s = 0;
       ph ^= 1u;
     }
+  }
+};
+
+// The tile counter of a launch: a word of the grid's flag area (zeroed when
+// memory is bound), 128 bytes after the device error flag.
+__device__ __forceinline__ unsigned* tile_counter(const Launch& L) {
+  return reinterpret_cast<unsigned*>(L.err_flag) + 32;
+}
+
+// Tiles claimed at run time by warp-specialised kernels: lane 0 of the
+// producer warp takes the next tile number from a counter in device memory
+// and hands it to the CTA's other warps through a four-slot queue guarded by
+// mbarriers (count 1).  Every CTA ends on one claim past the last tile, so
+// atomicInc with wrap = tiles + CTAs - 1 leaves the counter at 0 for the
+// next launch.  An SM that shares its issue slots with other work takes
+// fewer tiles instead of holding up the launch.
+struct TileQueue {
+  unsigned long long* bar;  // 4 mbarriers
+  unsigned* slot;           // 4 tile numbers
+  __device__ __forceinline__ void init() const {
+#pragma unroll
+    for (int s = 0; s < 4; ++s) mbar_init(smem_u32(&bar[s]), 1);
+  }
+  // producer warp, every lane: the k-th tile of this CTA
+  __device__ __forceinline__ unsigned claim(unsigned k, unsigned* ctr, unsigned wrap,
+                                            int lane) const {
+    unsigned v = 0;
+    if (lane == 0) {
+      v = atomicInc(ctr, wrap);
+      slot[k & 3] = v;
+      mbar_arrive(smem_u32(&bar[k & 3]));
+    }
+    return __shfl_sync(0xffffffffu, v, 0);
+  }
+  // the other warps: false if the bounded wait gave up
+  __device__ __forceinline__ bool take(unsigned k, long long& t) const {
+    if (!mbar_wait_split(smem_u32(&bar[k & 3]), (k >> 2) & 1u)) return false;
+    t = slot[k & 3];
+    return true;
   }
 };
 
