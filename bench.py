@@ -221,7 +221,7 @@ def oracle_sample(seconds_hint=False, detail=True):
     el, cores = _oracle_step_time(n, 0)
     out = {"value": n ** 3 / el / 1e9, "unit": UNIT, "cores": cores, "kind": "oracle",
            "sample": "1 RK2 step (2 x 50 Jacobi sweeps) of the 256^3 lid-driven cavity, "
-                     "FP64 C oracle, OpenMP over z; %.1f s" % el}
+                     "FP64 C oracle, OpenMP over rows (k, j); %.1f s" % el}
     if detail:
         m = 128
         e1, _ = _oracle_step_time(m, 1)
@@ -273,7 +273,7 @@ def run_reference(a):
     value = cells * steps / total / 1e9
     ke, umax, divmax = o.reduce(u)
     sample = ("%d consecutive RK2 steps (2 x %d Jacobi sweeps each) of the %dx%dx%d lid-driven "
-              "cavity from the bench's start, FP64 C oracle, OpenMP over z on %d host threads; "
+              "cavity from the bench's start, FP64 C oracle, OpenMP over rows (k, j) on %d host threads; "
               "%.1f s timed%s" % (steps, cfg["jacobi_iters"], dims[0], dims[1], dims[2], cores,
                                   total, "" if steps == a.steps else
                                   "; stopped after %d of %d requested steps (%.0f s budget)"

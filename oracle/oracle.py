@@ -28,7 +28,7 @@ FORMS = {"advective": 0, "flux": 1}
 
 
 def build(force: bool = False) -> str:
-    """Compile the oracle with gcc (plain C99, -O2, OpenMP over k)."""
+    """Compile the oracle with gcc (plain C99, -O2, OpenMP over rows (k, j))."""
     srcs = [os.path.join(_HERE, s) for s in _SOURCES if os.path.exists(os.path.join(_HERE, s))]
     newest = max(os.path.getmtime(s) for s in srcs + [os.path.join(_HERE, "cfd_oracle.h")])
     if not force and os.path.exists(_LIB_PATH) and os.path.getmtime(_LIB_PATH) >= newest:
