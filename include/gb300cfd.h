@@ -361,10 +361,11 @@ cfd_status cfd_set_host_copy(cfd_grid* g, int mode);
  * ring, ty consumer warps; vx 4 with ty in {4,8,16} and stages in {6,8}, or
  * vx 2 (64-wide tiles, for narrow blocks) with ty in {8,16} and 6 stages),
  * kind 9 two sweeps per launch in the warp-specialised TMA form (temporal
- * blocking; vx 4 with (ty, stages) in {(16,6), (16,7), (8,5), (8,6)}; used on
- * single-block grids whose six faces are walls or, with two ghost layers,
- * are all periodic; odd sweep counts and other grids take single sweeps of
- * kind 0);
+ * blocking; vx 4 with (ty, stages) in {(16,6), (16,7), (8,5), (8,6)}, or
+ * vx 2 (64-wide tiles, for narrow blocks) with ty in {8,16} and 6 stages;
+ * used on single-block grids whose six faces are walls, and on grids or
+ * block sets whose faces are all periodic with two ghost layers; odd sweep
+ * counts and other grids take single sweeps of kind 0);
  * zc = z-planes per tile.
  * stencil = {ty in {4,8}, zc, tile_tz in {0..4}} for the point kernels:
  * rows per CTA, z chunk, and for the RHS + stage kernel either neighbour
@@ -382,15 +383,18 @@ cfd_status cfd_get_kernel_config(const cfd_grid* g, int jacobi[5], int stencil[3
  * keeps U and P) and selects the fastest; with cache_path, reuses or
  * appends a line keyed by GPU name, dtype, ghost, order and block sizes.
  * The Cactus driver's auto-tuning of the data distribution (Sec. 1.2),
- * re-targeted to the kernels' tile shapes.  sweep_us (may be NULL)
- * receives the chosen Jacobi sweep time in microseconds. */
+ * re-targeted to the kernels' tile shapes.  Each Jacobi variant is timed
+ * on runs of as many sweeps as a solve takes (rounded down to a multiple of
+ * four, 4 .. 16), ghost fills between launches included.  sweep_us (may be
+ * NULL) receives the chosen variant's time per sweep in microseconds. */
 cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us);
 
 /* Launch mode of the stencil kernels (RHS/stage, divergence, Jacobi,
  * projection) on a block set: 0 (default) = one persistent launch walks the
  * tiles of all blocks; 1 = one launch per block per kernel (the baseline the
- * batched form is measured against).  Ghost fills stay one launch.  Results
- * are identical. */
+ * batched form is measured against; its Jacobi sweeps are single sweeps,
+ * so a two-sweep variant sweeps once per launch with the register kernel
+ * there).  Ghost fills stay one launch.  Results are identical. */
 cfd_status cfd_set_launch_mode(cfd_grid* g, int per_block);
 
 /* Number of kernel launches this grid has enqueued so far (graph replays

@@ -127,21 +127,26 @@ cudaError_t launch_adj_stage(const Launch& L, const AdjSet& lam, const Ptr3& y, 
                              float nu, double* partials, int nparts, double* nu_acc,
                              double nu_coef, bool flux);
 
-// One piece of a block's ghost shell, built on the host: rows r0 .. r1 - 1
-// of the box of one direction (dx, dy, dz) around block dst (g layers deep
-// along the axes where d is non-zero, the block's extent elsewhere), copied
-// from block src.  ax = {inner axis, row axis j, row axis k}; per those
-// axes: extent e, destination origin d0 (ghost index in dst), source origin
-// s0 and step st in src (+1: the shifted copy across a periodic or
-// block-to-block face, -1: the mirror image at a wall).  wface[a] is the
-// wall face met along axis a (x, y, z), -1 if none; the wall rules compose
-// in that axis order.
+// One piece of a block's ghost shell, built on the host, from the box of
+// one direction (dx, dy, dz) around block dst (g layers deep along the axes
+// where d is non-zero, the block's extent elsewhere), copied from block src.
+// ax = {inner axis, row axis j, plane axis k}; per those axes: destination
+// origin d0 (ghost index in dst), source origin s0 and step st in src (+1:
+// the shifted copy across a periodic or block-to-block face, -1: the mirror
+// image at a wall).  wface[a] is the wall face met along axis a (x, y, z),
+// -1 if none; the wall rules compose in that axis order.  The piece is the
+// inner-axis range i0 .. i0 + ni - 1 (ni <= kGhostItemCells) of rows
+// rj0 .. rj0 + nrows - 1 of plane rk; a warp lays its lanes out as 2^sh
+// columns by 32 >> sh rows and covers it in at most eight steps (passes
+// over the row range: P = ni / 2^sh rounded up).
+constexpr int kGhostItemCells = 256;
 struct GhostItem {
   int dst, src;
   int ax[3];
-  int e[3], d0[3], s0[3], st[3];
+  int d0[3], s0[3], st[3];
   int wface[3];
-  int r0, r1;
+  int i0, ni, rj0, nrows, rk;
+  int sh, passes;
 };
 
 cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr, const GhostItem* items,

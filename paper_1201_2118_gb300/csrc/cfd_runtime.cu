@@ -165,11 +165,10 @@ cfd_status usable(cfd_grid* g) {
 // neighbours nbr (6 each), faces bc, ghost width gw, appended to out: per
 // block the 26 boxes of its ghost shell with their sources (axis by axis,
 // x then y then z: across a periodic face into the neighbour, mirrored at a
-// wall), each cut into pieces of at most 16 rows.  False if a box has 2^31
-// or more rows.
+// wall), each cut into pieces of at most eight warp-wide steps (GhostItem).
+// False if the grid has 2^30 or more pieces.
 bool ghost_items(const int* n, const int* nbr, int nb, const int bc[6], int gw,
                  std::vector<GhostItem>& out) {
-  constexpr int kRows = 16;
   for (int b = 0; b < nb; ++b)
     for (int dir = 0; dir < 27; ++dir) {
       if (dir == 13) continue;
@@ -199,32 +198,49 @@ bool ghost_items(const int* n, const int* nbr, int nb, const int bc[6], int gw,
           wf[a] = face;
         }
       }
-      const int ia = ext[0] >= 16 ? 0 : (ext[1] >= ext[2] ? 1 : 2);
-      const int ax[3] = {ia, ia == 0 ? 1 : 0, ia == 2 ? 1 : 2};
-      const long long rows = (long long)ext[ax[1]] * ext[ax[2]];
-      if (rows >= (1LL << 31)) return false;
-      for (long long r = 0; r < rows; r += kRows) {
-        GhostItem it{};
-        it.dst = b;
-        it.src = sbk;
-        for (int k = 0; k < 3; ++k) {
-          it.ax[k] = ax[k];
-          it.e[k] = ext[ax[k]];
-          it.d0[k] = d0[ax[k]];
-          it.s0[k] = s0[ax[k]];
-          it.st[k] = st[ax[k]];
-          it.wface[k] = wf[k];
-        }
-        it.r0 = (int)r;
-        it.r1 = (int)std::min(rows, r + kRows);
-        out.push_back(it);
+      // inner axis x unless the box is one cell thin there (two ghost
+      // layers side by side share a 32-byte sector, so one warp access
+      // takes both); rows along the longer of the other two axes
+      const int ia = ext[0] >= 2 ? 0 : (ext[1] >= ext[2] ? 1 : 2);
+      const int o1 = ia == 0 ? 1 : 0, o2 = ia == 2 ? 1 : 2;
+      const int ja = ext[o1] >= ext[o2] ? o1 : o2, ka = ja == o1 ? o2 : o1;
+      const int ax[3] = {ia, ja, ka};
+      const int ei = ext[ia], ej = ext[ja], ek = ext[ka];
+      for (int i0 = 0; i0 < ei; i0 += kGhostItemCells) {
+        const int ni = std::min(kGhostItemCells, ei - i0);
+        int sh = 0;
+        while ((1 << sh) < ni && sh < 5) ++sh;     // columns: ni rounded up to a power of two, <= 32
+        const int passes = (ni + (1 << sh) - 1) >> sh;
+        const int rows = (32 >> sh) * std::max(1, 8 / passes);  // rows of one piece
+        for (int rk = 0; rk < ek; ++rk)
+          for (int rj0 = 0; rj0 < ej; rj0 += rows) {
+            GhostItem it{};
+            it.dst = b;
+            it.src = sbk;
+            for (int k = 0; k < 3; ++k) {
+              it.ax[k] = ax[k];
+              it.d0[k] = d0[ax[k]];
+              it.s0[k] = s0[ax[k]];
+              it.st[k] = st[ax[k]];
+              it.wface[k] = wf[k];
+            }
+            it.i0 = i0;
+            it.ni = ni;
+            it.rj0 = rj0;
+            it.nrows = std::min(rows, ej - rj0);
+            it.rk = rk;
+            it.sh = sh;
+            it.passes = passes;
+            out.push_back(it);
+            if (out.size() >= (size_t)1 << 30) return false;  // CTA numbers x 8 warps in 32 bits
+          }
       }
     }
   return true;
 }
 
 // All ghost items of the grid and of its multigrid levels (gitems empty if
-// a box is too large).  Depends on the faces' kinds: rebuilt with the tables.
+// there are too many).  Depends on the faces' kinds: rebuilt with the tables.
 void build_ghost_items(cfd_grid* g) {
   g->gitems.clear();
   g->gitem_first.assign(g->mgl.size() + 1, 0);
@@ -435,8 +451,8 @@ cfd_status common_init(cfd_grid* g, int ghost, const double h[3], int storage, v
     for (int d = 0; d < 3; ++d) g->hn[3 * b + d] = g->hb[b].n[d];
   g->jcfg = JacobiCfg{0, 4, 8, 32, 4};
   plan_layout(g);
-  if (g->gitems.empty())  // the ghost kernel counts a box's rows in 32 bits
-    return fail(CFD_EINVAL, "a block's ghost box has 2^31 or more rows");
+  if (g->gitems.empty())  // the ghost kernel numbers its pieces in 32 bits
+    return fail(CFD_EINVAL, "the ghost shell has 2^30 or more pieces");
   if (!g->mgl.empty() && (e = prepare_mg_bottom()) != cudaSuccess)
     return cuda_fail(nullptr, e, "cudaFuncSetAttribute");
   return CFD_OK;
@@ -534,8 +550,10 @@ bool ws2_periodic(const cfd_grid* g) {
 
 // Fused two-sweep launches apply: kind 9 on a single block whose six faces
 // are walls, or in the periodic form (single blocks and block sets); kind 5
-// on single blocks with tiles dividing x and y.
+// on single blocks with tiles dividing x and y.  Never in the one-launch-
+// per-block mode, whose sweeps are the baseline of the batched form.
 bool fused_ok(const cfd_grid* g) {
+  if (g->per_block && g->nblocks > 1) return false;
   if (g->jcfg.kind == 9) {
     if (!g->maps_ready) return false;
     if (ws2_periodic(g)) return true;
@@ -902,9 +920,17 @@ cfd_status enq_adjoint_step(cfd_grid* g, double dt, const Ptr3& un, const Ptr3& 
     if ((s = enq_ghost(g, stage == 2 ? m_lu : set_mask(CFD_SET_U1))) != CFD_OK) return s;
     CK(g, launch_adj_proj(L, lam_in, A_LP, (float)c_dt, r_scale, A_P, A_R));
     if ((s = enq_ghost(g, 1u << A_P)) != CFD_OK) return s;
+    // the first K - 1 sweeps as a solve (two per launch where the variant
+    // does that), the last one single, so that both of the last two
+    // iterates are stored
     int cur = A_P, oth = A_P2;
-    for (int it = 0; it < g->iters; ++it) {
+    if (g->iters >= 2) {
+      if ((s = enq_sweeps(g, g->iters - 1, g->omega, A_P, &cur)) != CFD_OK) return s;
+      oth = cur == A_P ? A_P2 : A_P;
+    }
+    if (g->iters >= 1) {
       CK(g, sweep(g, L, cur, oth, (float)g->omega));
+      g->launches += 1;
       std::swap(cur, oth);
     }
     // cur = b_{K+1}, oth = b_K (for K = 0, b_1 in both roles: lam_r = 0 path)
@@ -917,7 +943,7 @@ cfd_status enq_adjoint_step(cfd_grid* g, double dt, const Ptr3& un, const Ptr3& 
     else
       CK(g, launch_adj_stage(L, ws, un, lu, 1, 1.0f, (float)dt, 0, lu, 0.0f, (float)g->nu,
                              partials, g->nparts, nu_acc, dt, g->form == CFD_FLUX));
-    g->launches += 5 + g->iters;
+    g->launches += 5;
   }
   return CFD_OK;
 }
@@ -946,6 +972,10 @@ std::string tune_key(cfd_grid* g) {
   return buf;
 }
 
+// Jacobi sweeps per timed region of the autotuner: the solve's count
+// rounded down to a multiple of four, within 4 .. 16.
+int tune_sweeps(const cfd_grid* g) { return std::min(16, std::max(4, g->iters / 4 * 4)); }
+
 cfd_status time_region(cfd_grid* g, int reps, float* ms, int what) {
   cudaEvent_t a, b;
   CK(g, cudaEventCreate(&a));
@@ -953,11 +983,13 @@ cfd_status time_region(cfd_grid* g, int reps, float* ms, int what) {
   CK(g, cudaEventRecord(a, g->own));
   cfd_status s = CFD_OK;
   for (int r = 0; r < reps && s == CFD_OK; ++r)
-    // four sweeps end in P for every variant, so no copy is timed; the RHS
-    // kernels are timed in both of a step's forms (stage 1 reads one
-    // velocity set, stage 2 two)
+    // a multiple of four sweeps ends in P for every variant, so no copy is
+    // timed, and as many as a solve takes up to 16, so that the ghost fill a
+    // two-sweep solve makes before its first launch weighs as in a solve;
+    // the RHS kernels are timed in both of a step's forms (stage 1 reads
+    // one velocity set, stage 2 two)
     if (what == 0) {
-      s = enq_sweeps(g, 4, g->omega);
+      s = enq_sweeps(g, tune_sweeps(g), g->omega);
     } else {
       s = enq_stage(g, 0.0, CFD_SET_U, 1.0, CFD_SET_U, 1e-3, CFD_SET_W);
       if (s == CFD_OK) s = enq_stage(g, 0.5, CFD_SET_U, 0.5, CFD_SET_U1, 1e-3, CFD_SET_W);
@@ -1393,9 +1425,10 @@ cfd_status cfd_set_kernel_config(cfd_grid* g, const int jacobi[5], const int ste
                      ((c.vx == 4 && (c.ty == 4 || c.ty == 8 || c.ty == 16) &&
                        (c.stages == 6 || c.stages == 8)) ||
                       (c.vx == 2 && (c.ty == 8 || c.ty == 16) && c.stages == 6));
-    const bool ok9 = c.kind == 9 && c.vx == 4 &&
-                     ((c.ty == 16 && (c.stages == 6 || c.stages == 7)) ||
-                      (c.ty == 8 && (c.stages == 5 || c.stages == 6)));
+    const bool ok9 = c.kind == 9 &&
+                     ((c.vx == 4 && ((c.ty == 16 && (c.stages == 6 || c.stages == 7)) ||
+                                     (c.ty == 8 && (c.stages == 5 || c.stages == 6)))) ||
+                      (c.vx == 2 && (c.ty == 16 || c.ty == 8) && c.stages == 6));
     if (!(ok0 || ok1 || ok2 || ok3 || ok5 || ok7 || ok9) || c.zc < 1)
       return fail(CFD_EINVAL, "unsupported Jacobi config");
     g->jcfg = c;
@@ -1460,6 +1493,9 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
     for (const JacobiCfg& d : {JacobiCfg{9, 4, 16, zc, 7}, JacobiCfg{9, 4, 16, zc, 6},
                                JacobiCfg{9, 4, 8, zc, 5}, JacobiCfg{9, 4, 8, zc, 6}})
       cands.push_back(d);
+  if (g->nblocks > 1)  // two sweeps per launch on 64-wide tiles
+    for (int zc : {16, 32, 64})
+      for (int ty : {8, 16}) cands.push_back({9, 2, ty, zc, 6});
   const int avx = g->dtype == CFD_F32 ? 4 : 8;
   for (int zc : {16, 32, 64})
     for (const JacobiCfg& d : {JacobiCfg{3, avx, 4, zc, 5}, JacobiCfg{3, avx, 4, zc, 6},
@@ -1512,7 +1548,7 @@ cfd_status cfd_autotune(cfd_grid* g, const char* cache_path, double* sweep_us) {
     }
   g->scfg = sbest;
   invalidate_graph(g);
-  const double us = best_ms * 1000.0 / 20.0;  // 5 repetitions x 4 sweeps
+  const double us = best_ms * 1000.0 / (5.0 * tune_sweeps(g));  // 5 timed repetitions
   if (sweep_us) *sweep_us = us;
   if (cache_path) {
     if (FILE* f = fopen(cache_path, "a")) {

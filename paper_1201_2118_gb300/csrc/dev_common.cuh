@@ -156,6 +156,25 @@ __device__ __forceinline__ void jac_row4(const Jac2& J, const float (&c)[4], flo
   unpk2(o23, out[2], out[3]);
 }
 
+// two cells of a row (VX = 2) with their x neighbours left/right
+__device__ __forceinline__ void jac_row2(const Jac2& J, const float (&c)[2], float left,
+                                         float right, const float (&ym)[2], const float (&yp)[2],
+                                         const float (&zm)[2], const float (&zp)[2],
+                                         const float (&r)[2], float (&out)[2]) {
+  const unsigned long long x01 = pk2(__fadd_rn(left, c[1]), __fadd_rn(c[0], right));
+  const unsigned long long o01 = J(pk2(c[0], c[1]), x01, pk2(ym[0], ym[1]), pk2(yp[0], yp[1]),
+                                   pk2(zm[0], zm[1]), pk2(zp[0], zp[1]), pk2(r[0], r[1]));
+  unpk2(o01, out[0], out[1]);
+}
+template <int VX>
+__device__ __forceinline__ void jac_row(const Jac2& J, const float (&c)[VX], float left,
+                                        float right, const float (&ym)[VX], const float (&yp)[VX],
+                                        const float (&zm)[VX], const float (&zp)[VX],
+                                        const float (&r)[VX], float (&out)[VX]) {
+  if constexpr (VX == 4) jac_row4(J, c, left, right, ym, yp, zm, zp, r, out);
+  else jac_row2(J, c, left, right, ym, yp, zm, zp, r, out);
+}
+
 // ------------------------------------------------------- ghost-on-write
 //
 // A Jacobi sweep writes each new face value of p also into the first ghost

@@ -410,18 +410,18 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
 // blocking for grids whose six faces are walls).  p' = J(p), p'' = J(p')
 // with the same r; p' never leaves the SM.
 //
-// Tile: 128 x TY output cells of one block, walked along z in chunks of zc
-// planes.  Warps: TY + 2 row warps, one extras warp, one producer warp.
+// Tile: 32 VX x TY output cells of one block (VX = 4, or 2 for narrow
+// blocks), walked along z in chunks of zc planes.  Warps: TY + 2 row warps, one extras warp, one producer warp.
 // The producer loads, per plane, the p box (x from i0 - HX, rows j0 - 2 ..
 // j0 + TY + 1) and the r box (rows j0 - 1 .. j0 + TY) into an S-stage ring.
 // In iteration t, row warps 1 .. TY first take the second sweep on plane
 // m - 2 (m = k0 - 1 + t) from slots t - 3 .. t - 1 of a shared-memory ring
 // of NS1 first-sweep planes and r from the stage of plane m - 2, and write
 // it to global memory with its ghost-on-write images; then row warp w
-// (row y = j0 - 1 + w, 4 cells per lane) takes the first sweep on plane m
-// over x = i0 .. i0 + 127 and the extras warp the cells x = i0 - 1 and
-// x = i0 + 128 of every row; both store it, rounded to the storage type,
-// into slot t (row width 136: x = i0 - 4 at index 0).  An mbarrier per
+// (row y = j0 - 1 + w, VX cells per lane) takes the first sweep on plane m
+// over x = i0 .. i0 + 32 VX - 1 and the extras warp the cells x = i0 - 1 and
+// x = i0 + 32 VX of every row; both store it, rounded to the storage type,
+// into slot t (row width 32 VX + 8: x = i0 - 4 at index 0).  An mbarrier per
 // slot (count TY + 3) says that every row of a first-sweep plane is
 // written; each iteration starts by waiting for the plane of iteration
 // t - 2, which is all the second sweep needs from other warps and bounds
@@ -436,16 +436,16 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
 // the second sweep then needs no substitution and writes no ghost images
 // (the caller fills the output's ghosts after the launch).
 
-template <typename T, int TY>
+template <typename T, int VX, int TY>
 struct Ws2Geom {
-  static constexpr int TX = 128;
+  static constexpr int TX = 32 * VX;
   static constexpr int HX = 16 / (int)sizeof(T);
   static constexpr int PW = TX + 2 * HX;  // p and r box width
   static constexpr int PBYTES = PW * (TY + 4) * (int)sizeof(T);
   static constexpr int RBYTES = PW * (TY + 2) * (int)sizeof(T);
   static constexpr int PSTRIDE = (PBYTES + 127) / 128 * 128;
   static constexpr int STAGE = PSTRIDE + (RBYTES + 127) / 128 * 128;
-  static constexpr int SW = 136;            // first-sweep row width (floats)
+  static constexpr int SW = TX + 8;         // first-sweep row width (floats)
   static constexpr int SPLANE = SW * (TY + 2);
   static constexpr int NS1 = 8;             // first-sweep ring slots (a power of two)
 };
@@ -460,11 +460,11 @@ __device__ __forceinline__ float jac_point(float c, float xm, float xp, float ym
 template <int N>
 __device__ __forceinline__ int wrapn(int x) { return x >= N ? x - N : x; }
 
-template <typename T, int TY, int S, bool PER>
+template <typename T, int VX, int TY, int S, bool PER>
 __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const CUtensorMap* maps,
                                                               int zc, int src_slot, int dst,
                                                               float omega, float inv_diag) {
-  using G = Ws2Geom<T, TY>;
+  using G = Ws2Geom<T, VX, TY>;
   constexpr int TX = G::TX, HX = G::HX, PW = G::PW, SW = G::SW, NS1 = G::NS1;
   constexpr int NW = TY + 2;              // row warps
   constexpr int PWARP = NW + 1;           // warp NW: extras, warp NW + 1: producer
@@ -553,14 +553,14 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     const bool out_row = w >= 1 && w <= TY && yreal;  // second-sweep rows of this tile
     // first-sweep rows: inside the block, or (PER) also the ghost rows
     const bool y1 = PER ? rowwarp && y >= -1 && y <= ny : yreal;
-    const int xl = lane * 4;
+    const int xl = lane * VX;
     const int x0 = i0 + xl;
-    const int nv = min(4, nx - x0);          // cells of this lane inside the block
+    const int nv = min(VX, nx - x0);         // cells of this lane inside the block
     const int prow = (w + 1) * PW + HX + xl; // p box: this lane's first cell
     const int rrow = RS_T + w * PW + HX + xl;
     const int srow = w * SW + 4 + xl;        // first-sweep ring
     const bool xhi_in = nv >= 1 && x0 + nv == nx;  // this lane holds x = nx - 1
-    // extras warp: cell c < 2 NW is row c / 2, x = i0 - 1 (even c) or i0 + 128;
+    // extras warp: cell c < 2 NW is row c / 2, x = i0 - 1 (even c) or i0 + TX;
     // lane l takes cells l and l + 32
     constexpr int NE = (2 * NW + 31) / 32;
     const long long pzl = B.pz;
@@ -598,23 +598,26 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       float* S1 = s1 + (int)((it1 + t) & (NS1 - 1)) * G::SPLANE;
       const bool mreal = PER ? (m >= -1) & (m <= nz) : (m >= 0) & (m < nz);
       if (act1 && mreal) {
-        float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
-        ldv<4>(Pc + prow, c);
-        ldv<4>(Pm + prow, zm);
-        ldv<4>(Pp + prow, zp);
-        ldv<4>(Pc + prow + PW, yp);
-        ldv<4>(Pc + prow - PW, ym);
-        ldv<4>(Pc + rrow, rr);
+        float c[VX], zm[VX], zp[VX], yp[VX], ym[VX], rr[VX];
+        ldv<VX>(Pc + prow, c);
+        ldv<VX>(Pm + prow, zm);
+        ldv<VX>(Pp + prow, zp);
+        ldv<VX>(Pc + prow + PW, yp);
+        ldv<VX>(Pc + prow - PW, ym);
+        ldv<VX>(Pc + rrow, rr);
         const float left = tof(Pc[prow - 1]);
-        const float right = tof(Pc[prow + 4]);
-        float o[4];
-        jac_row4(J2, c, left, right, ym, yp, zm, zp, rr, o);
+        const float right = tof(Pc[prow + VX]);
+        float o[VX];
+        jac_row<VX>(J2, c, left, right, ym, yp, zm, zp, rr, o);
 #pragma unroll
-        for (int e = 0; e < 4; ++e) o[e] = tof(cvt<T>(o[e]));
-        *reinterpret_cast<float4*>(S1 + srow) = make_float4(o[0], o[1], o[2], o[3]);
+        for (int e = 0; e < VX; ++e) o[e] = tof(cvt<T>(o[e]));
+        if constexpr (VX == 4)
+          *reinterpret_cast<float4*>(S1 + srow) = make_float4(o[0], o[1], o[2], o[3]);
+        else
+          *reinterpret_cast<float2*>(S1 + srow) = make_float2(o[0], o[1]);
         if constexpr (!PER) {
-          if (lane == 0 && i0 == 0) S1[srow - 1] = o[0];   // x = -1 <- x = 0
-          if (xhi_in) S1[srow + nv] = pick<4>(o, nv - 1);  // x = nx <- x = nx - 1
+          if (lane == 0 && i0 == 0) S1[srow - 1] = o[0];    // x = -1 <- x = 0
+          if (xhi_in) S1[srow + nv] = pick<VX>(o, nv - 1);  // x = nx <- x = nx - 1
         }
       }
       if (!rowwarp && mreal) {
@@ -644,35 +647,35 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       const float* Bc = s1 + (int)((u - 2) & (NS1 - 1)) * G::SPLANE + srow;
       const float* C = s1 + (int)((u - 1) & (NS1 - 1)) * G::SPLANE + srow;
       const T* Rp = ring + (sq >= 1 ? sq - 1 : S - 1) * STAGE_T;
-      float c[4], zm[4], zp[4], yp[4], ym[4], rr[4];
-      ldv<4>(Bc, c);
-      ldv<4>(A, zm);
-      ldv<4>(C, zp);
-      ldv<4>(Bc + SW, yp);
-      ldv<4>(Bc - SW, ym);
-      ldv<4>(Rp + rrow, rr);
+      float c[VX], zm[VX], zp[VX], yp[VX], ym[VX], rr[VX];
+      ldv<VX>(Bc, c);
+      ldv<VX>(A, zm);
+      ldv<VX>(C, zp);
+      ldv<VX>(Bc + SW, yp);
+      ldv<VX>(Bc - SW, ym);
+      ldv<VX>(Rp + rrow, rr);
       const float left = Bc[-1];
-      const float right = Bc[4];
+      const float right = Bc[VX];
       const bool zlo = !PER && P == 0, zhi = !PER && P == nz - 1;
       if (!PER && (yface | zlo | zhi)) {
         // face rows and planes: the first sweep's ghost is the face value
 #pragma unroll
-        for (int e = 0; e < 4; ++e) {
+        for (int e = 0; e < VX; ++e) {
           if (y == 0) ym[e] = c[e];
           if (y == ny - 1) yp[e] = c[e];
           if (zlo) zm[e] = c[e];
           if (zhi) zp[e] = c[e];
         }
       }
-      float out[4];
-      jac_row4(J2, c, left, right, ym, yp, zm, zp, rr, out);
+      float out[VX];
+      jac_row<VX>(J2, c, left, right, ym, yp, zm, zp, rr, out);
       T* qk = qrow + (long long)(P - k0) * pzl;
       auto put = [&](T* q) {
-        if (nv >= 4) {
-          stv<T, 4>(q, out);
+        if (nv >= VX) {
+          stv<T, VX>(q, out);
         } else {
 #pragma unroll
-          for (int e = 0; e < 4; ++e)
+          for (int e = 0; e < VX; ++e)
             if (e < nv) q[e] = cvt<T>(out[e]);
         }
       };
@@ -682,7 +685,7 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       // the same block, next to the face cell
       if (!PER && __builtin_expect(xface | yface | zlo | zhi, 0)) {
         if (lane == 0 && i0 == 0) qk[-1] = cvt<T>(out[0]);
-        if (xhi_in) qk[nv] = cvt<T>(pick<4>(out, nv - 1));
+        if (xhi_in) qk[nv] = cvt<T>(pick<VX>(out, nv - 1));
         if (y == 0) put(qk - pyl);
         if (y == ny - 1) put(qk + pyl);
         if (zlo) put(qk - pzl);
@@ -747,11 +750,11 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       mbar_wait(smem_u32(&full[f % S]), (f / S) & 1u);
 }
 
-template <typename T, int TY, int S, bool PER>
+template <typename T, int VX, int TY, int S, bool PER>
 cudaError_t run_ws2(const Launch& L, const JacobiCfg& c, const void* maps, int src_slot, int dst,
                     float omega, float inv_diag) {
-  using G = Ws2Geom<T, TY>;
-  auto kern = k_jacobi2_ws<T, TY, S, PER>;
+  using G = Ws2Geom<T, VX, TY>;
+  auto kern = k_jacobi2_ws<T, VX, TY, S, PER>;
   const int smem = S * G::STAGE + G::NS1 * G::SPLANE * 4 + 8 * (2 * S + G::NS1 + 4) + 16;
   static int occ = -1;
   if (occ < 0) {
@@ -878,10 +881,12 @@ static cudaError_t dispatch_ws2(const Launch& L, const JacobiCfg& c, const void*
                                 int src_slot, int dst, float omega, float inv_diag) {
   cudaError_t e = cudaErrorInvalidValue;
   CFD_DISPATCH_T(L.dtype, {
-    if (c.ty == 16 && c.stages == 7) e = run_ws2<T, 16, 7, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
-    else if (c.ty == 16) e = run_ws2<T, 16, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
-    else if (c.stages == 6) e = run_ws2<T, 8, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
-    else e = run_ws2<T, 8, 5, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    if (c.vx == 2 && c.ty == 16) e = run_ws2<T, 2, 16, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.vx == 2) e = run_ws2<T, 2, 8, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.ty == 16 && c.stages == 7) e = run_ws2<T, 4, 16, 7, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.ty == 16) e = run_ws2<T, 4, 16, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else if (c.stages == 6) e = run_ws2<T, 4, 8, 6, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
+    else e = run_ws2<T, 4, 8, 5, PER>(L, c, maps_dev, src_slot, dst, omega, inv_diag);
   });
   return e;
 }

@@ -20,12 +20,6 @@ namespace {
 
 // ------------------------------------------------------------------ ghosts
 //
-// One thread per ghost cell.  Ghost cells of a block are enumerated without
-// overlap: z-slabs (k outside, all i, j), y-slabs (k inside, j outside, all
-// i), x-slabs (j, k inside, i outside).  The value is that of the sequential
-// x, y, z passes: the source cell is found axis by axis (neighbour block or
-// mirror image) and the wall rules compose as affine maps v -> A + S v.
-
 struct GhostArrays { int arr[kNumArrays]; int n; };
 
 // Ghost fill of the arrays in ga.  A block's ghost shell is 26 disjoint
@@ -36,15 +30,29 @@ struct GhostArrays { int arr[kNumArrays]; int n; };
 // wall rule v -> A + S v (zero normal velocity, tangential 2 U_wall - v,
 // pressure v).  The result is that of ghost passes x, y, z over the full
 // extent, each reading the previous pass's ghosts, with nothing but copies
-// between blocks.  The host cuts the boxes into items of at most 16 rows
-// (GhostItem); CTA i copies item i: its eight warps take rows, the lanes
-// run along the box's inner axis (x unless the box is thinner than 16
-// there), one array at a time, eight cells per lane loaded before any is
-// stored (the loads do not wait behind stores through the same base).
-template <typename T>
-__global__ void __launch_bounds__(256) k_ghost(Launch L, const GhostItem* items,
-                                               const __grid_constant__ GhostArrays ga) {
-  const GhostItem it = items[blockIdx.x];
+// between blocks.  Every source is an interior cell and every destination a
+// ghost cell, so no load of a launch reads what the launch stores.
+//
+// The host cuts the boxes into pieces (GhostItem): an inner-axis range of
+// at most kGhostItemCells cells over some rows of one plane.  Warp w of CTA
+// b copies piece 8 b + w: its lanes form 2^sh columns by 32 >> sh rows, and
+// in up to eight steps they pass over the range (passes steps per row
+// group) and then on to the next rows, so every step is one contiguous run
+// per row and no lane divides.  NA arrays are copied at a time (1, 2 or 4:
+// the fewest that cover the call's arrays in one group, up to four), all
+// their loads issued before any store.  One launch is about one wave of
+// short-lived warps, so the piece -> block -> data chain of loads is paid
+// once per warp, side by side.
+constexpr int kGhostWarps = 8;
+constexpr int kGhostU = 8;  // steps per piece
+template <typename T, int NA>
+__global__ void __launch_bounds__(32 * kGhostWarps) k_ghost(Launch L, const GhostItem* items,
+                                                            int nitems,
+                                                            const __grid_constant__ GhostArrays ga) {
+  const int lane = threadIdx.x & 31;
+  const int item = blockIdx.x * kGhostWarps + (threadIdx.x >> 5);
+  if (item >= nitems) return;
+  const GhostItem it = items[item];
   const BlockDev& B = L.blocks[it.dst];
   const BlockDev& Sd = L.blocks[it.src];
   auto pick3 = [](int i, long long v0, long long v1, long long v2) {
@@ -54,18 +62,64 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, const GhostItem* items,
   const long long dsk = pick3(it.ax[2], 1, B.py, B.pz);
   const long long ssi = pick3(it.ax[0], 1, Sd.py, Sd.pz), ssj = pick3(it.ax[1], 1, Sd.py, Sd.pz);
   const long long ssk = pick3(it.ax[2], 1, Sd.py, Sd.pz);
-  const int ei = it.e[0], ej = it.e[1];
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  const long long dinc = dsi, sinc = (long long)it.st[0] * ssi;
-  constexpr int U = 8;  // cells per lane loaded before any is stored
-  for (int r = it.r0 + warp; r < it.r1; r += 8) {
-    const int rj = r % ej, rk = r / ej;
-    const long long dbase = (long long)(it.d0[1] + rj) * dsj + (long long)(it.d0[2] + rk) * dsk +
-                            (long long)it.d0[0] * dsi;
-    const long long sbase = (long long)(it.s0[1] + it.st[1] * rj) * ssj +
-                            (long long)(it.s0[2] + it.st[2] * rk) * ssk + (long long)it.s0[0] * ssi;
-    for (int ai = 0; ai < ga.n; ++ai) {
-      const int arr = ga.arr[ai];
+  // this lane: column col of each pass, row rs of each row group
+  const int W = 1 << it.sh, RPI = 32 >> it.sh;
+  const int col = lane & (W - 1), rs = lane >> it.sh;
+  const int i = it.i0 + col, rj = it.rj0 + rs;
+  const long long sbase = (long long)(it.s0[0] + it.st[0] * i) * ssi +
+                          (long long)(it.s0[1] + it.st[1] * rj) * ssj +
+                          (long long)(it.s0[2] + it.st[2] * it.rk) * ssk;
+  const long long dbase = (long long)(it.d0[0] + i) * dsi + (long long)(it.d0[1] + rj) * dsj +
+                          (long long)(it.d0[2] + it.rk) * dsk;
+  const long long sp_step = (long long)(it.st[0] * W) * ssi, st_step = (long long)(it.st[1] * RPI) * ssj;
+  const long long dp_step = (long long)W * dsi, dt_step = (long long)RPI * dsj;
+  // step u is pass p, row group t (u = t * passes + p); valid while the
+  // column and the row are inside the piece
+  unsigned valid = 0;
+  {
+    int p = 0, t = 0;
+#pragma unroll
+    for (int u = 0; u < kGhostU; ++u) {
+      if (col + W * p < it.ni && rs + RPI * t < it.nrows) valid |= 1u << u;
+      if (++p == it.passes) {
+        p = 0;
+        ++t;
+      }
+    }
+  }
+  T* const base = reinterpret_cast<T*>(L.base);
+  for (int a0 = 0; a0 < ga.n; a0 += NA) {
+    float v[NA][kGhostU];
+    // both sides' array origins are read before any store: the block table
+    // sits in global memory, so a read after a store would wait for it
+    const T* sp[NA];
+    T* dp[NA];
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      const int arr = ga.arr[a0 + q < ga.n ? a0 + q : a0];
+      sp[q] = base + Sd.org[arr] + sbase;
+      dp[q] = base + B.org[arr] + dbase;
+    }
+    {
+      int p = 0, t = 0;
+#pragma unroll
+      for (int u = 0; u < kGhostU; ++u) {
+        if (valid & (1u << u)) {
+          const long long so = p * sp_step + t * st_step;
+#pragma unroll
+          for (int q = 0; q < NA; ++q)
+            if (a0 + q < ga.n) v[q][u] = ldf<T>(sp[q] + so);
+        }
+        if (++p == it.passes) {
+          p = 0;
+          ++t;
+        }
+      }
+    }
+#pragma unroll
+    for (int q = 0; q < NA; ++q) {
+      if (a0 + q >= ga.n) continue;
+      const int arr = ga.arr[a0 + q];
       // the array's wall rule v -> A + S v, composed over the axes in order
       const int kind = array_kind(arr);
       float A = 0.f, S = 1.f;
@@ -79,16 +133,21 @@ __global__ void __launch_bounds__(256) k_ghost(Launch L, const GhostItem* items,
         A = a + s1 * A;
         S = s1 * S;
       }
-      const T* sp = reinterpret_cast<const T*>(L.base) + Sd.org[arr] + sbase;
-      T* dp = reinterpret_cast<T*>(L.base) + B.org[arr] + dbase;
-      for (int i0 = lane; i0 < ei; i0 += 32 * U) {
-        float v[U];
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (i0 + 32 * u < ei) v[u] = ldf<T>(sp + (i0 + 32 * u) * sinc);
+      for (int u = 0; u < kGhostU; ++u) v[q][u] = S != 0.f ? A + S * v[q][u] : A;
+    }
+    int p = 0, t = 0;
 #pragma unroll
-        for (int u = 0; u < U; ++u)
-          if (i0 + 32 * u < ei) dp[(i0 + 32 * u) * dinc] = cvt<T>(S != 0.f ? A + S * v[u] : A);
+    for (int u = 0; u < kGhostU; ++u) {
+      if (valid & (1u << u)) {
+        const long long d = p * dp_step + t * dt_step;
+#pragma unroll
+        for (int q = 0; q < NA; ++q)
+          if (a0 + q < ga.n) dp[q][d] = cvt<T>(v[q][u]);
+      }
+      if (++p == it.passes) {
+        p = 0;
+        ++t;
       }
     }
   }
@@ -1717,7 +1776,17 @@ cudaError_t launch_ghost(const Launch& L, const int* arrays, int narr, const Gho
   GhostArrays ga{};
   ga.n = narr;
   for (int e = 0; e < narr; ++e) ga.arr[e] = arrays[e];
-  CFD_DISPATCH_T(L.dtype, k_ghost<T><<<(unsigned)nitems, 256, 0, L.stream>>>(L, items, ga));
+  const unsigned ctas = (unsigned)((nitems + kGhostWarps - 1) / kGhostWarps);
+  if (narr == 1) {
+    CFD_DISPATCH_T(L.dtype,
+                   k_ghost<T, 1><<<ctas, 32 * kGhostWarps, 0, L.stream>>>(L, items, nitems, ga));
+  } else if (narr == 2) {
+    CFD_DISPATCH_T(L.dtype,
+                   k_ghost<T, 2><<<ctas, 32 * kGhostWarps, 0, L.stream>>>(L, items, nitems, ga));
+  } else {
+    CFD_DISPATCH_T(L.dtype,
+                   k_ghost<T, 4><<<ctas, 32 * kGhostWarps, 0, L.stream>>>(L, items, nitems, ga));
+  }
   return cudaGetLastError();
 }
 

@@ -18,7 +18,15 @@ smoothed by the first --jacobi variant (default: the grid's).  With
 --time, each variant first runs 4 warm-up sweeps and the timed sweeps are
 bracketed by CUDA events on the grid's stream; the line printed per variant
 gives microseconds per sweep and the algorithmic bytes (read p and r, write
-p) per second.  The launch to capture under ncu is selected with -k/-s/-c.
+p) per second.  With --blocks the grid is the 64-block workload instead
+(per-axis widths U{16..96}, seed 2, periodic, curl-noise start; ghost width
+1 with --order 2, 2 with --order 4).  With --ghost N it runs N ghost fills
+of each array list given by --arrays (e.g. p r,p u,v,w,p).  The launch to
+capture under ncu is selected with -k/-s/-c.
+
+    python -m paper_1201_2118_gb300.profile_case --blocks --order 4 --ghost 5 --arrays p r,p u,v,w,p
+    python -m paper_1201_2118_gb300.profile_case --blocks --order 4 --time --sweeps 20 \\
+        --jacobi 9,2,8,32,6 7,2,8,32,6
 """
 import argparse
 import os
@@ -42,6 +50,11 @@ def main(argv=None):
     ap.add_argument("--descriptor", type=int, default=0,
                     help="instead of sweeps: this many projections by the library's kernel "
                          "and by the same projection generated from a kernel descriptor")
+    ap.add_argument("--blocks", action="store_true",
+                    help="the 64-block workload instead of the n^3 cavity")
+    ap.add_argument("--ghost", type=int, default=0,
+                    help="instead of sweeps: this many ghost fills of each --arrays list")
+    ap.add_argument("--arrays", nargs="*", default=["p"], help="array lists, e.g. p r,p u,v,w,p")
     a = ap.parse_args(argv)
     root = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
     if root not in sys.path:
@@ -51,13 +64,47 @@ def main(argv=None):
     from paper_1201_2118_gb300 import Grid
     n = a.n
     s = torch.cuda.Stream()
-    g = Grid((n, n, n), ghost=1 if a.order == 2 else 2, h=(1.0 / n,) * 3, dtype=a.dtype, stream=s)
-    g.set_cavity(1.0)
-    g.set_params(1e-3, 50, 1.0, a.order)
-    g.set_advection(a.form)
-    g.upload(workloads.ldc_noise(n, seed=1))
+    if a.blocks:
+        cfg = workloads.WORKLOADS["blocks64"]
+        gd, blocks = workloads.block_tiling(seed=cfg["tiling_seed"])
+        h = workloads.workload_h("blocks64")
+        g = Grid(ghost=1 if a.order == 2 else 2, h=h, dtype=a.dtype, stream=s,
+                 blocks=[(b["dims"], b["origin"]) for b in blocks], global_dims=gd)
+        g.set_params(cfg["nu"], cfg["jacobi_iters"], 1.0, a.order)
+        g.set_advection(a.form)
+        g.upload_blocks(workloads.split_blocks(workloads.random_div_free(gd, h, seed=cfg["ic_seed"]),
+                                               blocks))
+        cells = gd[0] * gd[1] * gd[2]
+        name = "blocks64 g=%d" % (1 if a.order == 2 else 2)
+    else:
+        g = Grid((n, n, n), ghost=1 if a.order == 2 else 2, h=(1.0 / n,) * 3, dtype=a.dtype,
+                 stream=s)
+        g.set_cavity(1.0)
+        g.set_params(1e-3, 50, 1.0, a.order)
+        g.set_advection(a.form)
+        g.upload(workloads.ldc_noise(n, seed=1))
+        cells = n ** 3
+        name = "%d^3" % n
     g.pressure_solve(1e-3, 0)
     es = 4 if a.dtype == "f32" else 2
+    if a.ghost:
+        import paper_1201_2118_gb300 as pk
+        for lst in a.arrays:
+            m = pk.mask(*[getattr(pk, x.strip().upper()) for x in lst.split(",")])
+            if a.time:
+                g.ghost_fill(m)
+                torch.cuda.synchronize()
+                e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                e0.record(s)
+            for _ in range(a.ghost):
+                g.ghost_fill(m)
+            if a.time:
+                e1.record(s)
+            torch.cuda.synchronize()
+            print("%s %s ghost fill of %s%s" % (name, a.dtype, lst, " %.1f us" % (
+                e0.elapsed_time(e1) * 1e3 / a.ghost) if a.time else ""), flush=True)
+        g.check()
+        return
     if a.descriptor:
         from paper_1201_2118_gb300 import (Descriptor, GeneratedKernel, P, SET_U1, U1, V1, W1, WU,
                                            WV, WW)
@@ -151,7 +198,7 @@ def main(argv=None):
         if not a.time:
             g.jacobi(a.sweeps)
             torch.cuda.synchronize()
-            print("ok", n, a.dtype, cfg, a.sweeps, flush=True)
+            print("ok", name, a.dtype, cfg, a.sweeps, flush=True)
             continue
         g.jacobi(4)
         torch.cuda.synchronize()
@@ -161,8 +208,8 @@ def main(argv=None):
         e1.record(s)
         torch.cuda.synchronize()
         us = e0.elapsed_time(e1) * 1e3 / a.sweeps
-        gbs = 3 * es * n ** 3 / (us * 1e-6) / 1e9
-        print("%d^3 %s %s %.1f us/sweep %.0f GB/s" % (n, a.dtype, cfg, us, gbs), flush=True)
+        gbs = 3 * es * cells / (us * 1e-6) / 1e9
+        print("%s %s %s %.1f us/sweep %.0f GB/s" % (name, a.dtype, cfg, us, gbs), flush=True)
     g.check()
 
 

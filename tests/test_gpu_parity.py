@@ -327,7 +327,8 @@ def test_blockset_step_equals_global_oracle(order, g):
 
 
 @pytest.mark.parametrize("order,g,jacobi", [(2, 1, (0, 4, 4, 32, 4)), (4, 2, (0, 4, 4, 32, 4)),
-                                             (4, 2, (9, 4, 16, 16, 6)), (4, 2, (9, 4, 8, 32, 6))])
+                                             (4, 2, (9, 4, 16, 16, 6)), (4, 2, (9, 4, 8, 32, 6)),
+                                             (4, 2, (9, 2, 16, 16, 6)), (4, 2, (9, 2, 8, 32, 6))])
 def test_blockset_workload_tiling_equals_global_oracle(order, g, jacobi):
     """The block-set workload's own tiling: 64 blocks with per-axis widths
     U{16..96} (seed 2), curl-noise start (seed 3), two RK2 steps with 20

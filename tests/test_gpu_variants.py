@@ -204,10 +204,38 @@ def test_per_block_launch_mode_is_bitwise_identical(g):
         np.testing.assert_array_equal(x, y)
 
 
+@pytest.mark.parametrize("cfg", [(9, 4, 16, 16, 6), (9, 2, 8, 16, 6)], ids=cfg_id)
+def test_two_sweep_blockset_equals_per_block_single_sweeps(cfg):
+    """With two ghost layers the batched form takes the Jacobi sweeps two
+    per launch over all blocks; the per-block baseline takes them one per
+    launch and block.  Two steps with 11 sweeps per solve (an odd count:
+    five two-sweep launches and a single one) agree bit for bit."""
+    from paper_1201_2118_gb300 import Grid, U, V, W, P
+    gd, blocks = workloads.block_tiling(seed=2, lo=8, hi=24)
+    h = (2 * math.pi / 64,) * 3
+    fl = workloads.random_div_free(gd, h, seed=3)
+    per = workloads.split_blocks(fl, blocks)
+    res = []
+    for mode in (False, True):
+        grid = Grid(ghost=2, h=h, blocks=[(b["dims"], b["origin"]) for b in blocks], global_dims=gd)
+        grid.set_params(0.01, 11, 1.0, 4)
+        grid.set_kernel_config(jacobi=cfg)
+        grid.set_launch_mode(mode)
+        grid.upload_blocks(per)
+        l0 = grid.launches
+        grid.step(workloads.cfl_dt(h), 2)
+        res.append([grid.download(a, block=b) for b in range(len(blocks)) for a in (U, V, W, P)])
+        if mode:  # single sweeps, one launch per block
+            assert grid.launches - l0 >= 2 * 2 * 11 * len(blocks)
+        grid.check()
+    for x, y in zip(*res):
+        np.testing.assert_array_equal(x, y)
+
+
 @pytest.mark.parametrize("dtype", ["bf16", "f16"])
 @pytest.mark.parametrize("cfg", [(3, 8, 4, 32, 5), (3, 8, 8, 16, 6), (3, 8, 2, 64, 6),
                                  (1, 4, 8, 32, 6), (2, 4, 4, 2, 0), (7, 4, 8, 32, 8),
-                                 (9, 4, 16, 16, 6), (9, 4, 8, 32, 5)],
+                                 (9, 4, 16, 16, 6), (9, 4, 8, 32, 5), (9, 2, 16, 16, 6)],
                          ids=cfg_id)
 def test_16bit_jacobi_variants_agree_with_register_sweep(dtype, cfg):
     """Every 16-bit sweep variant computes the same FP32 expression and
@@ -283,7 +311,8 @@ def test_fused_two_sweep_launches_match_oracle(cfg, bc, iters, dims):
     g.check()
 
 
-@pytest.mark.parametrize("cfg", [(9, 4, 16, 16, 7), (9, 4, 8, 7, 5), (9, 4, 8, 64, 6), (9, 4, 16, 3, 6)],
+@pytest.mark.parametrize("cfg", [(9, 4, 16, 16, 7), (9, 4, 8, 7, 5), (9, 4, 8, 64, 6), (9, 4, 16, 3, 6),
+                                 (9, 2, 16, 16, 6), (9, 2, 8, 7, 6)],
                          ids=cfg_id)
 @pytest.mark.parametrize("iters", [1, 2, 5, 10])
 @pytest.mark.parametrize("dims", [(128, 40, 21), (150, 37, 21), (300, 16, 2), (70, 5, 33)])
@@ -313,7 +342,8 @@ def test_two_sweep_ws_launches_match_oracle(cfg, iters, dims):
     g.check()
 
 
-@pytest.mark.parametrize("cfg", [(9, 4, 16, 16, 6), (9, 4, 8, 7, 5), (9, 4, 16, 64, 7)], ids=cfg_id)
+@pytest.mark.parametrize("cfg", [(9, 4, 16, 16, 6), (9, 4, 8, 7, 5), (9, 4, 16, 64, 7), (9, 2, 16, 16, 6),
+                                 (9, 2, 8, 7, 6)], ids=cfg_id)
 @pytest.mark.parametrize("iters", [1, 2, 5, 10])
 @pytest.mark.parametrize("dims", [(128, 40, 21), (150, 37, 21), (70, 5, 33)])
 def test_two_sweep_ws_periodic_ghost2_matches_oracle(cfg, iters, dims):
