@@ -422,8 +422,8 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
 // over x = i0 .. i0 + 32 VX - 1 and the extras warp the cells x = i0 - 1 and
 // x = i0 + 32 VX of every row; both store it, rounded to the storage type,
 // into slot t (row width 32 VX + 8: x = i0 - 4 at index 0).  An mbarrier per
-// slot (count TY + 3) says that every row of a first-sweep plane is
-// written; each iteration starts by waiting for the plane of iteration
+// slot (one arrival per thread of the TY + 3 row and extras warps) says
+// that every row of a first-sweep plane is written; each iteration starts by waiting for the plane of iteration
 // t - 2, which is all the second sweep needs from other warps and bounds
 // the skew: a warp writing slot t may coexist with one reading slot t - 4,
 // so NS1 >= 5; it is 8.  First-sweep values outside the block (walls:
@@ -484,10 +484,10 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
 #pragma unroll
     for (int s = 0; s < S; ++s) {
       mbar_init(smem_u32(&full[s]), 1);
-      mbar_init(smem_u32(&empty[s]), NW + 1);
+      mbar_init(smem_u32(&empty[s]), 32 * (NW + 1));  // every lane of the row and extras warps
     }
 #pragma unroll
-    for (int s = 0; s < NS1; ++s) mbar_init(smem_u32(&s1bar[s]), NW + 1);
+    for (int s = 0; s < NS1; ++s) mbar_init(smem_u32(&s1bar[s]), 32 * (NW + 1));
     tq.init();
     mbar_fence_init();
   }
@@ -566,36 +566,71 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     const long long pzl = B.pz;
     T* qrow = reinterpret_cast<T*>(L.base) + B.org[dst] + (long long)y * B.py + x0 +
               (long long)k0 * pzl;  // plane k0 of the output row
-    auto release = [&](int st) {
-      __syncwarp();
-      if (lane == 0) mbar_arrive(smem_u32(&empty[st]));
-    };
-    // ring positions: stage of plane m - 1 (q = t) with its phase; first-
-    // sweep iterations are numbered across tiles (u = it1 + t), slot u % 8
-    int sq = (int)(seq % S);
-    uint32_t phq = (seq / S) & 1u;
     // this lane has first-sweep cells (PER: also the ghost column x = nx)
     const bool act1 = y1 && (PER ? x0 <= nx : nv > 0);
     const bool act2 = out_row && nv > 0;               // ... and second-sweep outputs
     const bool yface = (y == 0) | (y == ny - 1);
     const bool xface = (lane == 0 && i0 == 0) | xhi_in;  // lanes with an x image
     const int pyl = B.py;
-    auto wait_full = [&](int st, uint32_t ph) {
-      if (!mbar_wait_split(smem_u32(&full[st]), ph)) bad = true;
-    };
-    auto wait_s1 = [&](unsigned u) {
-      if (!mbar_wait_split(smem_u32(&s1bar[u & (NS1 - 1)]), (u / NS1) & 1u)) bad = true;
+    // Ring cursors, moved on once per iteration t by an add and a wrap: the
+    // stages of p planes q - 1 .. q + 2 (q = t), the full barrier of q + 2
+    // with its phase, the empty barrier of q - 1, the first-sweep slots of
+    // iterations u - 3 .. u (u = it1 + t, numbered across tiles), the slot
+    // barrier of u - 2 (waited on, with its phase) and that of u (arrived
+    // at), and the output row of plane k0 - 3 + t.  Every lane arrives on
+    // the empty and slot barriers itself (their counts are per thread), so
+    // no warp sync or single-lane branch is needed.
+    const T* const ring_end = ring + S * STAGE_T;
+    float* const s1_end = s1 + NS1 * G::SPLANE;
+    const uint32_t full0 = smem_u32(&full[0]), empty0 = smem_u32(&empty[0]);
+    const uint32_t s1b0 = smem_u32(&s1bar[0]);
+    const int st0 = (int)(seq % S);
+    const T* stR = ring + (st0 == 0 ? S - 1 : st0 - 1) * STAGE_T;
+    const T* stM = ring + st0 * STAGE_T;
+    const T* stC = ring + wrapn<S>(st0 + 1) * STAGE_T;
+    const T* stP = ring + wrapn<S>(st0 + 2) * STAGE_T;
+    uint32_t fbar = full0 + 8u * (uint32_t)wrapn<S>(st0 + 2), fph = ((seq + 2) / S) & 1u;
+    uint32_t ebar = empty0 + 8u * (uint32_t)(st0 == 0 ? S - 1 : st0 - 1);
+    const unsigned u0 = it1;
+    float* sA = s1 + (int)((u0 - 3) & (NS1 - 1)) * G::SPLANE;
+    float* sB = s1 + (int)((u0 - 2) & (NS1 - 1)) * G::SPLANE;
+    float* sC = s1 + (int)((u0 - 1) & (NS1 - 1)) * G::SPLANE;
+    float* sW = s1 + (int)(u0 & (NS1 - 1)) * G::SPLANE;
+    uint32_t bwait = s1b0 + 8u * ((u0 - 2) & (NS1 - 1)), bwph = ((u0 - 2) / NS1) & 1u;
+    uint32_t barr = s1b0 + 8u * (u0 & (NS1 - 1));
+    T* qk = qrow - 3 * pzl;
+    auto advance = [&]() {
+      stR = stM;
+      stM = stC;
+      stC = stP;
+      stP = stP + STAGE_T == ring_end ? ring : stP + STAGE_T;
+      fbar += 8u;
+      if (fbar == full0 + 8u * S) {
+        fbar = full0;
+        fph ^= 1u;
+      }
+      ebar = ebar + 8u == empty0 + 8u * S ? empty0 : ebar + 8u;
+      sA = sB;
+      sB = sC;
+      sC = sW;
+      sW = sW + G::SPLANE == s1_end ? s1 : sW + G::SPLANE;
+      bwait += 8u;
+      if (bwait == s1b0 + 8u * NS1) {
+        bwait = s1b0;
+        bwph ^= 1u;
+      }
+      barr = barr + 8u == s1b0 + 8u * NS1 ? s1b0 : barr + 8u;
+      qk += pzl;
     };
     // first sweep on plane m = k0 - 1 + t into slot u = it1 + t
     auto sweep1 = [&](int t) {
       const int m = k0 - 1 + t;
-      const int sc = wrapn<S>(sq + 1), sp = wrapn<S>(sq + 2);
-      wait_full(sp, phq ^ (uint32_t)(sq + 2 >= S));
+      if (!mbar_wait_split(fbar, fph)) bad = true;
       if (bad) return;
-      const T* Pm = ring + sq * STAGE_T;
-      const T* Pc = ring + sc * STAGE_T;
-      const T* Pp = ring + sp * STAGE_T;
-      float* S1 = s1 + (int)((it1 + t) & (NS1 - 1)) * G::SPLANE;
+      const T* Pm = stM;
+      const T* Pc = stC;
+      const T* Pp = stP;
+      float* S1 = sW;
       const bool mreal = PER ? (m >= -1) & (m <= nz) : (m >= 0) & (m < nz);
       if (act1 && mreal) {
         float c[VX], zm[VX], zp[VX], yp[VX], ym[VX], rr[VX];
@@ -641,12 +676,11 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     // second sweep on plane P = k0 - 3 + t from slots u - 3, u - 2, u - 1
     // (u = it1 + t) and r from the stage of plane P (q = t - 1)
     auto sweep2 = [&](int t) {
-      const unsigned u = it1 + t;
       const int P = k0 - 3 + t;
-      const float* A = s1 + (int)((u - 3) & (NS1 - 1)) * G::SPLANE + srow;
-      const float* Bc = s1 + (int)((u - 2) & (NS1 - 1)) * G::SPLANE + srow;
-      const float* C = s1 + (int)((u - 1) & (NS1 - 1)) * G::SPLANE + srow;
-      const T* Rp = ring + (sq >= 1 ? sq - 1 : S - 1) * STAGE_T;
+      const float* A = sA + srow;
+      const float* Bc = sB + srow;
+      const float* C = sC + srow;
+      const T* Rp = stR;
       float c[VX], zm[VX], zp[VX], yp[VX], ym[VX], rr[VX];
       ldv<VX>(Bc, c);
       ldv<VX>(A, zm);
@@ -669,7 +703,6 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
       }
       float out[VX];
       jac_row<VX>(J2, c, left, right, ym, yp, zm, zp, rr, out);
-      T* qk = qrow + (long long)(P - k0) * pzl;
       auto put = [&](T* q) {
         if (nv >= VX) {
           stv<T, VX>(q, out);
@@ -694,53 +727,48 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     };
     // end of iteration t: the first-sweep plane of slot u is written and
     // (t >= 1) the stage of plane m - 2 is no longer read
-    auto finish = [&](int t, bool first_plane_done, bool stage_done) {
-      __syncwarp();
-      if (lane == 0) {
-        if (first_plane_done) mbar_arrive(smem_u32(&s1bar[(it1 + t) & (NS1 - 1)]));
-        if (stage_done) mbar_arrive(smem_u32(&empty[sq >= 1 ? sq - 1 : S - 1]));
-      }
-      if (++sq == S) {
-        sq = 0;
-        phq ^= 1u;
-      }
+    auto finish = [&](bool first_plane_done, bool stage_done) {
+      if (first_plane_done) mbar_arrive(barr);
+      if (stage_done) mbar_arrive(ebar);
+      advance();
     };
     // planes k0 - 2 and k0 - 1 must be there before the first iteration
-    wait_full(sq, phq);
-    wait_full(wrapn<S>(sq + 1), phq ^ (uint32_t)(sq + 1 >= S));
+    if (!mbar_wait_split(full0 + 8u * (uint32_t)st0, (seq / S) & 1u)) bad = true;
+    if (!mbar_wait_split(full0 + 8u * (uint32_t)wrapn<S>(st0 + 1), ((seq + 1) / S) & 1u)) bad = true;
     // Each iteration first waits for the first-sweep plane of two iterations
     // before (also across tiles: this bounds the skew between warps), takes
     // the second sweep (iterations 3 ..), then the first (.. nzc + 1).
     // Iterations 0 .. 2: first sweep only (the first output plane needs the
     // first sweep on k0 - 1 .. k0 + 1).
     for (int t2 = 0; t2 < 3 && !bad; ++t2) {
-      if (it1 + t2 >= 2) wait_s1(it1 + t2 - 2);
+      if (it1 + t2 >= 2 && !mbar_wait_split(bwait, bwph)) bad = true;
       if (bad) break;
       sweep1(t2);
       if (bad) break;
-      finish(t2, true, t2 >= 1);
+      finish(true, t2 >= 1);
     }
     // iterations 3 .. nzc + 1: both sweeps
     for (int t2 = 3; t2 <= nzc + 1 && !bad; ++t2) {
-      wait_s1(it1 + t2 - 2);
+      if (!mbar_wait_split(bwait, bwph)) bad = true;
       if (bad) break;
       if (act2) sweep2(t2);
       sweep1(t2);
       if (bad) break;
-      finish(t2, true, true);
+      finish(true, true);
     }
     // iteration nzc + 2: second sweep on the last plane only
     if (!bad) {
-      wait_s1(it1 + nzc);
+      if (!mbar_wait_split(bwait, bwph)) bad = true;
       if (!bad) {
         if (act2) sweep2(nzc + 2);
-        finish(nzc + 2, false, true);
+        finish(false, true);
       }
     }
     if (bad) break;
-    // stages of planes k1, k1 + 1 (q = nzc + 2, nzc + 3): sq now points at q = nzc + 3
-    release(sq >= 1 ? sq - 1 : S - 1);
-    release(sq);
+    // stages of planes k1, k1 + 1 (q = nzc + 2, nzc + 3): ebar is that of
+    // q = nzc + 2 now
+    mbar_arrive(ebar);
+    mbar_arrive(ebar + 8u == empty0 + 8u * S ? empty0 : ebar + 8u);
     seq += np;
     it1 += nzc + 2;
   }
