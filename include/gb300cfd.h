@@ -405,7 +405,10 @@ cfd_status cfd_stats(const cfd_grid* g, long long* kernel_launches);
  * once any kernel has set the grid's device error flag (a bounded wait ran
  * out, or a TMA destination was misaligned).  The flag stays set, so later
  * calls keep reporting it, until memory is bound again (cfd_bind_memory /
- * cfd_alloc_memory clear it); the CUDA context stays usable. */
+ * cfd_alloc_memory clear it); the CUDA context stays usable.  Results
+ * computed after a kernel gave up are undefined until then: such a kernel
+ * leaves early, also leaving the run-time tile counter of the TMA-staged
+ * sweeps off its start, which binding memory resets as well. */
 cfd_status cfd_check(cfd_grid* g);
 
 /* Failure-detection self-test (the paper has no counterpart: it checks the
