@@ -408,7 +408,9 @@ cfd_status cfd_stats(const cfd_grid* g, long long* kernel_launches);
  * cfd_alloc_memory clear it); the CUDA context stays usable.  Results
  * computed after a kernel gave up are undefined until then: such a kernel
  * leaves early, also leaving the run-time tile counter of the TMA-staged
- * sweeps off its start, which binding memory resets as well. */
+ * sweeps off its start, which binding memory resets as well.  While the
+ * flag is set, TMA-staged sweep launches (kinds 1, 7, 9) do no work, so a
+ * failed solve costs one wait limit rather than one per launch. */
 cfd_status cfd_check(cfd_grid* g);
 
 /* Failure-detection self-test (the paper has no counterpart: it checks the

@@ -89,7 +89,10 @@ __global__ void __launch_bounds__(32 * TY) k_jacobi_tma(Launch L, const CUtensor
   uint32_t parity = 0;
   int sbase = 0;
   __shared__ TileTable tt;
+  __shared__ int flag0;
+  flag_at_start(L, flag0);
   tile_table_build(tt, L, TX, TY, zc);
+  if (flag0) return;
   int blk = L.b0;
   // tiles claimed at run time from the counter in the grid's flag area:
   // thread 0 claims, the CTA barrier hands the number out (two slots: a
@@ -271,7 +274,10 @@ __global__ void __launch_bounds__(32 * (TY + 1)) k_jacobi_ws(Launch L, const CUt
     mbar_fence_init();
   }
   __shared__ TileTable tt;
+  __shared__ int flag0;
+  flag_at_start(L, flag0);
   tile_table_build(tt, L, TX, TY, zc);  // also orders the barrier init before use
+  if (flag0) return;
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
   const int g = L.ghost;
   constexpr int xo = kAlignBytes / (int)sizeof(T);
@@ -492,7 +498,10 @@ __global__ void __launch_bounds__(32 * (TY + 4), 1) k_jacobi2_ws(Launch L, const
     mbar_fence_init();
   }
   __shared__ TileTable tt;
+  __shared__ int flag0;
+  flag_at_start(L, flag0);
   tile_table_build(tt, L, TX, TY, zc);  // also orders the barrier init before use
+  if (flag0) return;
   const float cx = L.ih2[0], cy = L.ih2[1], cz = L.ih2[2];
   const Jac2 J2(cx, cy, cz, omega, inv_diag);
   const int g = L.ghost;

@@ -101,6 +101,16 @@ struct Ring {
   }
 };
 
+// The device error flag as a launch finds it: thread (0, 0) copies it to
+// shared memory before the CTA's first barrier; after that barrier every
+// thread tests the copy.  A launch that finds it set (a bounded wait of an
+// earlier launch gave up, and results are undefined until memory is bound
+// again) does no work, so a failed solve costs one wait limit, not one per
+// launch.
+__device__ __forceinline__ void flag_at_start(const Launch& L, int& shared_copy) {
+  if (threadIdx.x == 0 && threadIdx.y == 0) shared_copy = *reinterpret_cast<volatile int*>(L.err_flag);
+}
+
 // The tile counter of a launch: a word of the grid's flag area (zeroed when
 // memory is bound), 128 bytes after the device error flag.
 __device__ __forceinline__ unsigned* tile_counter(const Launch& L) {

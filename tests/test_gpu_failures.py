@@ -104,6 +104,38 @@ def test_device_wait_runs_out_and_check_reports_timeout(form):
     assert L.cfd_selftest_wait_timeout(g.handle, 2) == 1
 
 
+@pytest.mark.parametrize("jacobi", [(9, 4, 16, 16, 6), (7, 4, 16, 32, 8), (1, 4, 16, 16, 4)])
+def test_sweeps_do_no_work_once_a_wait_gave_up(jacobi):
+    """A TMA-staged sweep launch that finds the device error flag set does
+    nothing (a failed solve then costs one wait limit, not one per launch):
+    after the self-test has set the flag, four sweeps leave P as it was;
+    once memory is bound again they run."""
+    import torch
+    from paper_1201_2118_gb300 import Grid, P, _lib
+    L = _lib.lib()
+    n = (64, 32, 16)
+    g = Grid(n, ghost=1, h=tuple(1.0 / d for d in n))
+    g.set_cavity(1.0)
+    g.set_kernel_config(jacobi=jacobi)
+    g.set_params(1e-3, 10, 1.0, 2)
+    g.upload(workloads.ldc_noise(n, seed=1))
+    g.step(1e-3, 1)                      # R, P and its ghosts from a full step
+    g.check()
+    p0 = g.download(P)
+    assert np.isfinite(p0).all()
+    g.selftest_wait_timeout(0)
+    assert L.cfd_check(g.handle) == 7
+    g.jacobi(4)
+    torch.cuda.synchronize()
+    np.testing.assert_array_equal(g.download(P), p0)
+    assert L.cfd_check(g.handle) == 7
+    assert L.cfd_bind_memory(g.handle, ctypes.c_void_p(g.mem.data_ptr() + g._shift), g.nbytes) == 0
+    g.jacobi(4)
+    g.check()
+    p1 = g.download(P)
+    assert np.isfinite(p1).all() and np.abs(p1 - p0).max() > 0
+
+
 @pytest.mark.parametrize("case", ["cavity", "periodic_tg"])
 def test_checkpoint_restore_continues_bitwise(case):
     """Run A: n1 steps, save, n2 more.  Run B: a fresh grid restored from
