@@ -7,7 +7,9 @@
   completes through the same bounded wait as the TMA-staged Jacobi kernels;
   the wait runs out after its limit, the kernel sets the device error flag
   and returns, cfd_check reports CFD_ETIMEOUT, and the context and the grid
-  stay usable.  No trap, no bad address, no endless loop.
+  stay usable.  No trap, no bad address, no endless loop.  While the flag
+  is set the TMA-staged sweep kernels do no work; binding memory again
+  clears it.
 * Checkpoint/resume: the state saved from one grid (u, v, w, p through the
   host-copy entry point, t and the step counter) and restored into a fresh
   grid continues bit for bit like the uninterrupted run.
